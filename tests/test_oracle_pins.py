@@ -1,0 +1,285 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test targets a plausible mistake: a dropped or extra factor in Eq. 2 (closed
+form, brute force), a wrong cavity index (closed form), a transposed pairwise
+table (asymmetric tables on trees), a wrong residual or convergence test
+(invariants, special cases), a wrong schedule (identities, serial RBP), a wrong
+random stream (Philox known answers), a wrong selection (top-k, BFS).
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse
+import scipy.sparse.csgraph
+
+from paper_1909_11469_gb300 import synth
+from tests import _exact
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------- Philox
+def test_philox_known_answers(orc):
+    rows = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out = orc.philox4x32_10(w[:4], w[4:6])
+        assert [int(x) for x in out] == w[6:]
+        rows += 1
+    assert rows == 3
+
+
+def test_rnbp_random_filter_fraction(orc):
+    """With every message above eps and p = HighP = 0.3 in round 1, the committed
+    fraction is Binomial(M, 0.3): within 5 sigma."""
+    prob = synth.ising_grid(60, 1.0, seed=3)
+    res = orc.run(prob, "rnbp", parallelism=0.3, high_p=0.3, eps=1e-12, max_rounds=1,
+                  trace_cap=1)
+    m = prob.m
+    picked = int(np.unpackbits(res["trace"][0].view(np.uint8)).sum())
+    assert res["committed_updates"] == picked
+    sd = np.sqrt(m * 0.3 * 0.7)
+    assert abs(picked - 0.3 * m) < 5 * sd
+
+
+# --------------------------------------------------------------------------- Eq. 2
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ising_message_closed_form(orc, seed):
+    """Every candidate of a random message state equals the atanh closed form."""
+    prob = synth.ising_grid(6, 2.5, seed=seed)
+    rng = np.random.default_rng(100 + seed)
+    p1 = rng.uniform(0.05, 0.95, size=prob.m)
+    msg = np.stack([1 - p1, p1], axis=1)
+    cand, r = orc.evaluate(prob, msg)
+    for e in range(prob.m):
+        u = 0.5 * np.log(cand[e, 1] / cand[e, 0])
+        assert abs(u - _exact.ising_closed_form(prob, msg, e)) < 1e-13
+        assert abs(r[e] - np.abs(cand[e] - msg[e]).max()) < 1e-15
+    assert np.allclose(cand.sum(axis=1), 1.0, atol=1e-14)
+
+
+def test_table_message_direct_eq2(orc):
+    """Asymmetric tables, k = 3: every candidate equals a direct transcription of
+    Eq. 2 (catches a transposed table or a wrong cavity)."""
+    prob = synth.random_table_graph(7, 3, extra_edges=3, seed=5)
+    rng = np.random.default_rng(9)
+    msg = rng.uniform(0.1, 1.0, size=(prob.m, 3))
+    msg /= msg.sum(axis=1, keepdims=True)
+    cand, _ = orc.evaluate(prob, msg)
+    for e in range(prob.m):
+        np.testing.assert_allclose(cand[e], _exact.message_eq2(prob, msg, e), rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------------------------------- trees
+@pytest.mark.parametrize("schedule,par", [("lbp", 1.0), ("rbp", 0.1), ("rs", 0.05), ("rnbp", 0.5)])
+def test_tree_exact_brute_force(orc, schedule, par):
+    """BP is exact on trees: every schedule converges to the brute-force marginals."""
+    prob = synth.ising_tree(12, 2.0, seed=11)
+    res = orc.run(prob, schedule, parallelism=par, eps=1e-13, max_rounds=5000, seed=7)
+    assert res["converged"]
+    exact = _exact.brute_force_marginals(prob)
+    assert np.abs(res["beliefs"] - exact).max() < 1e-12
+
+
+def test_tree_exact_tables_k3(orc):
+    prob = synth.random_table_graph(9, 3, extra_edges=0, seed=4)
+    res = orc.run(prob, "lbp", eps=1e-14, max_rounds=100)
+    assert res["converged"]
+    assert np.abs(res["beliefs"] - _exact.brute_force_marginals(prob)).max() < 1e-12
+
+
+def test_lbp_tree_rounds_bounded_by_diameter(orc):
+    """On a tree LBP messages are exact after diameter rounds, so the residuals are
+    exactly zero at the next evaluation."""
+    prob = synth.ising_chain(40, 2.0, seed=2)
+    res = orc.run(prob, "lbp", eps=1e-300, max_rounds=1000)
+    assert res["converged"] and res["final_max_residual"] == 0.0
+    assert res["rounds"] <= 39
+
+
+def test_chain_forward_backward(orc):
+    prob = synth.paper_ising(1, 300, C=10.0, seed=1)
+    res = orc.run(prob, "lbp", eps=1e-14, max_rounds=1000)
+    assert res["converged"]
+    assert np.abs(res["beliefs"] - _exact.chain_marginals(prob)).max() < 1e-11
+
+
+# --------------------------------------------------------------------------- special cases
+def test_zero_field_symmetric_beliefs(orc):
+    """lambda = 0: the model is symmetric under x -> -x, so beliefs are (1/2, 1/2)."""
+    prob = synth.ising_grid(8, 2.0, seed=4, lam_max=0.0)
+    res = orc.run(prob, "lbp", eps=1e-4, max_rounds=50)
+    assert np.abs(res["beliefs"] - 0.5).max() < 1e-15
+
+
+def test_zero_coupling_converges_immediately(orc):
+    """beta = 0: every candidate is uniform, so the uniform start is already a fixed
+    point: rounds = 0 and beliefs are the normalised unaries."""
+    prob = synth.ising_grid(7, 0.0, seed=4)
+    res = orc.run(prob, "lbp", eps=1e-12, max_rounds=50)
+    assert res["converged"] and res["rounds"] == 0
+    un = np.exp(prob.unary_log.astype(np.float64).reshape(-1, 2))
+    assert np.abs(res["beliefs"] - un / un.sum(axis=1, keepdims=True)).max() < 1e-15
+
+
+def test_single_edge_one_round(orc):
+    """Two vertices, one edge: the first round commits the exact messages; the
+    next evaluation finds zero residuals."""
+    row_ptr, col, rev = synth.csr_from_undirected(2, np.array([0]), np.array([1]))
+    prob = synth.Problem(2, 2, row_ptr, col, rev, np.array([-0.3, 0.3, 0.7, -0.7], np.float32),
+                         synth.PAIR_ISING_BETA, np.array([1.1, 1.1], np.float32),
+                         np.array([0, 2], np.int64))
+    res = orc.run(prob, "lbp", eps=1e-15, max_rounds=10)
+    assert res["converged"] and res["rounds"] == 1
+    assert np.abs(res["beliefs"] - _exact.brute_force_marginals(prob)).max() < 1e-15
+
+
+def test_isolated_vertices(orc):
+    """A vertex without neighbours keeps its normalised unary as belief."""
+    row_ptr, col, rev = synth.csr_from_undirected(4, np.array([0]), np.array([2]))
+    un = np.array([0.1, -0.2, 0.5, 0.4, -1.0, 1.0, 0.0, 0.3], np.float32)
+    prob = synth.Problem(4, 2, row_ptr, col, rev, un, synth.PAIR_ISING_BETA,
+                         np.array([0.8, 0.8], np.float32), np.array([0, 4], np.int64))
+    res = orc.run(prob, "lbp", eps=1e-15, max_rounds=10)
+    e = np.exp(un.astype(np.float64).reshape(4, 2))
+    for v in (1, 3):
+        assert np.abs(res["beliefs"][v] - e[v] / e[v].sum()).max() < 1e-15
+    assert np.abs(res["beliefs"] - _exact.brute_force_marginals(prob)).max() < 1e-15
+
+
+def test_empty_graph(orc):
+    row_ptr, col, rev = synth.csr_from_undirected(3, np.zeros(0, np.int64), np.zeros(0, np.int64))
+    prob = synth.Problem(3, 2, row_ptr, col, rev, np.zeros(6, np.float32),
+                         synth.PAIR_ISING_BETA, np.zeros(0, np.float32), np.array([0, 3], np.int64))
+    res = orc.run(prob, "rnbp", parallelism=0.5)
+    assert res["converged"] and res["rounds"] == 0
+    assert np.all(res["beliefs"] == 0.5)
+
+
+# --------------------------------------------------------------------------- invariants
+@pytest.mark.parametrize("schedule,par", [("lbp", 1.0), ("rbp", 0.05), ("rs", 0.01), ("rnbp", 0.5)])
+def test_loopy_invariants(orc, schedule, par):
+    """Messages stay normalised; a converged state is an eps fixed point of Eq. 2
+    (re-evaluated by a direct transcription); beliefs follow Eq. 3."""
+    prob = synth.ising_grid(8, 1.0, seed=21)
+    eps = 1e-6
+    res = orc.run(prob, schedule, parallelism=par, eps=eps, max_rounds=20000, seed=3)
+    msg = res["messages"]
+    assert np.abs(msg.sum(axis=1) - 1.0).max() < 1e-12
+    assert res["converged"]
+    worst = max(np.abs(_exact.message_eq2(prob, msg, e) - msg[e]).max() for e in range(prob.m))
+    assert worst < eps
+    assert np.abs(res["beliefs"] - _exact.beliefs_eq3(prob, msg)).max() < 1e-14
+    assert np.all(res["beliefs"] >= 0) and np.allclose(res["beliefs"].sum(axis=1), 1.0)
+
+
+# --------------------------------------------------------------------------- schedules
+def test_rbp_full_frontier_equals_lbp(orc):
+    prob = synth.ising_grid(9, 1.5, seed=8)
+    a = orc.run(prob, "lbp", eps=1e-6, max_rounds=300)
+    b = orc.run(prob, "rbp", parallelism=1.0, eps=1e-6, max_rounds=300)
+    assert a["rounds"] == b["rounds"] and a["converged"] == b["converged"]
+    assert np.array_equal(a["beliefs"], b["beliefs"])
+
+
+def test_rs_all_roots_equals_lbp(orc):
+    """With every vertex a root, the splash is one simultaneous sub-step over all
+    out-messages: exactly an LBP round."""
+    prob = synth.ising_grid(7, 1.5, seed=9)
+    a = orc.run(prob, "lbp", eps=1e-6, max_rounds=300)
+    b = orc.run(prob, "rs", parallelism=1.0, rs_roots_mode=1, eps=1e-6, max_rounds=300)
+    assert a["rounds"] == b["rounds"]
+    assert np.array_equal(a["beliefs"], b["beliefs"])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_rbp_k1_equals_serial_heap_rbp(orc, seed):
+    """RBP with a frontier of one message is serial residual BP driven by a
+    priority queue (the paper's SRBP comparator)."""
+    prob = synth.ising_grid(4, 1.5, seed=seed)
+    eps = 1e-8
+    res = orc.run(prob, "rbp", parallelism=1e-9, eps=eps, max_rounds=4000)
+    upd, conv, msg = _exact.serial_rbp(prob, eps, 4000)
+    assert res["converged"] == conv
+    assert res["rounds"] == upd
+    assert np.abs(res["messages"] - msg).max() < 1e-12
+
+
+def test_rnbp_full_p_commits_exactly_unconverged(orc):
+    """LowP = HighP = 1: the frontier of every round is exactly {r >= eps}."""
+    prob = synth.ising_grid(6, 2.0, seed=2)
+    eps = 1e-3
+    res = orc.run(prob, "rnbp", parallelism=1.0, high_p=1.0, eps=eps, max_rounds=3, trace_cap=3)
+    msg = np.full((prob.m, 2), 0.5)
+    for t in range(res["rounds"]):
+        cand = np.array([_exact.message_eq2(prob, msg, e) for e in range(prob.m)])
+        r = np.abs(cand - msg).max(axis=1)
+        bits = np.unpackbits(res["trace"][t].view(np.uint8), bitorder="little")[:prob.m]
+        assert np.array_equal(bits.astype(bool), r >= eps)
+        msg[r >= eps] = cand[r >= eps]
+
+
+def test_rnbp_edge_ratio_switch(orc):
+    """p follows EdgeRatio: replay the frontier sizes from the trace with the
+    Philox stream and check LowP is used exactly when N_t / N_{t-1} > 0.9."""
+    prob = synth.ising_grid(10, 2.5, seed=6)
+    eps, low = 1e-4, 0.3
+    T = 40
+    res = orc.run(prob, "rnbp", parallelism=low, eps=eps, max_rounds=T, seed=99, trace_cap=T)
+    msg = np.full((prob.m, 2), 0.5)
+    n_prev = None
+    used_low = 0
+    for t in range(1, res["rounds"] + 1):
+        cand = np.array([_exact.message_eq2(prob, msg, e) for e in range(prob.m)])
+        r = np.abs(cand - msg).max(axis=1)
+        n_t = int((r >= eps).sum())
+        p = 1.0 if t == 1 else (low if n_t / n_prev > 0.9 else 1.0)
+        sel = np.zeros(prob.m, bool)
+        for e in np.nonzero(r >= eps)[0]:
+            u = int(orc.philox4x32_10([e, t, 0, 0], [99, 0])[0])
+            sel[e] = p >= 1.0 or u < int(p * 2 ** 32)
+        bits = np.unpackbits(res["trace"][t - 1].view(np.uint8), bitorder="little")[:prob.m]
+        assert np.array_equal(bits.astype(bool), sel), t
+        used_low += p < 1
+        msg[sel] = cand[sel]
+        n_prev = n_t
+    assert used_low > 0
+
+
+# --------------------------------------------------------------------------- selection
+def test_top_k_matches_sort(orc):
+    rng = np.random.default_rng(0)
+    key = np.round(rng.random(5000), 2)        # many ties
+    for k in (1, 7, 100, 4999, 5000):
+        chosen = orc.top_k(key, k)
+        order = np.lexsort((np.arange(key.size), -key))
+        expect = np.zeros(key.size, bool)
+        expect[order[:k]] = True
+        assert np.array_equal(chosen, expect)
+
+
+def test_splash_levels_textbook_bfs(orc):
+    prob = synth.ising_grid(15, 1.0, seed=0)
+    rng = np.random.default_rng(1)
+    roots = np.zeros(prob.n, np.uint8)
+    roots[rng.choice(prob.n, 6, replace=False)] = 1
+    A = scipy.sparse.csr_matrix((np.ones(prob.m), prob.col, prob.row_ptr), shape=(prob.n, prob.n))
+    d = scipy.sparse.csgraph.shortest_path(A, unweighted=True, indices=np.nonzero(roots)[0]).min(axis=0)
+    for h in (0, 1, 2, 3):
+        lv = orc.splash_levels(prob, roots, h)
+        expect = np.where(d <= h, d, -1).astype(np.int32)
+        assert np.array_equal(lv, expect)
+
+
+def test_trace_follow_reproduces_run(orc):
+    """Following its own recorded frontiers, the oracle lands on the same state."""
+    prob = synth.ising_grid(8, 2.0, seed=5)
+    for sched, par in (("rnbp", 0.4), ("rbp", 0.05), ("rs", 0.02)):
+        a = orc.run(prob, sched, parallelism=par, eps=1e-5, max_rounds=60, seed=1, trace_cap=60)
+        b = orc.run(prob, sched, eps=1e-5, trace_in=a["trace"], trace_rounds=a["rounds"])
+        assert b["rounds"] == a["rounds"]
+        assert np.array_equal(a["beliefs"], b["beliefs"])
+        assert a["committed_updates"] == b["committed_updates"]
