@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of frontier-scheduled loopy BP on one GB300 (or N, one rank per GPU).
+
+Workload (default): binary Ising grids 100x100, lambda ~ U[-1, 1],
+beta ~ U[-2.5, 2.5], 50 seeds held as one batch of 50 independent graphs, FP32
+log-domain messages, eps = 1e-4. One step runs the whole hot path once over
+the batch: LBP, RnBP (LowP 0.5), RBP (p 0.1) and Residual Splash (p 0.1, h 2),
+each to convergence or its round cap (LBP 1000, RnBP ceil(1000/LowP),
+RBP/RS ceil(1000/p)), beliefs included.
+
+Metric: committed message updates per second (messages written by frontier
+commits) over the timed steps, with the per-schedule converged fraction and
+batch time-to-convergence reported beside it. The message-update kernel's
+roofline is taken from CUDA events recorded inside the captured round graph.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (the method has no other reference implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "ising100x100_b2.5_50seeds": dict(
+        side=100, beta_max=2.5, lam_max=1.0, n_seeds=50, eps=1e-4, dtype="f32",
+        schedules=[("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.1), ("rs", 0.1)]),
+}
+DEFAULT_WORKLOAD = "ising100x100_b2.5_50seeds"
+L2_FLUSH_BYTES = 512 << 20          # > 126 MB of L2
+# algorithmic bytes per evaluated message / per processed vertex of the
+# full-evaluation kernel (binary Ising, FP32 messages): rev, incoming message,
+# exp(-2 beta), old message, new message (+ residual for the frontier modes);
+# per vertex row_ptr, unary log-odds, graph id.
+BYTES_PER_MSG = {"lbp": 20, "rnbp": 24, "rbp": 24, "rs": 24}
+BYTES_PER_VERTEX = 12
+
+
+def round_cap(sched: str, p: float) -> int:
+    """Round caps where the configuration is silent: LBP 1000, RnBP ceil(1000/LowP),
+    RBP/RS ceil(1000/p) (about 1000 sweeps' worth of commits)."""
+    if sched == "lbp":
+        return 1000
+    return int(np.ceil(1000.0 / p))
+
+
+def make_batch(wl, rank: int):
+    from paper_1909_11469_gb300 import synth
+    seeds = range(rank * wl["n_seeds"], (rank + 1) * wl["n_seeds"])
+    return synth.ising_grid_batch(wl["side"], wl["beta_max"], seeds, wl["lam_max"])
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(wl, budget_rounds: int, seed: int = 0):
+    """The FP64 oracle on one seed of the workload, each schedule capped at
+    budget_rounds rounds. Returns (committed updates, seconds)."""
+    import oracle
+    from paper_1909_11469_gb300 import synth
+    prob = synth.ising_grid(wl["side"], wl["beta_max"], seed, wl["lam_max"])
+    committed, t = 0, 0.0
+    for sched, p in wl["schedules"]:
+        t0 = time.perf_counter()
+        r = oracle.run(prob, sched, parallelism=p, eps=wl["eps"],
+                       max_rounds=min(budget_rounds, round_cap(sched, p)), seed=seed)
+        t += time.perf_counter() - t0
+        committed += r["committed_updates"]
+    return committed, t
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    rounds = 60
+    for _ in range(args.warmup):
+        oracle_sample(wl, rounds)
+    committed, secs = 0, 0.0
+    for _ in range(args.steps):
+        c, t = oracle_sample(wl, rounds)
+        committed += c
+        secs += t
+    value = committed / secs
+    sample = (f"one {wl['side']}x{wl['side']} seed per step, each schedule capped at "
+              f"{rounds} rounds, FP64 oracle, single thread")
+    line = {
+        "metric": "message updates/sec", "value": value, "unit": "message updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "message updates/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "message updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_1909_11469_gb300 import bp
+
+    prob = make_batch(wl, rank)
+    stream = torch.cuda.current_stream()
+    g = bp.Graph(prob)
+    G = prob.n_graphs
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def opts(**kw):
+        return bp.bp_default_options(msg_dtype=wl["dtype"], cuda_stream=stream.cuda_stream,
+                                     graph_id_base=rank * G, **kw)
+
+    def one_step(profile: int):
+        out = []
+        for sched, p in wl["schedules"]:
+            st = bp.bp_run(g.handle, sched, p, wl["eps"], round_cap(sched, p), opts(profile=profile))
+            out.append((sched, p, st, bp.bp_get_profile(g.handle), bp.bp_get_graph_stats(g.handle)))
+        return out
+
+    for _ in range(max(args.warmup, 0)):
+        one_step(1)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    results = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()                     # L2 flush between timed steps (outside the events)
+        starts[i].record(stream)
+        results.append(one_step(1))
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    committed = sum(st["committed_updates"] for step in results for (_, _, st, _, _) in step)
+    evals = sum(st["candidate_evals"] for step in results for (_, _, st, _, _) in step)
+    launches = sum(pr["kernel_launches"] for step in results for (_, _, _, pr, _) in step)
+    if world > 1:
+        t = torch.tensor([committed, evals, launches], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t)
+        committed, evals, launches = (int(x) for x in t.tolist())
+    value = committed / (total_ms / 1e3)
+
+    # roofline of the message-update (full evaluation) kernel
+    alg_bytes, eval_ms, eval_launches = 0.0, 0.0, 0
+    phase = {"eval_ms": 0.0, "decide_ms": 0.0, "frontier_ms": 0.0}
+    per_sched = {}
+    for step in results:
+        for sched, p, st, pr, gst in step:
+            alg_bytes += BYTES_PER_MSG[sched] * pr["full_evals"] + BYTES_PER_VERTEX * pr["active_vertices"]
+            eval_ms += pr["eval_ms"]
+            eval_launches += pr["eval_launches"]
+            for k in phase:
+                phase[k] += pr[k]
+            key = f"{sched}_p{p}"
+            d = per_sched.setdefault(key, {"ms": [], "converged_fraction": None, "median_rounds": None,
+                                           "committed_updates": 0})
+            d["ms"].append(st["device_ms"])
+            d["committed_updates"] += st["committed_updates"]
+            d["converged_fraction"] = float(np.mean([x["converged"] for x in gst]))
+            d["median_rounds"] = float(np.median([x["rounds"] for x in gst]))
+    for d in per_sched.values():
+        d["batch_ms"] = float(np.median(d.pop("ms")))
+        d["committed_updates"] //= args.steps
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
+    roofline = {"bound": "hbm", "kernel": "k_eval_bin<float> (Eq. 2 + Eq. 4 + reduction)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "launches": eval_launches,
+                "bytes_per_launch": alg_bytes / max(eval_launches, 1),
+                "avg_launch_us": 1e3 * eval_ms / max(eval_launches, 1)}
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        unary_h = torch.from_numpy(prob.unary_log).pin_memory()
+        pair_h = torch.from_numpy(prob.pair_log).pin_memory()
+        bel_h = torch.empty((prob.n, 2), dtype=torch.float64).pin_memory()
+        e2e_committed, e2e_s = 0, 0.0
+        for it in range(args.steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bp.bp_set_potentials(g.handle, unary_h, prob.pair_kind, pair_h)
+            c = 0
+            for sched, p in wl["schedules"]:
+                st = bp.bp_run(g.handle, sched, p, wl["eps"], round_cap(sched, p), opts())
+                bp.bp_get_beliefs(g.handle, bel_h)
+                c += st["committed_updates"]
+            dt = time.perf_counter() - t0
+            if it > 0:                      # first pass is a warm-up
+                e2e_committed += c
+                e2e_s += dt
+        e2e = {"value": e2e_committed / e2e_s, "unit": "message updates/s",
+               "h2d_bytes_per_step": int(prob.unary_log.nbytes + prob.pair_log.nbytes),
+               "d2h_bytes_per_step": int(bel_h.numel() * 8 * len(wl["schedules"]))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c, t = oracle_sample(wl, 300)
+        cpu = {"value": c / t, "unit": "message updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"seed 0 of the workload, each schedule capped at 300 rounds "
+                         f"({t:.1f} s of FP64 oracle, single thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": "message updates/sec", "value": value, "unit": "message updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+            "config": {"workload": args.workload, "graphs_per_gpu": G,
+                       "vertices_per_graph": wl["side"] ** 2, "messages_per_graph": int(prob.m // G),
+                       "eps": wl["eps"], "schedules": [f"{s}:{p}" for s, p in wl["schedules"]],
+                       "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"dp{world}" if world > 1 else "single"},
+            "candidate_evals_per_s": evals / (total_ms / 1e3),
+            "schedules": per_sched,
+            "phase_ms_per_step": {k: v / args.steps for k, v in phase.items()},
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

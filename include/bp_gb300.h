@@ -1,0 +1,208 @@
+/*
+ * bp_gb300.h - C ABI of the GB300 (sm_103a) frontier-scheduled loopy belief
+ * propagation library (libbp_gb300.so).
+ *
+ * The library runs sum-product belief propagation on discrete pairwise Markov
+ * random fields (Section II-A, Eq. 1) with the frontier loop of Algorithm 1:
+ * every round it evaluates candidate messages (Eq. 2) and their residuals
+ * (Eq. 4), tests eps-convergence, selects a frontier and commits it. Four
+ * frontier generators are provided: synchronous LBP (Section II-B, III-A),
+ * top-k Residual BP (Section III-A, III-D), Residual Splash (Section II-B, III-A)
+ * and Randomized BP (Section IV-A). Beliefs follow Eq. 3.
+ *
+ * Conventions shared by every entry point
+ *  - All pointers are HOST pointers unless stated otherwise; the library copies
+ *    what it needs to the GPU, so the caller keeps ownership of every input and
+ *    provides every output buffer.
+ *  - Return value: BP_OK (0) or a negative bp_status code; bp_last_error()
+ *    returns a message describing the most recent failure of the calling thread.
+ *  - A handle is not thread-safe: use one handle per host thread.
+ *  - Graph layout: CSR of directed edges. Directed edge e = (i -> j) is stored in
+ *    row i (row_ptr[i] <= e < row_ptr[i+1]) with col[e] = j; rev[e] is the id of
+ *    the opposite edge (j -> i). Both directions of every undirected edge must be
+ *    present; self-loops are rejected.
+ *  - Non-convergence within max_rounds is not an error: the run's stats say
+ *    converged = 0 and the beliefs come from the last committed state.
+ */
+#ifndef BP_GB300_H
+#define BP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bp_graph bp_graph;
+
+typedef enum {
+    BP_OK = 0,
+    BP_ERR_INVALID_ARG = -1,   /* a NULL pointer, a size or a parameter out of range */
+    BP_ERR_BAD_GRAPH = -2,     /* CSR not monotone, col out of range, rev not an involution,
+                                  col[rev[e]] != source(e), self-loop, or an edge that
+                                  leaves its graph in a batch */
+    BP_ERR_NO_POTENTIALS = -3, /* bp_run before bp_set_potentials */
+    BP_ERR_NONFINITE = -4,     /* NaN/Inf potential, or an asymmetric pairwise table */
+    BP_ERR_CUDA = -5,          /* a CUDA runtime call failed (see bp_last_error) */
+    BP_ERR_TIMEOUT = -6,       /* the wall-clock budget of bp_run ran out */
+    BP_ERR_OOM = -7,           /* device or host allocation failed */
+    BP_ERR_UNSUPPORTED = -8,   /* combination not implemented (e.g. k > 32) */
+    BP_ERR_NO_RESULT = -9      /* results requested before any bp_run */
+} bp_status;
+
+/* Frontier generators (Algorithm 1, GenerateFrontier). */
+typedef enum {
+    BP_LBP = 0,   /* every message, every round (Section II-B) */
+    BP_RBP = 1,   /* top-k messages by residual, k = clamp(ceil(p*M), 1, M) (Section III-A) */
+    BP_RS = 2,    /* top-k vertices by vertex residual + depth-h splash (Section II-B) */
+    BP_RNBP = 3   /* residual >= eps, then a Philox Bernoulli(p) filter (Section IV-A) */
+} bp_schedule;
+
+/* Storage type of the log-domain messages (arithmetic is FP32, or FP64 for BP_F64). */
+typedef enum { BP_F64 = 0, BP_F32 = 1, BP_BF16 = 2 } bp_msg_dtype;
+
+/* Pairwise potential layouts, as natural logs theta = log psi (Eq. 1). */
+typedef enum {
+    BP_PAIR_ISING_BETA = 0, /* k = 2; beta per directed edge [M]:
+                               theta(x_i, x_j) = beta * s(x_i) * s(x_j), s(0) = -1, s(1) = +1;
+                               beta[rev[e]] must equal beta[e] */
+    BP_PAIR_TABLE = 1,      /* [M * k * k], entry (e, a, b) = theta(x_src = a, x_dst = b);
+                               table(rev[e]) must be the transpose of table(e) */
+    BP_PAIR_SHARED = 2      /* one symmetric [k * k] table for every edge (Potts-like) */
+} bp_pair_kind;
+
+/* Per-run (or per-graph) statistics. */
+typedef struct {
+    int32_t converged;          /* 1 if max residual < eps at the final evaluation */
+    int32_t rounds;             /* committing rounds (Algorithm 1 loop iterations) */
+    int64_t committed_updates;  /* sum of frontier sizes (RS: messages updated in splashes) */
+    int64_t candidate_evals;    /* message evaluations (Eq. 2) performed */
+    double final_max_residual;  /* max residual at the final evaluation */
+    int64_t final_unconverged;  /* messages with residual >= eps at the final evaluation */
+    int32_t status;             /* BP_OK, or BP_ERR_TIMEOUT when stopped by the budget */
+    int32_t n_graphs;           /* graphs summarised by this record */
+    double device_ms;           /* device time of the whole bp_run call */
+} bp_run_stats;
+
+/* Options of bp_run; bp_default_options fills the defaults noted here. */
+typedef struct {
+    uint64_t seed;            /* Philox key for RnBP (default 0) */
+    double high_p;            /* RnBP HighP (default 1.0, Section IV-D) */
+    double ratio_threshold;   /* RnBP EdgeRatio switch (default 0.9, Section IV-A) */
+    int32_t splash_depth;     /* RS splash depth h (default 2, Section III-D) */
+    int32_t rs_roots_mode;    /* RS roots: 0 = clamp(ceil(p*M), 1, n) (default), 1 = ceil(p*n) */
+    int32_t msg_dtype;        /* bp_msg_dtype (default BP_F32) */
+    int32_t record_trace;     /* 1: record each round's frontier as a bitmask (default 0) */
+    int32_t trace_capacity;   /* rounds the trace can hold (default 0) */
+    int32_t rounds_per_launch;/* rounds per CUDA-graph replay between host polls (0 = auto) */
+    void *cuda_stream;        /* cudaStream_t to run on (NULL = the legacy default stream) */
+    double time_budget_ms;    /* wall-clock budget of bp_run, 0 = none */
+    uint32_t graph_id_base;   /* Philox graph id of graph 0 of the handle (default 0) */
+    int32_t kernel_variant;   /* 0 = automatic choice; others reserved for tuning */
+    int32_t profile;          /* 1: time every round's phases with CUDA events (default 0) */
+} bp_options;
+
+/* Phase timings and launch counts of the last bp_run. The timings are filled
+ * only when the run had profile = 1: CUDA events recorded inside the captured
+ * round graph on the run's stream bracket the evaluation kernel (Eq. 2 + Eq. 4
+ * + convergence reduction), the per-graph decision, and the frontier work
+ * (selection, splash, commit); rounds after every graph had stopped are left
+ * out. Profiling adds event nodes between kernels, so a profiled run is slightly
+ * slower than an unprofiled one. */
+typedef struct {
+    int64_t kernel_launches;   /* kernels launched by bp_run (graph nodes replayed + direct) */
+    int64_t eval_launches;     /* timed full-evaluation launches (profile = 1) */
+    int64_t full_evals;        /* messages evaluated by those launches */
+    int64_t active_vertices;   /* vertices processed by those launches */
+    double eval_ms;            /* summed duration of those launches */
+    double decide_ms;          /* summed duration of the per-graph decisions */
+    double frontier_ms;        /* summed duration of selection / splash / commit */
+} bp_profile;
+
+/* Fills *opt with the defaults listed above. */
+void bp_default_options(bp_options *opt);
+
+/*
+ * Creates a handle for one graph. n_states = k (uniform over vertices,
+ * 2 <= k <= 32). row_ptr has n_vars + 1 entries (row_ptr[0] = 0,
+ * row_ptr[n_vars] = n_dir_edges), col and rev have n_dir_edges entries.
+ * The CSR is validated (BP_ERR_BAD_GRAPH) and copied to the device.
+ * n_dir_edges must be below 2^31. *out receives the handle.
+ */
+int bp_create_graph(int32_t n_vars, int32_t n_states, int64_t n_dir_edges,
+                    const int64_t *row_ptr, const int32_t *col, const int32_t *rev,
+                    bp_graph **out);
+
+/*
+ * Creates a handle for a batch of independent graphs given as one disjoint
+ * union: graph g owns vertices [graph_var_offsets[g], graph_var_offsets[g+1])
+ * and every edge of those rows, which must stay inside the graph. Each graph
+ * is tested for convergence, counts its rounds and stops on its own; graph g
+ * draws RnBP randomness with graph id graph_id_base + g.
+ */
+int bp_create_batch(int32_t n_graphs, const int64_t *graph_var_offsets, int32_t n_states,
+                    int64_t n_dir_edges, const int64_t *row_ptr, const int32_t *col,
+                    const int32_t *rev, bp_graph **out);
+
+/*
+ * Sets the log-potentials of Eq. 1. unary_log is [n_vars * k] (row = vertex);
+ * pair_log is laid out per bp_pair_kind (see above). Inputs are validated for
+ * finiteness and for the symmetry the kind requires (BP_ERR_NONFINITE) and
+ * copied to the device; any previous result of the handle is discarded.
+ */
+int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind,
+                      const float *pair_log);
+
+/*
+ * Runs Algorithm 1 from uniform messages (Section II-A) until every graph of
+ * the handle has max residual < eps (converged) or has committed max_rounds
+ * rounds. parallelism = p for RBP and RS, LowP for RnBP (HighP in opt),
+ * ignored for LBP; 0 < parallelism, eps > 0, max_rounds >= 0. opt may be NULL
+ * (defaults). stats (nullable) receives the whole-handle summary: converged =
+ * 1 only if all graphs converged, rounds = the largest round count, counters
+ * summed. On return the beliefs (Eq. 3) are ready for bp_get_beliefs.
+ */
+int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_t max_rounds,
+           const bp_options *opt, bp_run_stats *stats);
+
+/* Copies the beliefs of the last bp_run, [n_vars * k] float64, rows summing to 1. */
+int bp_get_beliefs(const bp_graph *g, double *out);
+
+/* Copies the final messages of the last bp_run in the probability domain,
+ * [n_dir_edges * k] float64 (row e = message on directed edge e). */
+int bp_get_messages(const bp_graph *g, double *out);
+
+/* Copies per-graph statistics of the last bp_run into out[n_graphs]. */
+int bp_get_graph_stats(const bp_graph *g, bp_run_stats *out);
+
+/*
+ * Copies the recorded frontiers of the last bp_run (record_trace = 1). Round t
+ * (1-based) occupies words [(t-1) * W, t * W) with W = ceil(count / 32), count =
+ * n_dir_edges (LBP, RBP, RnBP: bit e = message e committed) or n_vars (RS: bit
+ * v = vertex v chosen as splash root); bit b of a word is (word >> b) & 1.
+ * *rounds_out receives the number of recorded rounds; fails with
+ * BP_ERR_INVALID_ARG when capacity_words is too small.
+ */
+int bp_get_trace(const bp_graph *g, uint32_t *out, int64_t capacity_words, int32_t *rounds_out);
+
+/* Copies the phase profile of the last bp_run (see bp_profile). */
+int bp_get_profile(const bp_graph *g, bp_profile *out);
+
+/* Sizes of a handle (any pointer may be NULL). */
+int bp_graph_info(const bp_graph *g, int32_t *n_vars, int32_t *n_states, int64_t *n_dir_edges,
+                  int32_t *n_graphs);
+
+/* Frees the handle and its device memory. NULL is ignored. */
+void bp_destroy_graph(bp_graph *g);
+
+/* Static description of a status code. */
+const char *bp_status_string(int status);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *bp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BP_GB300_H */

@@ -1,0 +1,902 @@
+// Runtime and C ABI of libbp_gb300: graph validation and upload, potentials,
+// the CUDA-graph-captured round loop of Algorithm 1, beliefs and statistics.
+#include "bp_gb300.h"
+#include "bp_internal.cuh"
+#include "bp_launch.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace bpg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();   // clear a sticky-free error so the next call starts clean
+    if (e == cudaErrorMemoryAllocation)
+        return fail(BP_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    return fail(BP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define BP_CK(call)                                 \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess)                      \
+            return cuda_fail(_e, #call);            \
+    } while (0)
+
+template <typename T> int dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    return BP_OK;
+}
+
+template <typename T> void dfree(T *&p)
+{
+    if (p)
+        cudaFree((void *)p);
+    p = nullptr;
+}
+
+struct CachedGraph {
+    RunParams rp;
+    int dtype, rounds, kp, profile;
+    int64_t kernels;                    // kernel nodes in the graph
+    cudaGraphExec_t exec;
+    std::vector<cudaEvent_t> events;    // profile: 4 per round
+};
+
+void destroy_cached(CachedGraph &c)
+{
+    cudaGraphExecDestroy(c.exec);
+    for (auto ev : c.events)
+        cudaEventDestroy(ev);
+    c.events.clear();
+}
+
+}  // namespace
+
+struct bp_graph {
+    int32_t n = 0, k = 0, G = 0;
+    int64_t M = 0;
+    int dev = 0;
+    int kp = 32;
+    std::vector<int32_t> h_rev, h_gv_off, h_ge_off;
+    // structure
+    int32_t *d_row_ptr = nullptr, *d_col = nullptr, *d_rev = nullptr, *d_gid = nullptr;
+    int32_t *d_gv_off = nullptr, *d_ge_off = nullptr;
+    // potentials
+    int pair_kind = -1;
+    bool has_pot = false;
+    float *d_unary = nullptr, *d_udiff32 = nullptr, *d_q32 = nullptr, *d_pair = nullptr,
+          *d_psi_shared = nullptr;
+    double *d_udiff64 = nullptr, *d_q64 = nullptr;
+    // run buffers
+    int buf_dtype = -1;
+    void *d_msg[2] = {nullptr, nullptr};
+    void *d_resid = nullptr, *d_vres = nullptr;
+    int8_t *d_level = nullptr;
+    GState *d_gs = nullptr;
+    unsigned long long *d_red_max = nullptr;
+    unsigned int *d_red_cnt = nullptr;
+    int32_t *d_running = nullptr;
+    uint32_t *d_trace = nullptr;
+    size_t trace_alloc_words = 0;
+    double *d_beliefs = nullptr;
+    int32_t *h_running = nullptr;   // pinned
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<CachedGraph> cache;
+    // last result
+    bool has_result = false;
+    int res_dtype = 0;
+    int res_schedule = 0;
+    int32_t trace_rounds = 0;
+    int32_t trace_words = 0;
+    std::vector<bp_run_stats> last_stats;
+    bp_profile last_profile;
+};
+
+namespace {
+
+void clear_cache(bp_graph *g)
+{
+    for (auto &c : g->cache)
+        destroy_cached(c);
+    g->cache.clear();
+}
+
+void free_run_buffers(bp_graph *g)
+{
+    clear_cache(g);
+    dfree(g->d_msg[0]);
+    dfree(g->d_msg[1]);
+    dfree(g->d_resid);
+    dfree(g->d_vres);
+    g->buf_dtype = -1;
+}
+
+DevGraph dev_graph(const bp_graph *g)
+{
+    DevGraph d;
+    d.n = g->n;
+    d.k = g->k;
+    d.G = g->G;
+    d.M = (int32_t)g->M;
+    d.row_ptr = g->d_row_ptr;
+    d.col = g->d_col;
+    d.rev = g->d_rev;
+    d.gid = g->d_gid;
+    d.gv_off = g->d_gv_off;
+    d.ge_off = g->d_ge_off;
+    d.pair_kind = g->pair_kind;
+    d.unary = g->d_unary;
+    d.udiff32 = g->d_udiff32;
+    d.udiff64 = g->d_udiff64;
+    d.q32 = g->d_q32;
+    d.q64 = g->d_q64;
+    d.pair = g->d_pair;
+    d.psi_shared = g->d_psi_shared;
+    return d;
+}
+
+DevRun dev_run(const bp_graph *g)
+{
+    DevRun r;
+    r.msg[0] = g->d_msg[0];
+    r.msg[1] = g->d_msg[1];
+    r.resid = g->d_resid;
+    r.vres = g->d_vres;
+    r.level = g->d_level;
+    r.gs = g->d_gs;
+    r.red_max = g->d_red_max;
+    r.red_cnt = g->d_red_cnt;
+    r.n_running = g->d_running;
+    r.trace = g->d_trace;
+    r.beliefs = g->d_beliefs;
+    return r;
+}
+
+size_t dtype_size(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
+
+int ensure_msg_buffers(bp_graph *g, int dtype)
+{
+    if (g->buf_dtype == dtype)
+        return BP_OK;
+    free_run_buffers(g);
+    size_t elems = (size_t)g->M * (size_t)g->k;
+    size_t es = dtype_size(dtype);
+    size_t rs = dtype == DT_F64 ? 8 : 4;
+    int rc;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dalloc((char **)&g->d_msg[b], elems * es)) != BP_OK)
+            return rc;
+    }
+    if ((rc = dalloc((char **)&g->d_resid, (size_t)g->M * rs)) != BP_OK)
+        return rc;
+    if ((rc = dalloc((char **)&g->d_vres, (size_t)g->n * rs)) != BP_OK)
+        return rc;
+    g->buf_dtype = dtype;
+    return BP_OK;
+}
+
+int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32_t n, int32_t k, int64_t M,
+                        const int64_t *row_ptr, const int32_t *col, const int32_t *rev)
+{
+    if (n < 0 || M < 0 || n_graphs < 1)
+        return fail(BP_ERR_INVALID_ARG, "negative size or no graph");
+    if (k < 2 || k > 32)
+        return fail(BP_ERR_UNSUPPORTED, "n_states must be in [2, 32]");
+    if (M >= ((int64_t)1 << 31) - 1 || (int64_t)n * k >= ((int64_t)1 << 31))
+        return fail(BP_ERR_UNSUPPORTED, "graph too large for 32-bit device indexing");
+    if (!row_ptr || (M > 0 && (!col || !rev)))
+        return fail(BP_ERR_INVALID_ARG, "NULL graph array");
+    if (row_ptr[0] != 0 || row_ptr[n] != M)
+        return fail(BP_ERR_BAD_GRAPH, "row_ptr must start at 0 and end at n_dir_edges");
+    std::vector<int32_t> src((size_t)M);
+    for (int32_t i = 0; i < n; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i] || row_ptr[i + 1] > M)
+            return fail(BP_ERR_BAD_GRAPH, "row_ptr not monotone at vertex " + std::to_string(i));
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            src[(size_t)e] = i;
+    }
+    for (int64_t e = 0; e < M; ++e) {
+        int32_t j = col[e], r = rev[e];
+        if (j < 0 || j >= n)
+            return fail(BP_ERR_BAD_GRAPH, "col out of range at edge " + std::to_string(e));
+        if (j == src[(size_t)e])
+            return fail(BP_ERR_BAD_GRAPH, "self-loop at edge " + std::to_string(e));
+        if (r < 0 || r >= M || r == e)
+            return fail(BP_ERR_BAD_GRAPH, "rev out of range at edge " + std::to_string(e));
+        if (rev[r] != e)
+            return fail(BP_ERR_BAD_GRAPH, "rev is not an involution at edge " + std::to_string(e));
+        if (col[r] != src[(size_t)e] || src[(size_t)r] != j)
+            return fail(BP_ERR_BAD_GRAPH, "rev[e] is not the opposite edge at edge " + std::to_string(e));
+    }
+    std::vector<int32_t> gv((size_t)n_graphs + 1), ge((size_t)n_graphs + 1), gid((size_t)std::max(n, 1));
+    if (gvo) {
+        if (gvo[0] != 0 || gvo[n_graphs] != n)
+            return fail(BP_ERR_BAD_GRAPH, "graph_var_offsets must start at 0 and end at n_vars");
+        for (int32_t q = 0; q < n_graphs; ++q)
+            if (gvo[q + 1] < gvo[q])
+                return fail(BP_ERR_BAD_GRAPH, "graph_var_offsets not monotone");
+        for (int32_t q = 0; q <= n_graphs; ++q)
+            gv[(size_t)q] = (int32_t)gvo[q];
+    } else {
+        gv[0] = 0;
+        gv[1] = n;
+    }
+    for (int32_t q = 0; q <= n_graphs; ++q)
+        ge[(size_t)q] = (int32_t)row_ptr[gv[(size_t)q]];
+    for (int32_t q = 0; q < n_graphs; ++q) {
+        for (int32_t i = gv[(size_t)q]; i < gv[(size_t)q + 1]; ++i) {
+            gid[(size_t)i] = q;
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                if (col[e] < gv[(size_t)q] || col[e] >= gv[(size_t)q + 1])
+                    return fail(BP_ERR_BAD_GRAPH, "edge " + std::to_string(e) + " leaves graph " +
+                                                      std::to_string(q));
+        }
+    }
+    // Everything above is host-side validation; device work starts here.
+    cudaGetDevice(&g->dev);
+    g->n = n;
+    g->k = k;
+    g->M = M;
+    g->G = n_graphs;
+    g->kp = k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32));
+    g->h_rev.assign(rev, rev + M);
+    g->h_gv_off = gv;
+    g->h_ge_off = ge;
+    std::vector<int32_t> rp32((size_t)n + 1);
+    for (int32_t i = 0; i <= n; ++i)
+        rp32[(size_t)i] = (int32_t)row_ptr[i];
+    int rc;
+    if ((rc = dalloc(&g->d_row_ptr, (size_t)n + 1)) || (rc = dalloc(&g->d_col, (size_t)M)) ||
+        (rc = dalloc(&g->d_rev, (size_t)M)) || (rc = dalloc(&g->d_gid, (size_t)std::max(n, 1))) ||
+        (rc = dalloc(&g->d_gv_off, (size_t)n_graphs + 1)) || (rc = dalloc(&g->d_ge_off, (size_t)n_graphs + 1)))
+        return rc;
+    BP_CK(cudaMemcpy(g->d_row_ptr, rp32.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice));
+    if (M) {
+        BP_CK(cudaMemcpy(g->d_col, col, sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice));
+        BP_CK(cudaMemcpy(g->d_rev, rev, sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice));
+    }
+    BP_CK(cudaMemcpy(g->d_gid, gid.data(), sizeof(int32_t) * gid.size(), cudaMemcpyHostToDevice));
+    BP_CK(cudaMemcpy(g->d_gv_off, gv.data(), sizeof(int32_t) * gv.size(), cudaMemcpyHostToDevice));
+    BP_CK(cudaMemcpy(g->d_ge_off, ge.data(), sizeof(int32_t) * ge.size(), cudaMemcpyHostToDevice));
+    // per-graph state, reductions, beliefs
+    if ((rc = dalloc(&g->d_gs, (size_t)n_graphs)) || (rc = dalloc(&g->d_red_max, (size_t)n_graphs * NSUB)) ||
+        (rc = dalloc(&g->d_red_cnt, (size_t)n_graphs * NSUB)) || (rc = dalloc(&g->d_running, 1)) ||
+        (rc = dalloc(&g->d_level, (size_t)std::max(n, 1))) ||
+        (rc = dalloc(&g->d_beliefs, (size_t)n * (size_t)k)))
+        return rc;
+    BP_CK(cudaMallocHost((void **)&g->h_running, sizeof(int32_t)));
+    BP_CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    BP_CK(cudaEventCreate(&g->ev0));
+    BP_CK(cudaEventCreate(&g->ev1));
+    return BP_OK;
+}
+
+int create_common(int32_t n_graphs, const int64_t *gvo, int32_t n, int32_t k, int64_t M, const int64_t *row_ptr,
+                  const int32_t *col, const int32_t *rev, bp_graph **out)
+{
+    if (!out)
+        return fail(BP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    bp_graph *g = new (std::nothrow) bp_graph();
+    if (!g)
+        return fail(BP_ERR_OOM, "host allocation failed");
+    int rc = validate_and_upload(g, n_graphs, gvo, n, k, M, row_ptr, col, rev);
+    if (rc != BP_OK) {
+        std::string keep = g_last_error;
+        bp_destroy_graph(g);
+        g_last_error = keep;
+        return rc;
+    }
+    *out = g;
+    return BP_OK;
+}
+
+// Records one round (evaluation, decision, frontier work) on stream s and
+// returns the number of kernels it launched. ev (nullable) receives 4 events:
+// round start, after evaluation, after decision, round end.
+int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &dr, const RunParams &rp,
+                     cudaStream_t s, cudaEvent_t *ev)
+{
+    const bool any = dg.n > 0;
+    int64_t kernels = 0;
+    if (ev)
+        cudaEventRecord(ev[0], s);
+    launch_eval(dtype, dg, dr, rp, rp.schedule == SCHED_LBP ? MODE_LBP : MODE_CAND, 0, g->kp, s);
+    kernels += any;
+    if (ev)
+        cudaEventRecord(ev[1], s);
+    launch_decide(dg, dr, rp, s);
+    kernels += 1;
+    if (ev)
+        cudaEventRecord(ev[2], s);
+    switch (rp.schedule) {
+    case SCHED_LBP:
+        break;
+    case SCHED_RNBP:
+        launch_commit_rnbp(dtype, dg, dr, rp, s);
+        kernels += any;
+        break;
+    case SCHED_RBP:
+        launch_select_rbp(dtype, dg, dr, rp, s);
+        kernels += 1;
+        break;
+    default: {   // SCHED_RS
+        launch_select_rs(dtype, dg, dr, rp, s);
+        kernels += 1;
+        const int h = rp.splash_depth;
+        for (int d = 1; d <= h; ++d)
+            launch_bfs_level(dg, dr, d, s);
+        kernels += any ? h : 0;
+        for (int step = 0; step <= 2 * h; ++step) {
+            const int L = step <= h ? h - step : step - h;
+            launch_eval(dtype, dg, dr, rp, MODE_SPLASH, L, g->kp, s);
+            launch_splash_commit(dtype, dg, dr, L, s);
+            kernels += any ? 2 : 0;
+        }
+    }
+    }
+    if (ev)
+        cudaEventRecord(ev[3], s);
+    return kernels;
+}
+
+// Returns the instantiated graph of `rounds` rounds for these parameters,
+// capturing it on first use.
+int get_graph_exec(bp_graph *g, int dtype, const RunParams &rp, int rounds, int profile, CachedGraph **out)
+{
+    for (auto &c : g->cache) {
+        if (c.dtype == dtype && c.rounds == rounds && c.kp == g->kp && c.profile == profile &&
+            memcmp(&c.rp, &rp, sizeof(rp)) == 0) {
+            *out = &c;
+            return BP_OK;
+        }
+    }
+    if (g->cache.size() >= 24) {
+        destroy_cached(g->cache.front());
+        g->cache.erase(g->cache.begin());
+    }
+    CachedGraph c;
+    c.rp = rp;
+    c.dtype = dtype;
+    c.rounds = rounds;
+    c.kp = g->kp;
+    c.profile = profile;
+    c.kernels = 0;
+    if (profile) {
+        c.events.resize((size_t)rounds * 4);
+        for (auto &ev : c.events)
+            BP_CK(cudaEventCreate(&ev));
+    }
+    DevGraph dg = dev_graph(g);
+    DevRun dr = dev_run(g);
+    BP_CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < rounds; ++r)
+        c.kernels += record_round(g, dtype, dg, dr, rp, g->cap_stream, profile ? &c.events[(size_t)r * 4] : nullptr);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+    if (e != cudaSuccess) {
+        for (auto ev : c.events)
+            cudaEventDestroy(ev);
+        return cuda_fail(e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&c.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        for (auto ev : c.events)
+            cudaEventDestroy(ev);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    g->cache.push_back(c);
+    *out = &g->cache.back();
+    return BP_OK;
+}
+
+bool all_finite(const float *p, size_t n)
+{
+    for (size_t q = 0; q < n; ++q)
+        if (!std::isfinite(p[q]))
+            return false;
+    return true;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+void bp_default_options(bp_options *opt)
+{
+    if (!opt)
+        return;
+    memset(opt, 0, sizeof(*opt));
+    opt->seed = 0;
+    opt->high_p = 1.0;
+    opt->ratio_threshold = 0.9;
+    opt->splash_depth = 2;
+    opt->rs_roots_mode = 0;
+    opt->msg_dtype = BP_F32;
+    opt->record_trace = 0;
+    opt->trace_capacity = 0;
+    opt->rounds_per_launch = 0;
+    opt->cuda_stream = nullptr;
+    opt->time_budget_ms = 0.0;
+    opt->graph_id_base = 0;
+    opt->kernel_variant = 0;
+    opt->profile = 0;
+}
+
+int bp_create_graph(int32_t n_vars, int32_t n_states, int64_t n_dir_edges, const int64_t *row_ptr,
+                    const int32_t *col, const int32_t *rev, bp_graph **out)
+{
+    return create_common(1, nullptr, n_vars, n_states, n_dir_edges, row_ptr, col, rev, out);
+}
+
+int bp_create_batch(int32_t n_graphs, const int64_t *graph_var_offsets, int32_t n_states, int64_t n_dir_edges,
+                    const int64_t *row_ptr, const int32_t *col, const int32_t *rev, bp_graph **out)
+{
+    if (n_graphs < 1 || !graph_var_offsets)
+        return fail(BP_ERR_INVALID_ARG, "n_graphs < 1 or graph_var_offsets NULL");
+    int32_t n = (int32_t)graph_var_offsets[n_graphs];
+    if (graph_var_offsets[n_graphs] < 0 || graph_var_offsets[n_graphs] >= ((int64_t)1 << 31))
+        return fail(BP_ERR_INVALID_ARG, "bad vertex count");
+    return create_common(n_graphs, graph_var_offsets, n, n_states, n_dir_edges, row_ptr, col, rev, out);
+}
+
+int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, const float *pair_log)
+{
+    if (!g || !unary_log || (!pair_log && !(pair_kind == BP_PAIR_ISING_BETA && g->M == 0) &&
+                             !(pair_kind == BP_PAIR_TABLE && g->M == 0)))
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    BP_CK(cudaSetDevice(g->dev));
+    const int32_t n = g->n, k = g->k;
+    const int64_t M = g->M;
+    if (pair_kind < 0 || pair_kind > 2)
+        return fail(BP_ERR_INVALID_ARG, "unknown pair kind");
+    if (pair_kind == BP_PAIR_ISING_BETA && k != 2)
+        return fail(BP_ERR_INVALID_ARG, "Ising beta potentials need n_states = 2");
+    if (!all_finite(unary_log, (size_t)n * k))
+        return fail(BP_ERR_NONFINITE, "non-finite unary log-potential");
+    size_t plen = pair_kind == BP_PAIR_ISING_BETA ? (size_t)M
+                  : pair_kind == BP_PAIR_TABLE    ? (size_t)M * k * k
+                                                  : (size_t)k * k;
+    if (plen && !all_finite(pair_log, plen))
+        return fail(BP_ERR_NONFINITE, "non-finite pairwise log-potential");
+    if (pair_kind == BP_PAIR_ISING_BETA) {
+        for (int64_t e = 0; e < M; ++e)
+            if (pair_log[e] != pair_log[g->h_rev[(size_t)e]])
+                return fail(BP_ERR_NONFINITE, "beta[rev[e]] != beta[e] at edge " + std::to_string(e));
+    } else if (pair_kind == BP_PAIR_TABLE) {
+        for (int64_t e = 0; e < M; ++e) {
+            const float *a = pair_log + (size_t)e * k * k;
+            const float *b = pair_log + (size_t)g->h_rev[(size_t)e] * k * k;
+            for (int x = 0; x < k; ++x)
+                for (int y = 0; y < k; ++y)
+                    if (a[x * k + y] != b[y * k + x])
+                        return fail(BP_ERR_NONFINITE, "table(rev[e]) is not table(e) transposed at edge " +
+                                                          std::to_string(e));
+        }
+    } else {
+        for (int x = 0; x < k; ++x)
+            for (int y = 0; y < k; ++y)
+                if (pair_log[x * k + y] != pair_log[y * k + x])
+                    return fail(BP_ERR_NONFINITE, "shared pairwise table is not symmetric");
+    }
+    g->has_pot = false;
+    g->has_result = false;
+    dfree(g->d_unary);
+    dfree(g->d_udiff32);
+    dfree(g->d_udiff64);
+    dfree(g->d_q32);
+    dfree(g->d_q64);
+    dfree(g->d_pair);
+    dfree(g->d_psi_shared);
+    clear_cache(g);
+    int rc;
+    if ((rc = dalloc(&g->d_unary, (size_t)n * k)))
+        return rc;
+    BP_CK(cudaMemcpy(g->d_unary, unary_log, sizeof(float) * (size_t)n * k, cudaMemcpyHostToDevice));
+    std::vector<double> ud((size_t)n);
+    std::vector<float> ud32((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        ud[(size_t)i] = (double)unary_log[(size_t)i * k + 1] - (double)unary_log[(size_t)i * k];
+        ud32[(size_t)i] = (float)ud[(size_t)i];
+    }
+    if ((rc = dalloc(&g->d_udiff64, (size_t)n)) || (rc = dalloc(&g->d_udiff32, (size_t)n)))
+        return rc;
+    if (n) {
+        BP_CK(cudaMemcpy(g->d_udiff64, ud.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
+        BP_CK(cudaMemcpy(g->d_udiff32, ud32.data(), sizeof(float) * (size_t)n, cudaMemcpyHostToDevice));
+    }
+    if (pair_kind == BP_PAIR_ISING_BETA) {
+        std::vector<double> q64((size_t)M);
+        std::vector<float> q32((size_t)M);
+        for (int64_t e = 0; e < M; ++e) {
+            double q = std::exp(-2.0 * (double)pair_log[e]);
+            q64[(size_t)e] = std::min(std::max(q, 1e-300), 1e300);
+            q32[(size_t)e] = (float)std::min(std::max(q, 1e-30), 1e30);
+        }
+        if ((rc = dalloc(&g->d_q64, (size_t)M)) || (rc = dalloc(&g->d_q32, (size_t)M)))
+            return rc;
+        if (M) {
+            BP_CK(cudaMemcpy(g->d_q64, q64.data(), sizeof(double) * (size_t)M, cudaMemcpyHostToDevice));
+            BP_CK(cudaMemcpy(g->d_q32, q32.data(), sizeof(float) * (size_t)M, cudaMemcpyHostToDevice));
+        }
+    } else if (pair_kind == BP_PAIR_TABLE) {
+        if ((rc = dalloc(&g->d_pair, plen)))
+            return rc;
+        if (plen)
+            BP_CK(cudaMemcpy(g->d_pair, pair_log, sizeof(float) * plen, cudaMemcpyHostToDevice));
+    } else {
+        if ((rc = dalloc(&g->d_pair, plen)) || (rc = dalloc(&g->d_psi_shared, plen)))
+            return rc;
+        float mx = pair_log[0];
+        for (size_t q = 1; q < plen; ++q)
+            mx = std::max(mx, pair_log[q]);
+        std::vector<float> psi(plen);
+        for (size_t q = 0; q < plen; ++q)
+            psi[q] = (float)std::exp((double)pair_log[q] - (double)mx);
+        BP_CK(cudaMemcpy(g->d_pair, pair_log, sizeof(float) * plen, cudaMemcpyHostToDevice));
+        BP_CK(cudaMemcpy(g->d_psi_shared, psi.data(), sizeof(float) * plen, cudaMemcpyHostToDevice));
+    }
+    g->pair_kind = pair_kind;
+    g->has_pot = true;
+    return BP_OK;
+}
+
+int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_t max_rounds,
+           const bp_options *opt_in, bp_run_stats *stats)
+{
+    if (!g)
+        return fail(BP_ERR_INVALID_ARG, "NULL handle");
+    if (!g->has_pot)
+        return fail(BP_ERR_NO_POTENTIALS, "bp_set_potentials has not been called");
+    if (schedule < 0 || schedule > 3)
+        return fail(BP_ERR_INVALID_ARG, "unknown schedule");
+    if (!(eps > 0.0) || !std::isfinite(eps))
+        return fail(BP_ERR_INVALID_ARG, "eps must be positive and finite");
+    if (max_rounds < 0)
+        return fail(BP_ERR_INVALID_ARG, "max_rounds must be >= 0");
+    if (schedule != BP_LBP && (!(parallelism > 0.0) || !std::isfinite(parallelism)))
+        return fail(BP_ERR_INVALID_ARG, "parallelism must be positive and finite");
+    bp_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        bp_default_options(&opt);
+    if (opt.msg_dtype < 0 || opt.msg_dtype > 2)
+        return fail(BP_ERR_INVALID_ARG, "unknown msg_dtype");
+    if (!(opt.high_p >= 0.0) || !std::isfinite(opt.high_p) || !std::isfinite(opt.ratio_threshold))
+        return fail(BP_ERR_INVALID_ARG, "bad high_p or ratio_threshold");
+    if (opt.splash_depth < 0 || opt.splash_depth > 16)
+        return fail(BP_ERR_INVALID_ARG, "splash_depth must be in [0, 16]");
+    if (opt.record_trace && opt.trace_capacity < 0)
+        return fail(BP_ERR_INVALID_ARG, "negative trace_capacity");
+    BP_CK(cudaSetDevice(g->dev));
+    const int dtype = opt.msg_dtype;
+    int rc = ensure_msg_buffers(g, dtype);
+    if (rc != BP_OK)
+        return rc;
+
+    RunParams rp;
+    memset(&rp, 0, sizeof(rp));
+    rp.schedule = schedule;
+    rp.max_rounds = max_rounds;
+    rp.eps = eps;
+    rp.low_p = schedule == BP_LBP ? 1.0 : parallelism;
+    rp.high_p = opt.high_p;
+    rp.ratio_threshold = opt.ratio_threshold;
+    rp.seed = opt.seed;
+    rp.graph_id_base = opt.graph_id_base;
+    rp.splash_depth = opt.splash_depth;
+    rp.rs_roots_mode = opt.rs_roots_mode;
+    rp.record_trace = (opt.record_trace && opt.trace_capacity > 0 && schedule != BP_LBP) ? 1 : 0;
+    rp.trace_capacity = rp.record_trace ? opt.trace_capacity : 0;
+    const int64_t trace_count = schedule == BP_RS ? g->n : g->M;
+    rp.trace_words = (int32_t)((trace_count + 31) / 32);
+    if (rp.record_trace) {
+        size_t words = (size_t)rp.trace_capacity * (size_t)rp.trace_words;
+        if (words > g->trace_alloc_words) {
+            clear_cache(g);
+            dfree(g->d_trace);
+            if ((rc = dalloc(&g->d_trace, words)) != BP_OK)
+                return rc;
+            g->trace_alloc_words = words;
+        }
+    }
+
+    cudaStream_t s = (cudaStream_t)opt.cuda_stream;
+    DevGraph dg = dev_graph(g);
+    DevRun dr = dev_run(g);
+    g->has_result = false;
+    auto t_start = std::chrono::steady_clock::now();
+    int64_t kernels = 0;
+    BP_CK(cudaEventRecord(g->ev0, s));
+    launch_init(dtype, dg, dr, s);
+    kernels += ((size_t)g->M * g->k > 0) + 1;
+    if (rp.record_trace)
+        BP_CK(cudaMemsetAsync(g->d_trace, 0, sizeof(uint32_t) * (size_t)rp.trace_capacity * rp.trace_words, s));
+    BP_CK(cudaGetLastError());
+
+    const int max_chunk = opt.rounds_per_launch > 0 ? opt.rounds_per_launch
+                          : (schedule == BP_RS ? 16 : 64);
+    int chunk = opt.rounds_per_launch > 0 ? opt.rounds_per_launch : 2;
+    int64_t rounds_launched = 0;
+    bool stopped = false;
+    std::vector<float> t_eval, t_decide, t_front;   // per global round (profile)
+    // Each replay runs `chunk` rounds (evaluations); graphs that finish turn the
+    // rest of their kernels into no-ops. The host polls the running count once
+    // per replay.
+    for (;;) {
+        CachedGraph *cg = nullptr;
+        if ((rc = get_graph_exec(g, dtype, rp, chunk, opt.profile ? 1 : 0, &cg)) != BP_OK)
+            return rc;
+        BP_CK(cudaGraphLaunch(cg->exec, s));
+        rounds_launched += chunk;
+        kernels += cg->kernels;
+        BP_CK(cudaMemcpyAsync(g->h_running, g->d_running, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        BP_CK(cudaStreamSynchronize(s));
+        if (opt.profile) {
+            for (int r = 0; r < chunk; ++r) {
+                float a = 0.f, b = 0.f, c = 0.f;
+                cudaEvent_t *ev = &cg->events[(size_t)r * 4];
+                BP_CK(cudaEventElapsedTime(&a, ev[0], ev[1]));
+                BP_CK(cudaEventElapsedTime(&b, ev[1], ev[2]));
+                BP_CK(cudaEventElapsedTime(&c, ev[2], ev[3]));
+                t_eval.push_back(a);
+                t_decide.push_back(b);
+                t_front.push_back(c);
+            }
+        }
+        if (*g->h_running <= 0)
+            break;
+        if (rounds_launched > (int64_t)max_rounds + 1) {
+            // cannot happen: every running graph stops after max_rounds + 1 evaluations
+            return fail(BP_ERR_CUDA, "round loop did not terminate");
+        }
+        if (opt.time_budget_ms > 0.0) {
+            double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+            if (el > opt.time_budget_ms) {
+                launch_stop_running(dg, dr, s);
+                stopped = true;
+                break;
+            }
+        }
+        chunk = std::min(chunk * 2, max_chunk);
+    }
+    if (stopped)
+        kernels += 1;
+    launch_beliefs(dtype, dg, dr, g->kp, s);
+    kernels += g->n > 0;
+    BP_CK(cudaGetLastError());
+    BP_CK(cudaEventRecord(g->ev1, s));
+    std::vector<GState> hs((size_t)g->G);
+    BP_CK(cudaMemcpyAsync(hs.data(), g->d_gs, sizeof(GState) * (size_t)g->G, cudaMemcpyDeviceToHost, s));
+    BP_CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    BP_CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+
+    g->last_stats.assign((size_t)g->G, bp_run_stats());
+    bp_run_stats tot;
+    memset(&tot, 0, sizeof(tot));
+    tot.converged = 1;
+    tot.n_graphs = g->G;
+    tot.device_ms = ms;
+    int32_t max_r = 0;
+    bp_profile prof;
+    memset(&prof, 0, sizeof(prof));
+    prof.kernel_launches = kernels;
+    for (int32_t q = 0; q < g->G; ++q) {
+        prof.full_evals += (int64_t)hs[(size_t)q].full_evals;
+        prof.active_vertices += (int64_t)hs[(size_t)q].full_nodes;
+        const GState &st = hs[(size_t)q];
+        bp_run_stats &o = g->last_stats[(size_t)q];
+        memset(&o, 0, sizeof(o));
+        o.converged = st.status == ST_CONVERGED;
+        o.rounds = st.rounds;
+        o.committed_updates = (int64_t)st.committed;
+        o.candidate_evals = (int64_t)st.evals;
+        o.final_max_residual = st.final_maxr;
+        o.final_unconverged = (int64_t)st.final_cnt;
+        o.status = st.status == ST_STOPPED ? BP_ERR_TIMEOUT : BP_OK;
+        o.n_graphs = 1;
+        o.device_ms = ms;
+        tot.converged &= o.converged;
+        tot.rounds = std::max(tot.rounds, o.rounds);
+        tot.committed_updates += o.committed_updates;
+        tot.candidate_evals += o.candidate_evals;
+        tot.final_max_residual = std::max(tot.final_max_residual, o.final_max_residual);
+        tot.final_unconverged += o.final_unconverged;
+        if (o.status != BP_OK)
+            tot.status = o.status;
+        max_r = std::max(max_r, st.rounds);
+    }
+    if (opt.profile) {
+        // rounds with a running graph: every graph evaluates rounds + 1 times
+        const size_t live = std::min(t_eval.size(), (size_t)max_r + 1);
+        for (size_t r = 0; r < live; ++r) {
+            prof.eval_ms += t_eval[r];
+            prof.decide_ms += t_decide[r];
+            prof.frontier_ms += t_front[r];
+        }
+        prof.eval_launches = (int64_t)live;
+    }
+    g->last_profile = prof;
+    g->has_result = true;
+    g->res_dtype = dtype;
+    g->res_schedule = schedule;
+    g->trace_rounds = rp.record_trace ? std::min(max_r, rp.trace_capacity) : 0;
+    g->trace_words = rp.trace_words;
+    if (stats)
+        *stats = tot;
+    if (stopped)
+        return fail(BP_ERR_TIMEOUT, "wall-clock budget ran out; results are from the last committed state");
+    return BP_OK;
+}
+
+int bp_get_beliefs(const bp_graph *g, double *out)
+{
+    if (!g || !out)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (!g->has_result)
+        return fail(BP_ERR_NO_RESULT, "no bp_run result");
+    BP_CK(cudaSetDevice(g->dev));
+    BP_CK(cudaMemcpy(out, g->d_beliefs, sizeof(double) * (size_t)g->n * g->k, cudaMemcpyDeviceToHost));
+    return BP_OK;
+}
+
+int bp_get_messages(const bp_graph *g, double *out)
+{
+    if (!g || !out)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (!g->has_result)
+        return fail(BP_ERR_NO_RESULT, "no bp_run result");
+    BP_CK(cudaSetDevice(g->dev));
+    size_t count = (size_t)g->M * g->k;
+    if (!count)
+        return BP_OK;
+    double *d = nullptr;
+    int rc = dalloc(&d, count);
+    if (rc)
+        return rc;
+    launch_messages(g->res_dtype, dev_graph(g), dev_run(g), g->kp, d, 0);
+    cudaError_t e = cudaMemcpy(out, d, sizeof(double) * count, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy messages");
+    return BP_OK;
+}
+
+int bp_get_graph_stats(const bp_graph *g, bp_run_stats *out)
+{
+    if (!g || !out)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (!g->has_result)
+        return fail(BP_ERR_NO_RESULT, "no bp_run result");
+    memcpy(out, g->last_stats.data(), sizeof(bp_run_stats) * g->last_stats.size());
+    return BP_OK;
+}
+
+int bp_get_trace(const bp_graph *g, uint32_t *out, int64_t capacity_words, int32_t *rounds_out)
+{
+    if (!g || !rounds_out)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (!g->has_result)
+        return fail(BP_ERR_NO_RESULT, "no bp_run result");
+    *rounds_out = g->trace_rounds;
+    size_t words = (size_t)g->trace_rounds * (size_t)g->trace_words;
+    if (!words)
+        return BP_OK;
+    if (!out || capacity_words < (int64_t)words)
+        return fail(BP_ERR_INVALID_ARG, "trace buffer too small");
+    BP_CK(cudaSetDevice(g->dev));
+    BP_CK(cudaMemcpy(out, g->d_trace, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost));
+    return BP_OK;
+}
+
+int bp_get_profile(const bp_graph *g, bp_profile *out)
+{
+    if (!g || !out)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (!g->has_result)
+        return fail(BP_ERR_NO_RESULT, "no bp_run result");
+    *out = g->last_profile;
+    return BP_OK;
+}
+
+int bp_graph_info(const bp_graph *g, int32_t *n_vars, int32_t *n_states, int64_t *n_dir_edges, int32_t *n_graphs)
+{
+    if (!g)
+        return fail(BP_ERR_INVALID_ARG, "NULL handle");
+    if (n_vars)
+        *n_vars = g->n;
+    if (n_states)
+        *n_states = g->k;
+    if (n_dir_edges)
+        *n_dir_edges = g->M;
+    if (n_graphs)
+        *n_graphs = g->G;
+    return BP_OK;
+}
+
+void bp_destroy_graph(bp_graph *g)
+{
+    if (!g)
+        return;
+    cudaSetDevice(g->dev);
+    free_run_buffers(g);
+    dfree(g->d_row_ptr);
+    dfree(g->d_col);
+    dfree(g->d_rev);
+    dfree(g->d_gid);
+    dfree(g->d_gv_off);
+    dfree(g->d_ge_off);
+    dfree(g->d_unary);
+    dfree(g->d_udiff32);
+    dfree(g->d_udiff64);
+    dfree(g->d_q32);
+    dfree(g->d_q64);
+    dfree(g->d_pair);
+    dfree(g->d_psi_shared);
+    dfree(g->d_level);
+    dfree(g->d_gs);
+    dfree(g->d_red_max);
+    dfree(g->d_red_cnt);
+    dfree(g->d_running);
+    dfree(g->d_trace);
+    dfree(g->d_beliefs);
+    if (g->h_running)
+        cudaFreeHost(g->h_running);
+    if (g->cap_stream)
+        cudaStreamDestroy(g->cap_stream);
+    if (g->ev0)
+        cudaEventDestroy(g->ev0);
+    if (g->ev1)
+        cudaEventDestroy(g->ev1);
+    delete g;
+}
+
+const char *bp_status_string(int status)
+{
+    switch (status) {
+    case BP_OK: return "ok";
+    case BP_ERR_INVALID_ARG: return "invalid argument";
+    case BP_ERR_BAD_GRAPH: return "invalid graph";
+    case BP_ERR_NO_POTENTIALS: return "potentials not set";
+    case BP_ERR_NONFINITE: return "non-finite or inconsistent potentials";
+    case BP_ERR_CUDA: return "CUDA error";
+    case BP_ERR_TIMEOUT: return "time budget exhausted";
+    case BP_ERR_OOM: return "out of memory";
+    case BP_ERR_UNSUPPORTED: return "unsupported configuration";
+    case BP_ERR_NO_RESULT: return "no result available";
+    default: return "unknown status";
+    }
+}
+
+const char *bp_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+// Internal device structures and helpers of libbp_gb300 (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bpg {
+
+// Per-graph run status.
+enum : int32_t { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXROUNDS = 2, ST_STOPPED = 3 };
+
+// Sub-slots per graph for the max/count reductions (spreads same-address atomics).
+constexpr int NSUB = 32;
+
+// Per-graph device state, one per graph of a handle.
+struct GState {
+    int32_t status;
+    int32_t rounds;        // committing rounds so far
+    int32_t cur;           // message buffer holding the committed state
+    int32_t k_sel;         // RBP/RS frontier size of the current round
+    uint32_t thr;          // RnBP threshold floor(p * 2^32) of the current round
+    int32_t always;        // RnBP: p >= 1 this round
+    uint64_t n_prev;       // RnBP: unconverged count of the previous round
+    unsigned long long committed;
+    unsigned long long evals;        // all message evaluations (full + splash)
+    unsigned long long full_evals;   // messages evaluated by full-evaluation launches
+    unsigned long long full_nodes;   // vertices processed by full-evaluation launches
+    double final_maxr;
+    unsigned long long final_cnt;
+};
+
+// Read-only graph and potential arrays on the device.
+struct DevGraph {
+    int32_t n, k, G;
+    int32_t M;
+    const int32_t *row_ptr;   // [n+1]
+    const int32_t *col;       // [M]
+    const int32_t *rev;       // [M]
+    const int32_t *gid;       // [n] graph of each vertex
+    const int32_t *gv_off;    // [G+1]
+    const int32_t *ge_off;    // [G+1]
+    // potentials
+    int32_t pair_kind;
+    const float *unary;       // [n*k] log-potentials
+    const float *udiff32;     // [n]  theta_i(1) - theta_i(0)      (k = 2, Ising)
+    const double *udiff64;    // [n]
+    const float *q32;         // [M]  exp(-2 beta_e)                (k = 2, Ising)
+    const double *q64;        // [M]
+    const float *pair;        // table [M*k*k] (log) or shared [k*k] (log)
+    const float *psi_shared;  // [k*k] exp(Theta - max Theta)     (shared)
+};
+
+// Per-run parameters (kernel arguments, baked into the captured graph).
+struct RunParams {
+    int32_t schedule;
+    int32_t max_rounds;
+    double eps;
+    double low_p;
+    double high_p;
+    double ratio_threshold;
+    uint64_t seed;
+    uint32_t graph_id_base;
+    int32_t splash_depth;
+    int32_t rs_roots_mode;
+    int32_t record_trace;
+    int32_t trace_capacity;
+    int32_t trace_words;      // words per recorded round
+};
+
+// Mutable per-run device buffers.
+struct DevRun {
+    void *msg[2];                 // message buffers (storage dtype)
+    void *resid;                  // [M] residuals (float, or double for FP64)
+    void *vres;                   // [n] vertex residuals for RS (residual type)
+    int8_t *level;                // [n] splash level (-1 none)
+    GState *gs;                   // [G]
+    unsigned long long *red_max;  // [G*NSUB] double bits
+    unsigned int *red_cnt;        // [G*NSUB]
+    int32_t *n_running;           // [1]
+    uint32_t *trace;              // [trace_capacity * trace_words]
+    double *beliefs;              // [n*k]
+};
+
+// ---------------------------------------------------------------------------
+// Storage traits: message element type S, arithmetic type A.
+template <typename S> struct Store;
+template <> struct Store<double> {
+    using A = double;
+    static __device__ __forceinline__ double ld(const double *p) { return *p; }
+    static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
+    static __device__ __forceinline__ double quant(double v) { return v; }
+};
+template <> struct Store<float> {
+    using A = float;
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ float quant(float v) { return v; }
+};
+template <> struct Store<__nv_bfloat16> {
+    using A = float;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float quant(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+};
+
+// Residual element type: double for FP64 messages, float otherwise.
+template <typename S> struct ResidT { using T = float; };
+template <> struct ResidT<double> { using T = double; };
+
+// ---------------------------------------------------------------------------
+// Math in the arithmetic type. FP32 uses the SFU intrinsics.
+__device__ __forceinline__ float m_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_log(float x) { return __logf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float m_sigmoid(float u) { return __fdividef(1.0f, 1.0f + __expf(-u)); }
+__device__ __forceinline__ double m_sigmoid(double u) { return 1.0 / (1.0 + exp(-u)); }
+
+// Binary Ising message in log-odds u = log m(1) - log m(0).
+// With cavity log-odds h of x_i and q = exp(-2 beta):
+//   u = sign(h) * log((1 + q F) / (q + F)),  F = exp(-|h|),
+// which is log[(e^{-b} + e^{b+h}) / (e^{b} + e^{h-b})] rearranged so that no
+// term overflows (the sum over x_i of Eq. 2 for the 2x2 Ising table).
+__device__ __forceinline__ float ising_logodds(float q, float h)
+{
+    float F = __expf(-fabsf(h));
+    float u = __logf(__fdividef(1.0f + q * F, q + F));
+    return h >= 0.0f ? u : -u;
+}
+__device__ __forceinline__ double ising_logodds(double q, double h)
+{
+    double F = exp(-fabs(h));
+    double u = log1p(q * F) - log(q + F);
+    return h >= 0.0 ? u : -u;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11), one block of four words.
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return c0;
+}
+
+__device__ __forceinline__ bool rnbp_pick(const RunParams &rp, uint32_t local_edge, uint32_t round,
+                                          uint32_t graph, const GState &st)
+{
+    if (st.always)
+        return true;
+    uint32_t w = philox_word0(local_edge, round, rp.graph_id_base + graph, 0u,
+                              (uint32_t)(rp.seed & 0xffffffffu), (uint32_t)(rp.seed >> 32));
+    return w < st.thr;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions of (max residual, count >= eps) into per-graph sub-slots.
+// Threads of a block cover consecutive vertices, so graph ids are monotone
+// within a block; a block whose first and last vertex share a graph reduces
+// in shared memory and issues one atomic per quantity.
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ unsigned int warp_sum_u32(unsigned int v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// All threads of the block must call this. g = graph of the thread's item (any
+// value if !valid); uniform = block-wide flag that every valid item has graph g0.
+__device__ __forceinline__ void reduce_to_graph(const DevRun &dr, bool uniform, int32_t g0,
+                                                bool valid, int32_t g, double maxr, unsigned int cnt)
+{
+    unsigned long long mb = valid ? (unsigned long long)__double_as_longlong(maxr) : 0ull;
+    unsigned int c = valid ? cnt : 0u;
+    int slot = blockIdx.x & (NSUB - 1);
+    if (uniform) {
+        __shared__ unsigned long long s_max[32];
+        __shared__ unsigned int s_cnt[32];
+        mb = warp_max_u64(mb);
+        c = warp_sum_u32(c);
+        int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) {
+            s_max[warp] = mb;
+            s_cnt[warp] = c;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            int nw = (blockDim.x + 31) >> 5;
+            mb = lane < nw ? s_max[lane] : 0ull;
+            c = lane < nw ? s_cnt[lane] : 0u;
+            mb = warp_max_u64(mb);
+            c = warp_sum_u32(c);
+            if (lane == 0) {
+                if (mb)
+                    atomicMax(&dr.red_max[(size_t)g0 * NSUB + slot], mb);
+                if (c)
+                    atomicAdd(&dr.red_cnt[(size_t)g0 * NSUB + slot], c);
+            }
+        }
+    } else if (valid) {
+        if (mb)
+            atomicMax(&dr.red_max[(size_t)g * NSUB + slot], mb);
+        if (c)
+            atomicAdd(&dr.red_cnt[(size_t)g * NSUB + slot], c);
+    }
+}
+
+}  // namespace bpg

@@ -1,0 +1,695 @@
+// Round kernels of frontier-scheduled loopy BP on sm_103a.
+//
+// One round of Algorithm 1 on the device:
+//   eval    candidates of Eq. 2 for every message of every running graph, the
+//           residual of Eq. 4 (max-norm of the probability-domain change) fused
+//           in the epilogue, and the per-graph max-residual / unconverged count
+//   decide  per graph: eps test, max-rounds test, the next frontier's size or
+//           RnBP probability (EdgeRatio, Section IV-A)
+//   commit  LBP: swap buffers; RnBP: eps filter + Philox Bernoulli; RBP/RS: in
+//           the select kernels (bp_select.cu)
+// Messages live in the log domain: binary messages as one log-odds value
+// u = log m(1) - log m(0), k-state messages as k normalised logs.
+#include "bp_internal.cuh"
+#include "bp_launch.h"
+
+#include <math.h>
+
+namespace bpg {
+
+constexpr int BLOCK = 256;
+
+// --------------------------------------------------------------------------
+// Binary Ising messages, one thread per vertex: the thread gathers the
+// incoming log-odds of its vertex through rev[], forms the cavity of each
+// out-edge by subtraction and writes every out-message of the vertex.
+template <typename S, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunParams rp, int level_L)
+{
+    using A = typename Store<S>::A;
+    using RT = typename ResidT<S>::T;
+    const int first = blockIdx.x * blockDim.x;
+    const int last = min(g.n - 1, first + (int)blockDim.x - 1);
+    const int g0 = g.gid[first];
+    const bool uniform = (g0 == g.gid[last]);
+    const int i = first + threadIdx.x;
+    bool valid = false;
+    int gg = g0;
+    double maxr = 0.0;
+    unsigned int cnt = 0;
+    if (i < g.n) {
+        gg = g.gid[i];
+        const int status = dr.gs[gg].status;
+        bool act = (status == ST_RUNNING);
+        if (MODE == MODE_SPLASH)
+            act = act && (dr.level[i] == level_L);
+        if (act) {
+            valid = true;
+            const int cur_idx = dr.gs[gg].cur;
+            const S *cur = (const S *)dr.msg[cur_idx];
+            S *out = (S *)dr.msg[cur_idx ^ 1];
+            const int beg = g.row_ptr[i], end = g.row_ptr[i + 1];
+            const int deg = end - beg;
+            A h;
+            const A *q;
+            if constexpr (sizeof(A) == 8) {
+                h = g.udiff64[i];
+                q = (const A *)g.q64;
+            } else {
+                h = g.udiff32[i];
+                q = (const A *)g.q32;
+            }
+            constexpr int CACHE = 8;
+            A uin[CACHE];
+#pragma unroll
+            for (int c = 0; c < CACHE; ++c) {
+                if (c < deg) {
+                    uin[c] = Store<S>::ld(cur + g.rev[beg + c]);
+                    h += uin[c];
+                }
+            }
+            for (int e = beg + CACHE; e < end; ++e)
+                h += Store<S>::ld(cur + g.rev[e]);
+            RT *R = (RT *)dr.resid;
+            auto one = [&](int e, A u_in) {
+                A unew = ising_logodds(q[e], h - u_in);
+                if (MODE == MODE_SPLASH) {
+                    Store<S>::st(out + e, unew);
+                    return;
+                }
+                A uq = Store<S>::quant(unew);
+                A r = fabs(m_sigmoid(uq) - m_sigmoid(Store<S>::ld(cur + e)));
+                Store<S>::st(out + e, unew);
+                if (MODE == MODE_CAND)
+                    R[e] = (RT)r;
+                double rd = (double)r;
+                maxr = rd > maxr ? rd : maxr;
+                cnt += (rd >= rp.eps) ? 1u : 0u;
+            };
+#pragma unroll
+            for (int c = 0; c < CACHE; ++c)
+                if (c < deg)
+                    one(beg + c, uin[c]);
+            for (int e = beg + CACHE; e < end; ++e)
+                one(e, Store<S>::ld(cur + g.rev[e]));
+        }
+    }
+    if (MODE != MODE_SPLASH)
+        reduce_to_graph(dr, uniform, g0, valid, gg, maxr, cnt);
+}
+
+// --------------------------------------------------------------------------
+// k-state messages (k <= KP <= 32): a group of KP lanes per vertex, lane x
+// holds state x. S_i(x) = theta_i(x) + sum_in l(x); per out-edge the cavity is
+// S_i - l_{j->i}; with a(x) = exp(cav(x) - max cav) the new message is
+// c(y) = sum_x a(x) psi(x, y), normalised, stored as log c(y).
+// Lane mask of the KP-lane group that contains this thread. Groups of one warp
+// may run different trip counts (vertex degrees differ), so every shuffle names
+// only its own group's lanes.
+template <int KP> __device__ __forceinline__ unsigned grp_mask()
+{
+    if (KP == 32)
+        return 0xffffffffu;
+    return ((1u << KP) - 1u) << ((threadIdx.x & 31) & ~(KP - 1));
+}
+template <int KP> __device__ __forceinline__ float grp_max(unsigned m, float v)
+{
+#pragma unroll
+    for (int o = KP / 2; o; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(m, v, o, KP));
+    return v;
+}
+template <int KP> __device__ __forceinline__ double grp_max(unsigned m, double v)
+{
+#pragma unroll
+    for (int o = KP / 2; o; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(m, v, o, KP));
+    return v;
+}
+template <int KP, typename T> __device__ __forceinline__ T grp_sum(unsigned m, T v)
+{
+#pragma unroll
+    for (int o = KP / 2; o; o >>= 1)
+        v += __shfl_xor_sync(m, v, o, KP);
+    return v;
+}
+
+template <typename A> __device__ __forceinline__ A log_floor();
+template <> __device__ __forceinline__ float log_floor<float>() { return -80.0f; }
+template <> __device__ __forceinline__ double log_floor<double>() { return -700.0; }
+
+template <typename S, int KP, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_eval_gen(DevGraph g, DevRun dr, RunParams rp, int level_L)
+{
+    using A = typename Store<S>::A;
+    using RT = typename ResidT<S>::T;
+    __shared__ float s_psi[32 * 32];
+    const int k = g.k;
+    if (g.pair_kind == 2) {
+        for (int t = threadIdx.x; t < k * k; t += blockDim.x)
+            s_psi[t] = g.psi_shared[t];
+        __syncthreads();
+    }
+    constexpr int NPB = BLOCK / KP;
+    const int lane = threadIdx.x % KP;
+    const int first = blockIdx.x * NPB;
+    const int last = min(g.n - 1, first + NPB - 1);
+    const int g0 = g.gid[first];
+    const bool uniform = (g0 == g.gid[last]);
+    const int i = first + (int)threadIdx.x / KP;
+    const bool lane_ok = lane < k;
+    bool valid = false;
+    int gg = g0;
+    double maxr = 0.0;
+    unsigned int cnt = 0;
+    bool act = false;
+    if (i < g.n) {
+        gg = g.gid[i];
+        act = dr.gs[gg].status == ST_RUNNING;
+        if (MODE == MODE_SPLASH)
+            act = act && (dr.level[i] == level_L);
+    }
+    if (act) {   // uniform across the KP-lane group
+        const unsigned gm = grp_mask<KP>();
+        valid = (lane == 0);
+        const int cur_idx = dr.gs[gg].cur;
+        const S *cur = (const S *)dr.msg[cur_idx];
+        S *out = (S *)dr.msg[cur_idx ^ 1];
+        const int beg = g.row_ptr[i], end = g.row_ptr[i + 1];
+        A Sx = lane_ok ? (A)g.unary[(size_t)i * k + lane] : (A)0;
+        for (int e = beg; e < end; ++e)
+            if (lane_ok)
+                Sx += Store<S>::ld(cur + (size_t)g.rev[e] * k + lane);
+        RT *R = (RT *)dr.resid;
+        for (int e = beg; e < end; ++e) {
+            A lin = lane_ok ? Store<S>::ld(cur + (size_t)g.rev[e] * k + lane) : (A)0;
+            A cav = lane_ok ? Sx - lin : (A)(-1e30);
+            A mx = grp_max<KP>(gm, cav);
+            A a = lane_ok ? m_exp(cav - mx) : (A)0;
+            A acc = 0;
+            if (g.pair_kind == 2) {
+                for (int x = 0; x < k; ++x) {
+                    A ax = __shfl_sync(gm, a, x, KP);
+                    if (lane_ok)
+                        acc += ax * (A)s_psi[x * k + lane];
+                }
+            } else {
+                const float *tab = g.pair + (size_t)e * k * k;
+                for (int x = 0; x < k; ++x) {
+                    A ax = __shfl_sync(gm, a, x, KP);
+                    if (lane_ok)
+                        acc += ax * m_exp((A)tab[x * k + lane]);
+                }
+            }
+            A z = grp_sum<KP>(gm, lane_ok ? acc : (A)0);
+            A lnew = lane_ok ? m_log(m_div(acc, z)) : (A)0;
+            lnew = lnew > log_floor<A>() ? lnew : log_floor<A>();
+            if (MODE == MODE_SPLASH) {
+                if (lane_ok)
+                    Store<S>::st(out + (size_t)e * k + lane, lnew);
+                continue;
+            }
+            A pn = lane_ok ? m_exp(Store<S>::quant(lnew)) : (A)0;
+            A po = lane_ok ? m_exp(Store<S>::ld(cur + (size_t)e * k + lane)) : (A)0;
+            A r = grp_max<KP>(gm, fabs(pn - po));
+            if (lane_ok)
+                Store<S>::st(out + (size_t)e * k + lane, lnew);
+            if (MODE == MODE_CAND && lane == 0)
+                R[e] = (RT)r;
+            double rd = (double)r;
+            maxr = rd > maxr ? rd : maxr;
+            cnt += (rd >= rp.eps) ? 1u : 0u;
+        }
+    }
+    if (MODE != MODE_SPLASH)
+        reduce_to_graph(dr, uniform, g0, valid, gg, maxr, cnt);
+}
+
+// --------------------------------------------------------------------------
+// Per-graph decision after an evaluation (one warp per graph).
+__global__ void k_decide(DevGraph g, DevRun dr, RunParams rp)
+{
+    const int gg = blockIdx.x;
+    const int lane = threadIdx.x;
+    GState *stp = dr.gs + gg;
+    if (stp->status != ST_RUNNING)
+        return;
+    unsigned long long mb = dr.red_max[(size_t)gg * NSUB + lane];
+    unsigned int c = dr.red_cnt[(size_t)gg * NSUB + lane];
+    dr.red_max[(size_t)gg * NSUB + lane] = 0ull;
+    dr.red_cnt[(size_t)gg * NSUB + lane] = 0u;
+    mb = warp_max_u64(mb);
+    c = warp_sum_u32(c);
+    if (lane != 0)
+        return;
+    GState st = *stp;
+    const double maxr = __longlong_as_double((long long)mb);
+    const int64_t Mg = g.ge_off[gg + 1] - g.ge_off[gg];
+    const int64_t ng = g.gv_off[gg + 1] - g.gv_off[gg];
+    st.evals += (unsigned long long)Mg;
+    st.full_evals += (unsigned long long)Mg;
+    st.full_nodes += (unsigned long long)ng;
+    st.final_maxr = maxr;
+    st.final_cnt = c;
+    if (maxr < rp.eps) {
+        st.status = ST_CONVERGED;
+    } else if (st.rounds >= rp.max_rounds) {
+        st.status = ST_MAXROUNDS;
+    } else {
+        st.rounds += 1;
+        if (rp.schedule == SCHED_LBP) {
+            st.cur ^= 1;
+            st.committed += (unsigned long long)Mg;
+        } else if (rp.schedule == SCHED_RNBP) {
+            double p;
+            if (st.rounds == 1)
+                p = rp.high_p;
+            else
+                p = ((double)c / (double)st.n_prev > rp.ratio_threshold) ? rp.low_p : rp.high_p;
+            st.always = (p >= 1.0) ? 1 : 0;
+            st.thr = (p <= 0.0 || p >= 1.0) ? 0u : (uint32_t)(uint64_t)(p * 4294967296.0);
+        } else {
+            const int64_t base = (rp.schedule == SCHED_RS && rp.rs_roots_mode == 1) ? ng : Mg;
+            const int64_t hi = (rp.schedule == SCHED_RS) ? ng : Mg;
+            double v = ceil(rp.low_p * (double)base);
+            int64_t kk = (v > (double)hi) ? hi : (int64_t)v;
+            kk = kk < 1 ? 1 : kk;
+            kk = kk > hi ? hi : kk;
+            st.k_sel = (int32_t)kk;
+            if (rp.schedule == SCHED_RBP)
+                st.committed += (unsigned long long)kk;
+        }
+        st.n_prev = c;
+    }
+    *stp = st;
+    if (st.status != ST_RUNNING)
+        atomicSub(dr.n_running, 1);
+}
+
+// --------------------------------------------------------------------------
+// Per-vertex block reduction of a count into gs[g].committed (and evals).
+__device__ __forceinline__ void add_commit_counts(const DevRun &dr, bool uniform, int g0, bool valid,
+                                                  int g, unsigned int c, bool also_evals)
+{
+    if (uniform) {
+        __shared__ unsigned int s_c[32];
+        unsigned int v = warp_sum_u32(valid ? c : 0u);
+        int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0)
+            s_c[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int nw = (blockDim.x + 31) >> 5;
+            v = lane < nw ? s_c[lane] : 0u;
+            v = warp_sum_u32(v);
+            if (lane == 0 && v) {
+                atomicAdd(&dr.gs[g0].committed, (unsigned long long)v);
+                if (also_evals)
+                    atomicAdd(&dr.gs[g0].evals, (unsigned long long)v);
+            }
+        }
+    } else if (valid && c) {
+        atomicAdd(&dr.gs[g].committed, (unsigned long long)c);
+        if (also_evals)
+            atomicAdd(&dr.gs[g].evals, (unsigned long long)c);
+    }
+}
+
+// RnBP commit: keep messages with residual >= eps, then a Philox Bernoulli(p_t)
+// draw keyed by (seed; local edge id, round, graph id) (Section IV-A).
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_commit_rnbp(DevGraph g, DevRun dr, RunParams rp)
+{
+    using RT = typename ResidT<S>::T;
+    const int first = blockIdx.x * blockDim.x;
+    const int last = min(g.n - 1, first + (int)blockDim.x - 1);
+    const int g0 = g.gid[first];
+    const bool uniform = (g0 == g.gid[last]);
+    const int i = first + threadIdx.x;
+    bool valid = false;
+    int gg = g0;
+    unsigned int c = 0;
+    if (i < g.n) {
+        gg = g.gid[i];
+        const GState st = dr.gs[gg];
+        if (st.status == ST_RUNNING) {
+            valid = true;
+            const RT *R = (const RT *)dr.resid;
+            S *dst = (S *)dr.msg[0];
+            const S *src = (const S *)dr.msg[1];
+            const int e0 = g.ge_off[gg];
+            const int k = g.k;
+            const bool tr = rp.record_trace && st.rounds <= rp.trace_capacity;
+            for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
+                if ((double)R[e] >= rp.eps && rnbp_pick(rp, (uint32_t)(e - e0), (uint32_t)st.rounds,
+                                                        (uint32_t)gg, st)) {
+                    for (int x = 0; x < k; ++x)
+                        dst[(size_t)e * k + x] = src[(size_t)e * k + x];
+                    ++c;
+                    if (tr)
+                        atomicOr(&dr.trace[(size_t)(st.rounds - 1) * rp.trace_words + (e >> 5)],
+                                 1u << (e & 31));
+                }
+            }
+        }
+    }
+    add_commit_counts(dr, uniform, g0, valid, gg, c, false);
+}
+
+// Residual Splash: one BFS level (pull): an unreached vertex next to a vertex of
+// level d-1 gets level d.
+__global__ void __launch_bounds__(BLOCK) k_bfs_level(DevGraph g, DevRun dr, int d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n)
+        return;
+    if (dr.gs[g.gid[i]].status != ST_RUNNING || dr.level[i] >= 0)
+        return;
+    for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
+        if (dr.level[g.col[e]] == d - 1) {
+            dr.level[i] = (int8_t)d;
+            return;
+        }
+    }
+}
+
+// Residual Splash sub-step commit: out-messages of level-L vertices.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_splash_commit(DevGraph g, DevRun dr, int level_L)
+{
+    const int first = blockIdx.x * blockDim.x;
+    const int last = min(g.n - 1, first + (int)blockDim.x - 1);
+    const int g0 = g.gid[first];
+    const bool uniform = (g0 == g.gid[last]);
+    const int i = first + threadIdx.x;
+    bool valid = false;
+    int gg = g0;
+    unsigned int c = 0;
+    if (i < g.n) {
+        gg = g.gid[i];
+        if (dr.gs[gg].status == ST_RUNNING && dr.level[i] == level_L) {
+            valid = true;
+            S *dst = (S *)dr.msg[0];
+            const S *src = (const S *)dr.msg[1];
+            const int k = g.k;
+            const int beg = g.row_ptr[i], end = g.row_ptr[i + 1];
+            for (int t = beg * k; t < end * k; ++t)
+                dst[t] = src[t];
+            c = (unsigned int)(end - beg);
+        }
+    }
+    add_commit_counts(dr, uniform, g0, valid, gg, c, true);
+}
+
+// --------------------------------------------------------------------------
+// Set-up of a run.
+template <typename S>
+__global__ void k_init_msgs(S *a, S *b, size_t count, double value)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+         t += (size_t)gridDim.x * blockDim.x) {
+        Store<S>::st(a + t, (typename Store<S>::A)value);
+        Store<S>::st(b + t, (typename Store<S>::A)value);
+    }
+}
+
+__global__ void k_init_state(DevRun dr, int G)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G * NSUB; t += gridDim.x * blockDim.x) {
+        dr.red_max[t] = 0ull;
+        dr.red_cnt[t] = 0u;
+        if (t < G) {
+            GState st;
+            st.status = ST_RUNNING;
+            st.rounds = 0;
+            st.cur = 0;
+            st.k_sel = 0;
+            st.thr = 0;
+            st.always = 0;
+            st.n_prev = 0;
+            st.committed = 0;
+            st.evals = 0;
+            st.full_evals = 0;
+            st.full_nodes = 0;
+            st.final_maxr = 0.0;
+            st.final_cnt = 0;
+            dr.gs[t] = st;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *dr.n_running = G;
+}
+
+// Marks every still-running graph as stopped (wall-clock budget).
+__global__ void k_stop_running(DevRun dr, int G)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
+        if (dr.gs[t].status == ST_RUNNING) {
+            dr.gs[t].status = ST_STOPPED;
+            atomicSub(dr.n_running, 1);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Beliefs (Eq. 3), normalised in FP64, and messages in the probability domain.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_beliefs_bin(DevGraph g, DevRun dr)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n)
+        return;
+    const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
+    double h = g.udiff64[i];
+    for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
+        h += (double)Store<S>::ld(cur + g.rev[e]);
+    dr.beliefs[2 * (size_t)i + 1] = 1.0 / (1.0 + exp(-h));
+    dr.beliefs[2 * (size_t)i] = 1.0 / (1.0 + exp(h));
+}
+
+template <typename S, int KP>
+__global__ void __launch_bounds__(BLOCK) k_beliefs_gen(DevGraph g, DevRun dr)
+{
+    constexpr int NPB = BLOCK / KP;
+    const int lane = threadIdx.x % KP;
+    const int i = blockIdx.x * NPB + (int)threadIdx.x / KP;
+    if (i >= g.n)
+        return;
+    const int k = g.k;
+    const bool ok = lane < k;
+    const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
+    double s = ok ? (double)g.unary[(size_t)i * k + lane] : -1e300;
+    for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
+        if (ok)
+            s += (double)Store<S>::ld(cur + (size_t)g.rev[e] * k + lane);
+    const unsigned gm = grp_mask<KP>();
+    double mx = grp_max<KP>(gm, s);
+    double w = ok ? exp(s - mx) : 0.0;
+    double z = grp_sum<KP>(gm, w);
+    if (ok)
+        dr.beliefs[(size_t)i * k + lane] = w / z;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_messages_bin(DevGraph g, DevRun dr, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n)
+        return;
+    const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
+    for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
+        double u = (double)Store<S>::ld(cur + e);
+        out[2 * (size_t)e + 1] = 1.0 / (1.0 + exp(-u));
+        out[2 * (size_t)e] = 1.0 / (1.0 + exp(u));
+    }
+}
+
+template <typename S, int KP>
+__global__ void __launch_bounds__(BLOCK) k_messages_gen(DevGraph g, DevRun dr, double *out)
+{
+    constexpr int NPB = BLOCK / KP;
+    const int lane = threadIdx.x % KP;
+    const int i = blockIdx.x * NPB + (int)threadIdx.x / KP;
+    if (i >= g.n)
+        return;
+    const int k = g.k;
+    const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
+    if (lane < k)
+        for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
+            out[(size_t)e * k + lane] = exp((double)Store<S>::ld(cur + (size_t)e * k + lane));
+}
+
+// --------------------------------------------------------------------------
+// Host-side launchers.
+static inline int blocks_for(int n, int per_block) { return (n + per_block - 1) / per_block; }
+
+template <typename S>
+static void launch_eval_t(const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
+                          int kp, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    if (g.k == 2 && g.pair_kind == 0) {
+        int nb = blocks_for(g.n, BLOCK);
+        if (mode == MODE_LBP)
+            k_eval_bin<S, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+        else if (mode == MODE_CAND)
+            k_eval_bin<S, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+        else
+            k_eval_bin<S, MODE_SPLASH><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+        return;
+    }
+#define BPG_GEN(KPV)                                                                  \
+    {                                                                                 \
+        int nb = blocks_for(g.n, BLOCK / KPV);                                        \
+        if (mode == MODE_LBP)                                                         \
+            k_eval_gen<S, KPV, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);    \
+        else if (mode == MODE_CAND)                                                   \
+            k_eval_gen<S, KPV, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);   \
+        else                                                                          \
+            k_eval_gen<S, KPV, MODE_SPLASH><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L); \
+    }
+    if (kp == 4) BPG_GEN(4)
+    else if (kp == 8) BPG_GEN(8)
+    else if (kp == 16) BPG_GEN(16)
+    else BPG_GEN(32)
+#undef BPG_GEN
+}
+
+void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
+                 int kp, cudaStream_t s)
+{
+    if (dtype == DT_F64)
+        launch_eval_t<double>(g, dr, rp, mode, level_L, kp, s);
+    else if (dtype == DT_F32)
+        launch_eval_t<float>(g, dr, rp, mode, level_L, kp, s);
+    else
+        launch_eval_t<__nv_bfloat16>(g, dr, rp, mode, level_L, kp, s);
+}
+
+void launch_decide(const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
+{
+    k_decide<<<g.G, 32, 0, s>>>(g, dr, rp);
+}
+
+void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    int nb = blocks_for(g.n, BLOCK);
+    if (dtype == DT_F64)
+        k_commit_rnbp<double><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+    else if (dtype == DT_F32)
+        k_commit_rnbp<float><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+    else
+        k_commit_rnbp<__nv_bfloat16><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+}
+
+void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    k_bfs_level<<<blocks_for(g.n, BLOCK), BLOCK, 0, s>>>(g, dr, d);
+}
+
+void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int level_L, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    int nb = blocks_for(g.n, BLOCK);
+    if (dtype == DT_F64)
+        k_splash_commit<double><<<nb, BLOCK, 0, s>>>(g, dr, level_L);
+    else if (dtype == DT_F32)
+        k_splash_commit<float><<<nb, BLOCK, 0, s>>>(g, dr, level_L);
+    else
+        k_splash_commit<__nv_bfloat16><<<nb, BLOCK, 0, s>>>(g, dr, level_L);
+}
+
+void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s)
+{
+    size_t count = (size_t)g.M * (size_t)g.k;
+    double v = (g.k == 2 && g.pair_kind == 0) ? 0.0 : -log((double)g.k);
+    if (count) {
+        int nb = (int)((count + BLOCK - 1) / BLOCK);
+        nb = nb > 152 * 16 ? 152 * 16 : nb;
+        if (dtype == DT_F64)
+            k_init_msgs<double><<<nb, BLOCK, 0, s>>>((double *)dr.msg[0], (double *)dr.msg[1], count,
+                                                    v);
+        else if (dtype == DT_F32)
+            k_init_msgs<float><<<nb, BLOCK, 0, s>>>((float *)dr.msg[0], (float *)dr.msg[1], count, v);
+        else
+            k_init_msgs<__nv_bfloat16><<<nb, BLOCK, 0, s>>>((__nv_bfloat16 *)dr.msg[0],
+                                                           (__nv_bfloat16 *)dr.msg[1], count, v);
+    }
+    int nb2 = blocks_for(g.G * NSUB, BLOCK);
+    k_init_state<<<nb2, BLOCK, 0, s>>>(dr, g.G);
+}
+
+void launch_stop_running(const DevGraph &g, const DevRun &dr, cudaStream_t s)
+{
+    k_stop_running<<<blocks_for(g.G, BLOCK), BLOCK, 0, s>>>(dr, g.G);
+}
+
+void launch_beliefs(int dtype, const DevGraph &g, const DevRun &dr, int kp, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    if (g.k == 2 && g.pair_kind == 0) {
+        int nb = blocks_for(g.n, BLOCK);
+        if (dtype == DT_F64)
+            k_beliefs_bin<double><<<nb, BLOCK, 0, s>>>(g, dr);
+        else if (dtype == DT_F32)
+            k_beliefs_bin<float><<<nb, BLOCK, 0, s>>>(g, dr);
+        else
+            k_beliefs_bin<__nv_bfloat16><<<nb, BLOCK, 0, s>>>(g, dr);
+        return;
+    }
+#define BPG_B(KPV)                                                                   \
+    {                                                                                \
+        int nb = blocks_for(g.n, BLOCK / KPV);                                       \
+        if (dtype == DT_F64)                                                         \
+            k_beliefs_gen<double, KPV><<<nb, BLOCK, 0, s>>>(g, dr);                  \
+        else if (dtype == DT_F32)                                                    \
+            k_beliefs_gen<float, KPV><<<nb, BLOCK, 0, s>>>(g, dr);                   \
+        else                                                                         \
+            k_beliefs_gen<__nv_bfloat16, KPV><<<nb, BLOCK, 0, s>>>(g, dr);           \
+    }
+    if (kp == 4) BPG_B(4)
+    else if (kp == 8) BPG_B(8)
+    else if (kp == 16) BPG_B(16)
+    else BPG_B(32)
+#undef BPG_B
+}
+
+void launch_messages(int dtype, const DevGraph &g, const DevRun &dr, int kp, double *out, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    if (g.k == 2 && g.pair_kind == 0) {
+        int nb = blocks_for(g.n, BLOCK);
+        if (dtype == DT_F64)
+            k_messages_bin<double><<<nb, BLOCK, 0, s>>>(g, dr, out);
+        else if (dtype == DT_F32)
+            k_messages_bin<float><<<nb, BLOCK, 0, s>>>(g, dr, out);
+        else
+            k_messages_bin<__nv_bfloat16><<<nb, BLOCK, 0, s>>>(g, dr, out);
+        return;
+    }
+#define BPG_M(KPV)                                                                   \
+    {                                                                                \
+        int nb = blocks_for(g.n, BLOCK / KPV);                                       \
+        if (dtype == DT_F64)                                                         \
+            k_messages_gen<double, KPV><<<nb, BLOCK, 0, s>>>(g, dr, out);            \
+        else if (dtype == DT_F32)                                                    \
+            k_messages_gen<float, KPV><<<nb, BLOCK, 0, s>>>(g, dr, out);             \
+        else                                                                         \
+            k_messages_gen<__nv_bfloat16, KPV><<<nb, BLOCK, 0, s>>>(g, dr, out);     \
+    }
+    if (kp == 4) BPG_M(4)
+    else if (kp == 8) BPG_M(8)
+    else if (kp == 16) BPG_M(16)
+    else BPG_M(32)
+#undef BPG_M
+}
+
+}  // namespace bpg

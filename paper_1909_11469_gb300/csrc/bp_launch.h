@@ -1,0 +1,25 @@
+// Host-side launchers of the round kernels (internal to libbp_gb300).
+#pragma once
+
+#include "bp_internal.cuh"
+
+namespace bpg {
+
+enum { MODE_LBP = 0, MODE_CAND = 1, MODE_SPLASH = 2 };
+enum { SCHED_LBP = 0, SCHED_RBP = 1, SCHED_RS = 2, SCHED_RNBP = 3 };
+enum { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2 };
+
+void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s);
+void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
+                 int kp, cudaStream_t s);
+void launch_decide(const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
+void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
+void launch_select_rbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
+void launch_select_rs(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
+void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s);
+void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int level_L, cudaStream_t s);
+void launch_stop_running(const DevGraph &g, const DevRun &dr, cudaStream_t s);
+void launch_beliefs(int dtype, const DevGraph &g, const DevRun &dr, int kp, cudaStream_t s);
+void launch_messages(int dtype, const DevGraph &g, const DevRun &dr, int kp, double *out, cudaStream_t s);
+
+}  // namespace bpg

@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Protocol (see the parity readings in the design notes):
+  * FP64 messages: exact replay. GPU and oracle select on their own; frontiers,
+    round counts and convergence must agree, beliefs within 1e-10.
+  * FP32 / BF16 messages: trace-follow. The GPU records its frontier every round;
+    the oracle commits exactly those frontiers with its own FP64 arithmetic for
+    the same number of rounds. Max |belief error| <= 1e-5 (FP32), <= 2e-3 (BF16).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_11469_gb300 import bp, synth
+from tests import _exact
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-10
+TOL_F32 = 1e-5
+TOL_BF16 = 2e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def gpu_run(prob, sched, par=1.0, eps=1e-4, max_rounds=1000, dtype="f32", trace=0, **opts):
+    with bp.Graph(prob) as g:
+        st = g.run(sched, par, eps=eps, max_rounds=max_rounds, msg_dtype=dtype,
+                   record_trace=1 if trace else 0, trace_capacity=trace, **opts)
+        out = {"stats": st, "beliefs": g.beliefs(), "messages": g.messages(),
+               "graph_stats": g.graph_stats()}
+        if trace:
+            out["trace"] = g.trace(sched)
+    return out
+
+
+def all_ones_trace(count, rounds):
+    words = (count + 31) // 32
+    t = np.zeros((rounds, words), dtype=np.uint32)
+    bits = np.zeros(words * 32, dtype=np.uint8)
+    bits[:count] = 1
+    t[:] = np.packbits(bits, bitorder="little").view(np.uint32)
+    return t
+
+
+def follow(prob, sched, res, eps):
+    """Oracle run that commits the GPU's recorded frontiers."""
+    rounds = res["stats"]["rounds"]
+    if sched == "lbp":
+        tr = all_ones_trace(prob.m, rounds)
+        return oracle.run(prob, "lbp", eps=eps, trace_in=tr, trace_rounds=rounds)
+    assert res["trace"].shape[0] == rounds
+    return oracle.run(prob, sched, eps=eps, trace_in=res["trace"], trace_rounds=rounds)
+
+
+# ------------------------------------------------------------ FP64 exact replay
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5)])
+def test_ising10_fp64_exact_replay(sched, par):
+    """10x10 Ising, beta ~ U[-2, 2], seeds 0..9, eps 1e-4, max 1000 rounds."""
+    for seed in range(10):
+        prob = synth.ising_grid(10, 2.0, seed=seed)
+        ref = oracle.run(prob, sched, parallelism=par, eps=1e-4, max_rounds=1000, seed=seed)
+        res = gpu_run(prob, sched, par, 1e-4, 1000, "f64", seed=seed)
+        assert res["stats"]["converged"] == ref["converged"], seed
+        assert res["stats"]["rounds"] == ref["rounds"], seed
+        if ref["converged"]:
+            assert res["stats"]["committed_updates"] == ref["committed_updates"]
+            assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F64, seed
+
+
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5), ("rnbp", 0.1), ("rbp", 0.05),
+                                       ("rbp", 1e-3), ("rs", 0.02), ("rs", 0.2)])
+def test_fp64_exact_replay_trace(sched, par):
+    """Same frontier every round, same state after 60 rounds (ragged 13x11 grid)."""
+    prob = synth.ising_grid(13, 2.0, seed=4, cols=11)
+    T = 60
+    ref = oracle.run(prob, sched, parallelism=par, eps=1e-7, max_rounds=T, seed=5, trace_cap=T)
+    res = gpu_run(prob, sched, par, 1e-7, T, "f64", trace=T if sched != "lbp" else 0, seed=5)
+    assert res["stats"]["rounds"] == ref["rounds"]
+    if sched != "lbp":
+        assert np.array_equal(res["trace"], ref["trace"][:ref["rounds"]])
+    assert res["stats"]["committed_updates"] == ref["committed_updates"]
+    assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F64
+    assert np.abs(res["messages"] - ref["messages"]).max() < TOL_F64
+
+
+@pytest.mark.parametrize("sched,par", [("rbp", 0.1), ("rs", 0.1)])
+def test_ising10_fp64_converging_seeds_rbp_rs(sched, par):
+    for seed in (0, 5):
+        prob = synth.ising_grid(10, 2.0, seed=seed)
+        ref = oracle.run(prob, sched, parallelism=par, eps=1e-4, max_rounds=10000)
+        res = gpu_run(prob, sched, par, 1e-4, 10000, "f64")
+        assert ref["converged"] and res["stats"]["converged"]
+        assert res["stats"]["rounds"] == ref["rounds"]
+        assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F64
+
+
+# ------------------------------------------------------------ trees: exactness
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", TOL_F32)])
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.6), ("rbp", 0.2), ("rs", 0.05)])
+def test_tree_exact_marginals(dtype, tol, sched, par):
+    prob = synth.ising_tree(14, 2.0, seed=3)
+    res = gpu_run(prob, sched, par, 1e-9 if dtype == "f64" else 1e-6, 5000, dtype)
+    assert res["stats"]["converged"]
+    assert np.abs(res["beliefs"] - _exact.brute_force_marginals(prob)).max() < tol
+
+
+def test_chain_forward_backward_fp32():
+    prob = synth.paper_ising(1, 2000, C=10.0, seed=2)
+    res = gpu_run(prob, "lbp", 1.0, 1e-6, 5000, "f32")
+    assert res["stats"]["converged"]
+    assert np.abs(res["beliefs"] - _exact.chain_marginals(prob)).max() < TOL_F32
+
+
+# ------------------------------------------------------------ FP32 / BF16 trace-follow
+@pytest.mark.parametrize("dtype,tol", [("f32", TOL_F32), ("bf16", TOL_BF16)])
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5), ("rnbp", 0.1),
+                                       ("rbp", 0.01), ("rs", 0.01)])
+def test_trace_follow_ising(dtype, tol, sched, par):
+    """37x29 grid (ragged over 256-vertex blocks), beta ~ U[-1.5, 1.5]."""
+    prob = synth.ising_grid(37, 1.5, seed=7, cols=29)
+    T = 400 if sched in ("rbp", "rs") else 150
+    res = gpu_run(prob, sched, par, 1e-4, T, dtype, trace=T, seed=3)
+    ref = follow(prob, sched, res, 1e-4)
+    assert ref["rounds"] == res["stats"]["rounds"]
+    err = np.abs(res["beliefs"] - ref["beliefs"]).max()
+    assert err < tol, err
+
+
+def test_messages_normalised_and_beliefs_consistent():
+    prob = synth.ising_grid(40, 2.5, seed=1)
+    res = gpu_run(prob, "rnbp", 0.5, 1e-4, 300, "f32", seed=2)
+    msg = res["messages"]
+    assert np.abs(msg.sum(axis=1) - 1).max() < 1e-6
+    assert np.abs(res["beliefs"] - _exact.beliefs_eq3(prob, msg)).max() < 1e-6
+
+
+# ------------------------------------------------------------ k-state tables
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", TOL_F32)])
+def test_table_tree_k3_exact(dtype, tol):
+    prob = synth.random_table_graph(9, 3, extra_edges=0, seed=4)
+    res = gpu_run(prob, "lbp", 1.0, 1e-10 if dtype == "f64" else 1e-7, 200, dtype)
+    assert res["stats"]["converged"]
+    assert np.abs(res["beliefs"] - _exact.brute_force_marginals(prob)).max() < tol
+
+
+@pytest.mark.parametrize("k", [3, 5, 8, 13, 32])
+def test_table_loopy_fp64_replay(k):
+    prob = synth.random_table_graph(40, k, extra_edges=25, seed=k, pair_std=0.5)
+    ref = oracle.run(prob, "rnbp", parallelism=0.5, eps=1e-6, max_rounds=50, seed=1, trace_cap=50)
+    res = gpu_run(prob, "rnbp", 0.5, 1e-6, 50, "f64", trace=50, seed=1)
+    assert res["stats"]["rounds"] == ref["rounds"]
+    assert np.array_equal(res["trace"], ref["trace"][:ref["rounds"]])
+    assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F64
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", TOL_F32), ("bf16", TOL_BF16)])
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5)])
+def test_potts_trace_follow(dtype, tol, sched, par):
+    prob = synth.potts_grid(12, 32, seed=2)
+    res = gpu_run(prob, sched, par, 1e-4, 60, dtype, trace=60, seed=4)
+    ref = follow(prob, sched, res, 1e-4)
+    err = np.abs(res["beliefs"] - ref["beliefs"]).max()
+    assert err < tol, err
+
+
+# ------------------------------------------------------------ batches
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.05), ("rs", 0.05)])
+def test_batch_equals_independent_runs(sched, par):
+    """A batch of uneven graphs: every graph converges or stops on its own and
+    matches the oracle run of that graph alone (graph id = its batch index)."""
+    members = [synth.ising_grid(9, 1.0, seed=1), synth.ising_chain(300, 2.0, seed=2),
+               synth.ising_grid(20, 2.0, seed=3, cols=7), synth.ising_tree(50, 1.5, seed=4),
+               synth.ising_grid(3, 0.0, seed=5)]
+    members += [synth.er_batch(1, seed=s, n_min=30, n_max=200).graph(0) for s in range(5)]
+    batch = synth.concat_batch(members)
+    res = gpu_run(batch, sched, par, 1e-5, 500, "f64", seed=9)
+    gstats = res["graph_stats"]
+    for gi, m in enumerate(members):
+        ref = oracle.run(m, sched, parallelism=par, eps=1e-5, max_rounds=500, seed=9, graph_id=gi)
+        assert gstats[gi]["rounds"] == ref["rounds"], gi
+        assert bool(gstats[gi]["converged"]) == ref["converged"], gi
+        v0, v1 = batch.graph_var_offsets[gi], batch.graph_var_offsets[gi + 1]
+        if ref["converged"] or ref["rounds"] < 100:
+            assert np.abs(res["beliefs"][v0:v1] - ref["beliefs"]).max() < 1e-9, gi
+
+
+# ------------------------------------------------------------ edge cases
+def test_edge_cases():
+    # no edges at all
+    row_ptr, col, rev = synth.csr_from_undirected(5, np.zeros(0, np.int64), np.zeros(0, np.int64))
+    un = np.random.default_rng(0).normal(size=10).astype(np.float32)
+    prob = synth.Problem(5, 2, row_ptr, col, rev, un, synth.PAIR_ISING_BETA,
+                         np.zeros(0, np.float32), np.array([0, 5], np.int64))
+    res = gpu_run(prob, "rnbp", 0.5, 1e-4, 10, "f32")
+    e = np.exp(un.astype(np.float64).reshape(5, 2))
+    assert res["stats"]["converged"] and res["stats"]["rounds"] == 0
+    assert np.abs(res["beliefs"] - e / e.sum(1, keepdims=True)).max() < 1e-6
+    # max_rounds = 0: beliefs from uniform messages
+    prob = synth.ising_grid(6, 1.0, seed=1)
+    res = gpu_run(prob, "lbp", 1.0, 1e-4, 0, "f64")
+    ref = oracle.run(prob, "lbp", eps=1e-4, max_rounds=0)
+    assert res["stats"]["rounds"] == 0 and not res["stats"]["converged"]
+    assert np.abs(res["beliefs"] - ref["beliefs"]).max() < 1e-12
+    # beta = 0: converged at round 0
+    prob = synth.ising_grid(6, 0.0, seed=1)
+    res = gpu_run(prob, "rbp", 0.1, 1e-4, 10, "f32")
+    assert res["stats"]["converged"] and res["stats"]["rounds"] == 0
+    # single edge: one round
+    row_ptr, col, rev = synth.csr_from_undirected(2, np.array([0]), np.array([1]))
+    prob = synth.Problem(2, 2, row_ptr, col, rev, np.array([-0.3, 0.3, 0.7, -0.7], np.float32),
+                         synth.PAIR_ISING_BETA, np.array([1.1, 1.1], np.float32),
+                         np.array([0, 2], np.int64))
+    res = gpu_run(prob, "lbp", 1.0, 1e-12, 10, "f64")
+    assert res["stats"]["converged"] and res["stats"]["rounds"] == 1
+    assert np.abs(res["beliefs"] - _exact.brute_force_marginals(prob)).max() < 1e-14
+
+
+def test_errors_on_device():
+    prob = synth.ising_grid(4, 1.0, seed=0)
+    h = bp.bp_create_graph(prob.n, 2, prob.row_ptr, prob.col, prob.rev)
+    try:
+        with pytest.raises(bp.BPError) as ei:
+            bp.bp_run(h, "lbp", 1.0, 1e-4, 10)
+        assert ei.value.code == bp.BP_ERR_NO_POTENTIALS
+        with pytest.raises(bp.BPError) as ei:
+            bp.bp_get_beliefs(h)
+        assert ei.value.code == bp.BP_ERR_NO_RESULT
+        bad = prob.pair_log.copy()
+        bad[0] += 1.0
+        with pytest.raises(bp.BPError) as ei:
+            bp.bp_set_potentials(h, prob.unary_log, 0, bad)
+        assert ei.value.code == bp.BP_ERR_NONFINITE
+        un = prob.unary_log.copy()
+        un[3] = np.nan
+        with pytest.raises(bp.BPError) as ei:
+            bp.bp_set_potentials(h, un, 0, prob.pair_log)
+        assert ei.value.code == bp.BP_ERR_NONFINITE
+        bp.bp_set_potentials(h, prob.unary_log, 0, prob.pair_log)
+        for args in ((7, 1.0, 1e-4, 10), ("rbp", 0.0, 1e-4, 10), ("lbp", 1.0, 0.0, 10),
+                     ("lbp", 1.0, 1e-4, -1)):
+            with pytest.raises(bp.BPError) as ei:
+                bp.bp_run(h, *args)
+            assert ei.value.code == bp.BP_ERR_INVALID_ARG
+        st = bp.bp_run(h, "lbp", 1.0, 1e-4, 10)
+        assert st["status"] == 0
+    finally:
+        bp.bp_destroy_graph(h)
+
+
+def test_time_budget_stops_cleanly():
+    prob = synth.ising_grid(60, 3.0, seed=1)
+    with bp.Graph(prob) as g:
+        st = g.run("rbp", 1e-4, eps=1e-12, max_rounds=10_000_000, time_budget_ms=50.0)
+        assert st["status"] == bp.BP_ERR_TIMEOUT and not st["converged"]
+        b = g.beliefs()
+        assert np.all(np.isfinite(b)) and np.allclose(b.sum(1), 1.0)
+        st2 = g.run("lbp", 1.0, eps=1e-4, max_rounds=5)
+        assert st2["status"] == 0 and st2["rounds"] == 5
