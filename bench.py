@@ -10,8 +10,10 @@ RBP/RS ceil(1000/p)), beliefs included.
 
 Metric: committed message updates per second (messages written by frontier
 commits) over the timed steps, with the per-schedule converged fraction and
-batch time-to-convergence reported beside it. The message-update kernel's
-roofline is taken from CUDA events recorded inside the captured round graph.
+batch time-to-convergence reported beside it. The timed steps replay captured
+CUDA graphs; one further step of the same workload runs with CUDA events
+between the kernels of every round, which gives the message-update kernel's
+duration for the roofline and the share of each phase.
 
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload (the method has no other reference implementation).
@@ -209,7 +211,7 @@ def main():
         return out
 
     for _ in range(max(args.warmup, 0)):
-        one_step(1)
+        one_step(0)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -223,7 +225,7 @@ def main():
     for i in range(args.steps):
         flush.zero_()                     # L2 flush between timed steps (outside the events)
         starts[i].record(stream)
-        results.append(one_step(1))
+        results.append(one_step(0))
         ends[i].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -245,17 +247,22 @@ def main():
         committed, evals, launches = (int(x) for x in t.tolist())
     value = committed / (total_ms / 1e3)
 
-    # roofline of the message-update (full evaluation) kernel
+    # Roofline of the message-update (full evaluation) kernel: one more step of
+    # the same workload with per-phase CUDA events on the launching stream.
+    flush.zero_()
+    prof_step = one_step(1)
+    torch.cuda.synchronize()
     alg_bytes, eval_ms, eval_launches = 0.0, 0.0, 0
     phase = {"eval_ms": 0.0, "decide_ms": 0.0, "frontier_ms": 0.0}
+    for sched, p, st, pr, gst in prof_step:
+        alg_bytes += BYTES_PER_MSG[sched] * pr["full_evals"] + BYTES_PER_VERTEX * pr["active_vertices"]
+        eval_ms += pr["eval_ms"]
+        eval_launches += pr["eval_launches"]
+        for k in phase:
+            phase[k] += pr[k]
     per_sched = {}
     for step in results:
         for sched, p, st, pr, gst in step:
-            alg_bytes += BYTES_PER_MSG[sched] * pr["full_evals"] + BYTES_PER_VERTEX * pr["active_vertices"]
-            eval_ms += pr["eval_ms"]
-            eval_launches += pr["eval_launches"]
-            for k in phase:
-                phase[k] += pr[k]
             key = f"{sched}_p{p}"
             d = per_sched.setdefault(key, {"ms": [], "converged_fraction": None, "median_rounds": None,
                                            "committed_updates": 0})
@@ -324,7 +331,7 @@ def main():
                        "parallelism": f"dp{world}" if world > 1 else "single"},
             "candidate_evals_per_s": evals / (total_ms / 1e3),
             "schedules": per_sched,
-            "phase_ms_per_step": {k: v / args.steps for k, v in phase.items()},
+            "profiled_step_phase_ms": phase,
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": int(launches), "clocks": clk,
         }

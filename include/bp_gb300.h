@@ -58,8 +58,15 @@ typedef enum {
     BP_RNBP = 3   /* residual >= eps, then a Philox Bernoulli(p) filter (Section IV-A) */
 } bp_schedule;
 
-/* Storage type of the log-domain messages (arithmetic is FP32, or FP64 for BP_F64). */
-typedef enum { BP_F64 = 0, BP_F32 = 1, BP_BF16 = 2 } bp_msg_dtype;
+/* Storage type of the log-domain messages (arithmetic is FP32, or FP64 for BP_F64).
+ * Binary Ising messages (k = 2, BP_PAIR_ISING_BETA) are stored as one log-odds
+ * value u = log m(1) - log m(0); other messages as k values log m(x).
+ * BP_Q16 (binary Ising only) stores u as a signed 16-bit integer q with
+ * u = q * s, s = (float)(2 max_e |beta_e| / 32767): an Ising message satisfies
+ * |u| <= 2 |beta|, so the range is never exceeded and the step is uniform.
+ * With BF16 and Q16 a residual compares rounded candidates with the stored
+ * messages, so an unchanged stored value has residual 0. */
+typedef enum { BP_F64 = 0, BP_F32 = 1, BP_BF16 = 2, BP_Q16 = 3 } bp_msg_dtype;
 
 /* Pairwise potential layouts, as natural logs theta = log psi (Eq. 1). */
 typedef enum {
@@ -103,12 +110,13 @@ typedef struct {
 } bp_options;
 
 /* Phase timings and launch counts of the last bp_run. The timings are filled
- * only when the run had profile = 1: CUDA events recorded inside the captured
- * round graph on the run's stream bracket the evaluation kernel (Eq. 2 + Eq. 4
- * + convergence reduction), the per-graph decision, and the frontier work
- * (selection, splash, commit); rounds after every graph had stopped are left
- * out. Profiling adds event nodes between kernels, so a profiled run is slightly
- * slower than an unprofiled one. */
+ * only when the run had profile = 1: the rounds are then launched directly
+ * (not through a captured CUDA graph) with CUDA events on the run's stream
+ * between the evaluation kernel (Eq. 2 + Eq. 4 + convergence reduction), the
+ * per-graph decision and the frontier work (selection, splash, commit);
+ * rounds after every graph had stopped are left out. A profiled run pays the
+ * direct-launch overhead, so its wall time is above an unprofiled run's; the
+ * kernel durations themselves are unaffected. */
 typedef struct {
     int64_t kernel_launches;   /* kernels launched by bp_run (graph nodes replayed + direct) */
     int64_t eval_launches;     /* timed full-evaluation launches (profile = 1) */

@@ -40,7 +40,8 @@ class OrcParams(ctypes.Structure):
                 ("high_p", ctypes.c_double), ("ratio_threshold", ctypes.c_double),
                 ("splash_depth", ctypes.c_int32), ("rs_roots_mode", ctypes.c_int32),
                 ("trace_in", ctypes.c_void_p), ("trace_rounds", ctypes.c_int32),
-                ("trace_out", ctypes.c_void_p), ("trace_cap", ctypes.c_int32)]
+                ("trace_out", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("q16_scale", ctypes.c_double)]
 
 
 class OrcStats(ctypes.Structure):
@@ -108,9 +109,10 @@ class _Bound:
 
 def run(prob, schedule="lbp", parallelism=1.0, eps=1e-4, max_rounds=1000, seed=0,
         graph_id=0, high_p=1.0, ratio_threshold=0.9, splash_depth=2, rs_roots_mode=0,
-        trace_in=None, trace_rounds=0, trace_cap=0):
+        trace_in=None, trace_rounds=0, trace_cap=0, storage="f64", q16_scale=0.0):
     """Run one graph (prob must hold a single graph). Returns a dict with beliefs
-    [n, k], messages [M, k] (probability domain), stats and the selected trace."""
+    [n, k], messages [M, k] (probability domain), stats and the selected trace.
+    storage: "f64" (exact), "bf16" or "q16" (emulated 16-bit message storage)."""
     sched = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     b = _Bound(prob)
     n, k, m = int(prob.n), int(prob.k), int(b.col.shape[0])
@@ -124,7 +126,8 @@ def run(prob, schedule="lbp", parallelism=1.0, eps=1e-4, max_rounds=1000, seed=0
     params = OrcParams(sched, float(parallelism), float(eps), int(max_rounds), int(seed),
                        int(graph_id), float(high_p), float(ratio_threshold), int(splash_depth),
                        int(rs_roots_mode), _ptr(tin) if tin is not None else None,
-                       int(trace_rounds), _ptr(tout) if trace_cap > 0 else None, int(trace_cap))
+                       int(trace_rounds), _ptr(tout) if trace_cap > 0 else None, int(trace_cap),
+                       {"f64": 0, "bf16": 1, "q16": 2}[storage], float(q16_scale))
     beliefs = np.zeros(n * k + 1, dtype=np.float64)
     msgs = np.zeros(m * k + 1, dtype=np.float64)
     st = OrcStats()

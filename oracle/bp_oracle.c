@@ -74,6 +74,9 @@ typedef struct {
     int32_t trace_rounds;
     uint32_t *trace_out;     /* optional: frontier bitmask per round, as selected */
     int32_t trace_cap;
+    int32_t storage;         /* 0: exact FP64; 1: BF16 rounding of the stored log value;
+                                2: 16-bit fixed-point log-odds (Ising only) */
+    double q16_scale;        /* storage 2: log-odds step of one integer unit */
 } orc_params;
 
 typedef struct {
@@ -211,6 +214,51 @@ static void message_update(const orc_model *md, const double *msg, int64_t e, do
         c[b] /= z;
 }
 
+/* Storage emulation. Messages may be kept in a 16-bit format; every value that
+ * is committed then goes through the same rounding as the stored word, and
+ * residuals compare rounded candidates with rounded current messages, so a
+ * message whose stored value does not change has residual 0.
+ *   BF16: the stored quantity is rounded to float, then to bfloat16 (round to
+ *   nearest, ties to even). For the Ising layout (k = 2, beta potentials) the
+ *   stored quantity is the log-odds u = log m(1) - log m(0); otherwise it is
+ *   log m(x) of each state (not renormalised after rounding).
+ *   Q16: Ising log-odds rounded to the nearest multiple of q16_scale, clamped
+ *   to +-32767 multiples. */
+static double round_bf16(double v)
+{
+    float f = (float)v;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
+static void store_round(const orc_problem *pb, const orc_params *pr, double *c)
+{
+    int32_t k = pb->k;
+    if (pr->storage == 0)
+        return;
+    if (pb->pair_kind == ORC_PAIR_ISING) {
+        double u = log(c[1]) - log(c[0]);
+        if (pr->storage == 1) {
+            u = round_bf16(u);
+        } else {
+            double q = nearbyint(u / pr->q16_scale);
+            if (q > 32767.0)
+                q = 32767.0;
+            if (q < -32767.0)
+                q = -32767.0;
+            u = q * pr->q16_scale;
+        }
+        c[1] = 1.0 / (1.0 + exp(-u));
+        c[0] = 1.0 / (1.0 + exp(u));
+    } else {
+        for (int32_t x = 0; x < k; ++x)
+            c[x] = exp(round_bf16(log(c[x])));
+    }
+}
+
 /* Eq. 4 with the max-norm. */
 static double residual(const double *cand, const double *cur, int32_t k)
 {
@@ -223,13 +271,15 @@ static double residual(const double *cand, const double *cur, int32_t k)
     return r;
 }
 
-/* Candidates and residuals of every message from the current messages. */
-static void evaluate_all(const orc_model *md, const double *msg, double *cand, double *r)
+/* Candidates (as they would be stored) and residuals of every message. */
+static void evaluate_all(const orc_model *md, const orc_params *pr, const double *msg, double *cand,
+                         double *r)
 {
     const orc_problem *pb = md->pb;
     int32_t k = pb->k;
     for (int64_t e = 0; e < pb->m; ++e) {
         message_update(md, msg, e, cand + e * k);
+        store_round(pb, pr, cand + e * k);
         r[e] = residual(cand + e * k, msg + e * k, k);
     }
 }
@@ -369,6 +419,8 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
     /* Section II-A: messages start uniform. */
     for (size_t q = 0; q < (size_t)m * (size_t)k; ++q)
         msg[q] = 1.0 / (double)k;
+    for (int64_t e = 0; e < m; ++e)
+        store_round(pb, pr, msg + e * k);
 
     int follow = (pr->trace_in != NULL);
     int64_t sel_count = (pr->schedule == ORC_RS) ? n : m;
@@ -380,7 +432,7 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
 
     for (;;) {
         /* Evaluate: candidates and residuals of all messages (Eq. 2, Eq. 4). */
-        evaluate_all(&md, msg, cand, r);
+        evaluate_all(&md, pr, msg, cand, r);
         s.candidate_evals += m;
         double rmax = 0.0;
         int64_t n_t = 0;
@@ -446,6 +498,7 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
                         continue;
                     for (int64_t e = pb->row_ptr[v]; e < pb->row_ptr[v + 1]; ++e) {
                         message_update(&md, msg, e, cand + e * k);
+                        store_round(pb, pr, cand + e * k);
                         ++touched;
                     }
                 }
@@ -518,11 +571,13 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
 int orc_evaluate(const orc_problem *pb, const double *msg, double *cand, double *r)
 {
     orc_model md;
+    orc_params exact;
+    memset(&exact, 0, sizeof(exact));
     if (model_init(&md, pb) != 0) {
         model_free(&md);
         return -1;
     }
-    evaluate_all(&md, msg, cand, r);
+    evaluate_all(&md, &exact, msg, cand, r);
     model_free(&md);
     return 0;
 }

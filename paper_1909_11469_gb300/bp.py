@@ -29,8 +29,14 @@ BP_ERR_NO_RESULT = -9
 
 BP_LBP, BP_RBP, BP_RS, BP_RNBP = 0, 1, 2, 3
 SCHEDULES = {"lbp": BP_LBP, "rbp": BP_RBP, "rs": BP_RS, "rnbp": BP_RNBP}
-BP_F64, BP_F32, BP_BF16 = 0, 1, 2
-DTYPES = {"f64": BP_F64, "f32": BP_F32, "bf16": BP_BF16}
+BP_F64, BP_F32, BP_BF16, BP_Q16 = 0, 1, 2, 3
+DTYPES = {"f64": BP_F64, "f32": BP_F32, "bf16": BP_BF16, "q16": BP_Q16}
+
+
+def q16_scale(pair_log) -> float:
+    """The Q16 log-odds step the library uses for Ising potentials pair_log."""
+    bmax = float(np.abs(np.asarray(pair_log, dtype=np.float64)).max()) if len(pair_log) else 0.0
+    return float(np.float32(2.0 * bmax / 32767.0)) if bmax > 0 else float(np.float32(1.0 / 32767.0))
 BP_PAIR_ISING_BETA, BP_PAIR_TABLE, BP_PAIR_SHARED = 0, 1, 2
 
 

@@ -60,19 +60,12 @@ template <typename T> void dfree(T *&p)
 
 struct CachedGraph {
     RunParams rp;
-    int dtype, rounds, kp, profile;
+    int dtype, rounds, kp, epm;
     int64_t kernels;                    // kernel nodes in the graph
     cudaGraphExec_t exec;
-    std::vector<cudaEvent_t> events;    // profile: 4 per round
 };
 
-void destroy_cached(CachedGraph &c)
-{
-    cudaGraphExecDestroy(c.exec);
-    for (auto ev : c.events)
-        cudaEventDestroy(ev);
-    c.events.clear();
-}
+void destroy_cached(CachedGraph &c) { cudaGraphExecDestroy(c.exec); }
 
 }  // namespace
 
@@ -88,11 +81,13 @@ struct bp_graph {
     // potentials
     int pair_kind = -1;
     bool has_pot = false;
+    float qscale = 1.0f;   // Q16 log-odds step: 2 max|beta| / 32767
     float *d_unary = nullptr, *d_udiff32 = nullptr, *d_q32 = nullptr, *d_pair = nullptr,
           *d_psi_shared = nullptr;
     double *d_udiff64 = nullptr, *d_q64 = nullptr;
     // run buffers
     int buf_dtype = -1;
+    int buf_epm = 0;
     void *d_msg[2] = {nullptr, nullptr};
     void *d_resid = nullptr, *d_vres = nullptr;
     int8_t *d_level = nullptr;
@@ -106,6 +101,7 @@ struct bp_graph {
     int32_t *h_running = nullptr;   // pinned
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> prof_events;   // profile mode: 4 per round of a chunk
     std::vector<CachedGraph> cache;
     // last result
     bool has_result = false;
@@ -136,6 +132,9 @@ void free_run_buffers(bp_graph *g)
     g->buf_dtype = -1;
 }
 
+// Binary Ising messages are stored as one log-odds value, others as k logs.
+int epm_of(const bp_graph *g) { return (g->k == 2 && g->pair_kind == BP_PAIR_ISING_BETA) ? 1 : g->k; }
+
 DevGraph dev_graph(const bp_graph *g)
 {
     DevGraph d;
@@ -143,6 +142,8 @@ DevGraph dev_graph(const bp_graph *g)
     d.k = g->k;
     d.G = g->G;
     d.M = (int32_t)g->M;
+    d.epm = epm_of(g);
+    d.qscale = g->qscale;
     d.row_ptr = g->d_row_ptr;
     d.col = g->d_col;
     d.rev = g->d_rev;
@@ -177,14 +178,15 @@ DevRun dev_run(const bp_graph *g)
     return r;
 }
 
-size_t dtype_size(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
+size_t dtype_size(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }   // BF16, Q16: 2
 
 int ensure_msg_buffers(bp_graph *g, int dtype)
 {
-    if (g->buf_dtype == dtype)
+    if (g->buf_dtype == dtype && g->buf_epm == epm_of(g))
         return BP_OK;
     free_run_buffers(g);
-    size_t elems = (size_t)g->M * (size_t)g->k;
+    g->buf_epm = epm_of(g);
+    size_t elems = (size_t)g->M * (size_t)g->buf_epm;
     size_t es = dtype_size(dtype);
     size_t rs = dtype == DT_F64 ? 8 : 4;
     int rc;
@@ -367,10 +369,10 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
 
 // Returns the instantiated graph of `rounds` rounds for these parameters,
 // capturing it on first use.
-int get_graph_exec(bp_graph *g, int dtype, const RunParams &rp, int rounds, int profile, CachedGraph **out)
+int get_graph_exec(bp_graph *g, int dtype, const RunParams &rp, int rounds, CachedGraph **out)
 {
     for (auto &c : g->cache) {
-        if (c.dtype == dtype && c.rounds == rounds && c.kp == g->kp && c.profile == profile &&
+        if (c.dtype == dtype && c.rounds == rounds && c.kp == g->kp && c.epm == epm_of(g) &&
             memcmp(&c.rp, &rp, sizeof(rp)) == 0) {
             *out = &c;
             return BP_OK;
@@ -385,32 +387,21 @@ int get_graph_exec(bp_graph *g, int dtype, const RunParams &rp, int rounds, int 
     c.dtype = dtype;
     c.rounds = rounds;
     c.kp = g->kp;
-    c.profile = profile;
+    c.epm = epm_of(g);
     c.kernels = 0;
-    if (profile) {
-        c.events.resize((size_t)rounds * 4);
-        for (auto &ev : c.events)
-            BP_CK(cudaEventCreate(&ev));
-    }
     DevGraph dg = dev_graph(g);
     DevRun dr = dev_run(g);
     BP_CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int r = 0; r < rounds; ++r)
-        c.kernels += record_round(g, dtype, dg, dr, rp, g->cap_stream, profile ? &c.events[(size_t)r * 4] : nullptr);
+        c.kernels += record_round(g, dtype, dg, dr, rp, g->cap_stream, nullptr);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
-    if (e != cudaSuccess) {
-        for (auto ev : c.events)
-            cudaEventDestroy(ev);
+    if (e != cudaSuccess)
         return cuda_fail(e, "cudaStreamEndCapture");
-    }
     e = cudaGraphInstantiate(&c.exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-        for (auto ev : c.events)
-            cudaEventDestroy(ev);
+    if (e != cudaSuccess)
         return cuda_fail(e, "cudaGraphInstantiate");
-    }
     g->cache.push_back(c);
     *out = &g->cache.back();
     return BP_OK;
@@ -532,7 +523,13 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
         BP_CK(cudaMemcpy(g->d_udiff64, ud.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
         BP_CK(cudaMemcpy(g->d_udiff32, ud32.data(), sizeof(float) * (size_t)n, cudaMemcpyHostToDevice));
     }
+    g->qscale = 1.0f / 32767.0f;
     if (pair_kind == BP_PAIR_ISING_BETA) {
+        double bmax = 0.0;
+        for (int64_t e = 0; e < M; ++e)
+            bmax = std::max(bmax, std::fabs((double)pair_log[e]));
+        if (bmax > 0.0)
+            g->qscale = (float)(2.0 * bmax / 32767.0);
         std::vector<double> q64((size_t)M);
         std::vector<float> q32((size_t)M);
         for (int64_t e = 0; e < M; ++e) {
@@ -588,8 +585,10 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         opt = *opt_in;
     else
         bp_default_options(&opt);
-    if (opt.msg_dtype < 0 || opt.msg_dtype > 2)
+    if (opt.msg_dtype < 0 || opt.msg_dtype > 3)
         return fail(BP_ERR_INVALID_ARG, "unknown msg_dtype");
+    if (opt.msg_dtype == BP_Q16 && epm_of(g) != 1)
+        return fail(BP_ERR_UNSUPPORTED, "Q16 storage needs the binary Ising layout");
     if (!(opt.high_p >= 0.0) || !std::isfinite(opt.high_p) || !std::isfinite(opt.ratio_threshold))
         return fail(BP_ERR_INVALID_ARG, "bad high_p or ratio_threshold");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
@@ -652,18 +651,31 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     // rest of their kernels into no-ops. The host polls the running count once
     // per replay.
     for (;;) {
-        CachedGraph *cg = nullptr;
-        if ((rc = get_graph_exec(g, dtype, rp, chunk, opt.profile ? 1 : 0, &cg)) != BP_OK)
-            return rc;
-        BP_CK(cudaGraphLaunch(cg->exec, s));
+        if (opt.profile) {
+            // direct launches with events between the phases of every round
+            if (g->prof_events.size() < (size_t)chunk * 4) {
+                size_t old = g->prof_events.size();
+                g->prof_events.resize((size_t)chunk * 4);
+                for (size_t q = old; q < g->prof_events.size(); ++q)
+                    BP_CK(cudaEventCreate(&g->prof_events[q]));
+            }
+            for (int r = 0; r < chunk; ++r)
+                kernels += record_round(g, dtype, dg, dr, rp, s, &g->prof_events[(size_t)r * 4]);
+            BP_CK(cudaGetLastError());
+        } else {
+            CachedGraph *cg = nullptr;
+            if ((rc = get_graph_exec(g, dtype, rp, chunk, &cg)) != BP_OK)
+                return rc;
+            BP_CK(cudaGraphLaunch(cg->exec, s));
+            kernels += cg->kernels;
+        }
         rounds_launched += chunk;
-        kernels += cg->kernels;
         BP_CK(cudaMemcpyAsync(g->h_running, g->d_running, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         BP_CK(cudaStreamSynchronize(s));
         if (opt.profile) {
             for (int r = 0; r < chunk; ++r) {
                 float a = 0.f, b = 0.f, c = 0.f;
-                cudaEvent_t *ev = &cg->events[(size_t)r * 4];
+                cudaEvent_t *ev = &g->prof_events[(size_t)r * 4];
                 BP_CK(cudaEventElapsedTime(&a, ev[0], ev[1]));
                 BP_CK(cudaEventElapsedTime(&b, ev[1], ev[2]));
                 BP_CK(cudaEventElapsedTime(&c, ev[2], ev[3]));
@@ -877,6 +889,8 @@ void bp_destroy_graph(bp_graph *g)
         cudaEventDestroy(g->ev0);
     if (g->ev1)
         cudaEventDestroy(g->ev1);
+    for (auto ev : g->prof_events)
+        cudaEventDestroy(ev);
     delete g;
 }
 

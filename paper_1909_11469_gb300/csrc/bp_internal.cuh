@@ -34,6 +34,8 @@ struct GState {
 struct DevGraph {
     int32_t n, k, G;
     int32_t M;
+    int32_t epm;              // stored elements per message: 1 (binary log-odds) or k
+    float qscale;             // Q16 storage: log-odds per integer step
     const int32_t *row_ptr;   // [n+1]
     const int32_t *col;       // [M]
     const int32_t *rev;       // [M]
@@ -83,25 +85,41 @@ struct DevRun {
 };
 
 // ---------------------------------------------------------------------------
-// Storage traits: message element type S, arithmetic type A.
+// Storage traits: message element type S, arithmetic type A. sc is the Q16
+// step (log-odds per integer unit); the floating formats ignore it.
 template <typename S> struct Store;
 template <> struct Store<double> {
     using A = double;
-    static __device__ __forceinline__ double ld(const double *p) { return *p; }
-    static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
-    static __device__ __forceinline__ double quant(double v) { return v; }
+    static __device__ __forceinline__ double ld(const double *p, float) { return *p; }
+    static __device__ __forceinline__ void st(double *p, double v, float) { *p = v; }
+    static __device__ __forceinline__ double quant(double v, float) { return v; }
 };
 template <> struct Store<float> {
     using A = float;
-    static __device__ __forceinline__ float ld(const float *p) { return *p; }
-    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
-    static __device__ __forceinline__ float quant(float v) { return v; }
+    static __device__ __forceinline__ float ld(const float *p, float) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
+    static __device__ __forceinline__ float quant(float v, float) { return v; }
 };
 template <> struct Store<__nv_bfloat16> {
     using A = float;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
-    static __device__ __forceinline__ float quant(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float quant(float v, float)
+    {
+        return __bfloat162float(__float2bfloat16_rn(v));
+    }
+};
+// Q16: binary log-odds as a signed 16-bit multiple of sc, |q| <= 32767.
+template <> struct Store<int16_t> {
+    using A = float;
+    static __device__ __forceinline__ float code(float v, float sc)
+    {
+        float q = rintf(__fdividef(v, sc));
+        return fminf(fmaxf(q, -32767.0f), 32767.0f);
+    }
+    static __device__ __forceinline__ float ld(const int16_t *p, float sc) { return (float)*p * sc; }
+    static __device__ __forceinline__ void st(int16_t *p, float v, float sc) { *p = (int16_t)code(v, sc); }
+    static __device__ __forceinline__ float quant(float v, float sc) { return code(v, sc) * sc; }
 };
 
 // Residual element type: double for FP64 messages, float otherwise.

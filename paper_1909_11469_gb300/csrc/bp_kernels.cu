@@ -15,6 +15,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace bpg {
 
 constexpr int BLOCK = 256;
@@ -64,22 +66,22 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
 #pragma unroll
             for (int c = 0; c < CACHE; ++c) {
                 if (c < deg) {
-                    uin[c] = Store<S>::ld(cur + g.rev[beg + c]);
+                    uin[c] = Store<S>::ld(cur + g.rev[beg + c], g.qscale);
                     h += uin[c];
                 }
             }
             for (int e = beg + CACHE; e < end; ++e)
-                h += Store<S>::ld(cur + g.rev[e]);
+                h += Store<S>::ld(cur + g.rev[e], g.qscale);
             RT *R = (RT *)dr.resid;
             auto one = [&](int e, A u_in) {
                 A unew = ising_logodds(q[e], h - u_in);
                 if (MODE == MODE_SPLASH) {
-                    Store<S>::st(out + e, unew);
+                    Store<S>::st(out + e, unew, g.qscale);
                     return;
                 }
-                A uq = Store<S>::quant(unew);
-                A r = fabs(m_sigmoid(uq) - m_sigmoid(Store<S>::ld(cur + e)));
-                Store<S>::st(out + e, unew);
+                A uq = Store<S>::quant(unew, g.qscale);
+                A r = fabs(m_sigmoid(uq) - m_sigmoid(Store<S>::ld(cur + e, g.qscale)));
+                Store<S>::st(out + e, unew, g.qscale);
                 if (MODE == MODE_CAND)
                     R[e] = (RT)r;
                 double rd = (double)r;
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
                 if (c < deg)
                     one(beg + c, uin[c]);
             for (int e = beg + CACHE; e < end; ++e)
-                one(e, Store<S>::ld(cur + g.rev[e]));
+                one(e, Store<S>::ld(cur + g.rev[e], g.qscale));
         }
     }
     if (MODE != MODE_SPLASH)
@@ -179,10 +181,10 @@ __global__ void __launch_bounds__(BLOCK) k_eval_gen(DevGraph g, DevRun dr, RunPa
         A Sx = lane_ok ? (A)g.unary[(size_t)i * k + lane] : (A)0;
         for (int e = beg; e < end; ++e)
             if (lane_ok)
-                Sx += Store<S>::ld(cur + (size_t)g.rev[e] * k + lane);
+                Sx += Store<S>::ld(cur + (size_t)g.rev[e] * k + lane, g.qscale);
         RT *R = (RT *)dr.resid;
         for (int e = beg; e < end; ++e) {
-            A lin = lane_ok ? Store<S>::ld(cur + (size_t)g.rev[e] * k + lane) : (A)0;
+            A lin = lane_ok ? Store<S>::ld(cur + (size_t)g.rev[e] * k + lane, g.qscale) : (A)0;
             A cav = lane_ok ? Sx - lin : (A)(-1e30);
             A mx = grp_max<KP>(gm, cav);
             A a = lane_ok ? m_exp(cav - mx) : (A)0;
@@ -206,14 +208,14 @@ __global__ void __launch_bounds__(BLOCK) k_eval_gen(DevGraph g, DevRun dr, RunPa
             lnew = lnew > log_floor<A>() ? lnew : log_floor<A>();
             if (MODE == MODE_SPLASH) {
                 if (lane_ok)
-                    Store<S>::st(out + (size_t)e * k + lane, lnew);
+                    Store<S>::st(out + (size_t)e * k + lane, lnew, g.qscale);
                 continue;
             }
-            A pn = lane_ok ? m_exp(Store<S>::quant(lnew)) : (A)0;
-            A po = lane_ok ? m_exp(Store<S>::ld(cur + (size_t)e * k + lane)) : (A)0;
+            A pn = lane_ok ? m_exp(Store<S>::quant(lnew, g.qscale)) : (A)0;
+            A po = lane_ok ? m_exp(Store<S>::ld(cur + (size_t)e * k + lane, g.qscale)) : (A)0;
             A r = grp_max<KP>(gm, fabs(pn - po));
             if (lane_ok)
-                Store<S>::st(out + (size_t)e * k + lane, lnew);
+                Store<S>::st(out + (size_t)e * k + lane, lnew, g.qscale);
             if (MODE == MODE_CAND && lane == 0)
                 R[e] = (RT)r;
             double rd = (double)r;
@@ -338,13 +340,13 @@ __global__ void __launch_bounds__(BLOCK) k_commit_rnbp(DevGraph g, DevRun dr, Ru
             S *dst = (S *)dr.msg[0];
             const S *src = (const S *)dr.msg[1];
             const int e0 = g.ge_off[gg];
-            const int k = g.k;
+            const int epm = g.epm;
             const bool tr = rp.record_trace && st.rounds <= rp.trace_capacity;
             for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
                 if ((double)R[e] >= rp.eps && rnbp_pick(rp, (uint32_t)(e - e0), (uint32_t)st.rounds,
                                                         (uint32_t)gg, st)) {
-                    for (int x = 0; x < k; ++x)
-                        dst[(size_t)e * k + x] = src[(size_t)e * k + x];
+                    for (int x = 0; x < epm; ++x)
+                        dst[(size_t)e * epm + x] = src[(size_t)e * epm + x];
                     ++c;
                     if (tr)
                         atomicOr(&dr.trace[(size_t)(st.rounds - 1) * rp.trace_words + (e >> 5)],
@@ -391,9 +393,9 @@ __global__ void __launch_bounds__(BLOCK) k_splash_commit(DevGraph g, DevRun dr, 
             valid = true;
             S *dst = (S *)dr.msg[0];
             const S *src = (const S *)dr.msg[1];
-            const int k = g.k;
+            const int epm = g.epm;
             const int beg = g.row_ptr[i], end = g.row_ptr[i + 1];
-            for (int t = beg * k; t < end * k; ++t)
+            for (int t = beg * epm; t < end * epm; ++t)
                 dst[t] = src[t];
             c = (unsigned int)(end - beg);
         }
@@ -408,8 +410,8 @@ __global__ void k_init_msgs(S *a, S *b, size_t count, double value)
 {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
          t += (size_t)gridDim.x * blockDim.x) {
-        Store<S>::st(a + t, (typename Store<S>::A)value);
-        Store<S>::st(b + t, (typename Store<S>::A)value);
+        Store<S>::st(a + t, (typename Store<S>::A)value, 1.0f);
+        Store<S>::st(b + t, (typename Store<S>::A)value, 1.0f);
     }
 }
 
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(BLOCK) k_beliefs_bin(DevGraph g, DevRun dr)
     const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
     double h = g.udiff64[i];
     for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
-        h += (double)Store<S>::ld(cur + g.rev[e]);
+        h += (double)Store<S>::ld(cur + g.rev[e], g.qscale);
     dr.beliefs[2 * (size_t)i + 1] = 1.0 / (1.0 + exp(-h));
     dr.beliefs[2 * (size_t)i] = 1.0 / (1.0 + exp(h));
 }
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(BLOCK) k_beliefs_gen(DevGraph g, DevRun dr)
     double s = ok ? (double)g.unary[(size_t)i * k + lane] : -1e300;
     for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
         if (ok)
-            s += (double)Store<S>::ld(cur + (size_t)g.rev[e] * k + lane);
+            s += (double)Store<S>::ld(cur + (size_t)g.rev[e] * k + lane, g.qscale);
     const unsigned gm = grp_mask<KP>();
     double mx = grp_max<KP>(gm, s);
     double w = ok ? exp(s - mx) : 0.0;
@@ -498,7 +500,7 @@ __global__ void __launch_bounds__(BLOCK) k_messages_bin(DevGraph g, DevRun dr, d
         return;
     const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
     for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
-        double u = (double)Store<S>::ld(cur + e);
+        double u = (double)Store<S>::ld(cur + e, g.qscale);
         out[2 * (size_t)e + 1] = 1.0 / (1.0 + exp(-u));
         out[2 * (size_t)e] = 1.0 / (1.0 + exp(u));
     }
@@ -516,55 +518,72 @@ __global__ void __launch_bounds__(BLOCK) k_messages_gen(DevGraph g, DevRun dr, d
     const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
     if (lane < k)
         for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
-            out[(size_t)e * k + lane] = exp((double)Store<S>::ld(cur + (size_t)e * k + lane));
+            out[(size_t)e * k + lane] = exp((double)Store<S>::ld(cur + (size_t)e * k + lane, g.qscale));
 }
 
 // --------------------------------------------------------------------------
 // Host-side launchers.
 static inline int blocks_for(int n, int per_block) { return (n + per_block - 1) / per_block; }
 
+// Calls BODY with S bound to the storage type of dtype (Q16 only for the
+// binary Ising layout, which the runtime enforces).
+#define BPG_DISPATCH4(dtype, BODY)                                   \
+    switch (dtype) {                                                 \
+    case DT_F64: { using S = double; BODY; } break;                  \
+    case DT_F32: { using S = float; BODY; } break;                   \
+    case DT_BF16: { using S = __nv_bfloat16; BODY; } break;          \
+    default: { using S = int16_t; BODY; } break;                     \
+    }
+#define BPG_DISPATCH3(dtype, BODY)                                   \
+    switch (dtype) {                                                 \
+    case DT_F64: { using S = double; BODY; } break;                  \
+    case DT_F32: { using S = float; BODY; } break;                   \
+    default: { using S = __nv_bfloat16; BODY; } break;               \
+    }
+
 template <typename S>
-static void launch_eval_t(const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
-                          int kp, cudaStream_t s)
+static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
+                            cudaStream_t s)
 {
-    if (g.n == 0)
-        return;
-    if (g.k == 2 && g.pair_kind == 0) {
-        int nb = blocks_for(g.n, BLOCK);
-        if (mode == MODE_LBP)
-            k_eval_bin<S, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
-        else if (mode == MODE_CAND)
-            k_eval_bin<S, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
-        else
-            k_eval_bin<S, MODE_SPLASH><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
-        return;
-    }
-#define BPG_GEN(KPV)                                                                  \
-    {                                                                                 \
-        int nb = blocks_for(g.n, BLOCK / KPV);                                        \
-        if (mode == MODE_LBP)                                                         \
-            k_eval_gen<S, KPV, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);    \
-        else if (mode == MODE_CAND)                                                   \
-            k_eval_gen<S, KPV, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);   \
-        else                                                                          \
-            k_eval_gen<S, KPV, MODE_SPLASH><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L); \
-    }
-    if (kp == 4) BPG_GEN(4)
-    else if (kp == 8) BPG_GEN(8)
-    else if (kp == 16) BPG_GEN(16)
-    else BPG_GEN(32)
-#undef BPG_GEN
+    int nb = blocks_for(g.n, BLOCK);
+    if (mode == MODE_LBP)
+        k_eval_bin<S, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+    else if (mode == MODE_CAND)
+        k_eval_bin<S, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+    else
+        k_eval_bin<S, MODE_SPLASH><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+}
+
+template <typename S, int KP>
+static void launch_eval_gen(const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
+                            cudaStream_t s)
+{
+    int nb = blocks_for(g.n, BLOCK / KP);
+    if (mode == MODE_LBP)
+        k_eval_gen<S, KP, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+    else if (mode == MODE_CAND)
+        k_eval_gen<S, KP, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+    else
+        k_eval_gen<S, KP, MODE_SPLASH><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
 }
 
 void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
                  int kp, cudaStream_t s)
 {
-    if (dtype == DT_F64)
-        launch_eval_t<double>(g, dr, rp, mode, level_L, kp, s);
-    else if (dtype == DT_F32)
-        launch_eval_t<float>(g, dr, rp, mode, level_L, kp, s);
+    if (g.n == 0)
+        return;
+    if (g.epm == 1) {
+        BPG_DISPATCH4(dtype, (launch_eval_bin<S>(g, dr, rp, mode, level_L, s)));
+        return;
+    }
+    if (kp == 4)
+        BPG_DISPATCH3(dtype, (launch_eval_gen<S, 4>(g, dr, rp, mode, level_L, s)))
+    else if (kp == 8)
+        BPG_DISPATCH3(dtype, (launch_eval_gen<S, 8>(g, dr, rp, mode, level_L, s)))
+    else if (kp == 16)
+        BPG_DISPATCH3(dtype, (launch_eval_gen<S, 16>(g, dr, rp, mode, level_L, s)))
     else
-        launch_eval_t<__nv_bfloat16>(g, dr, rp, mode, level_L, kp, s);
+        BPG_DISPATCH3(dtype, (launch_eval_gen<S, 32>(g, dr, rp, mode, level_L, s)))
 }
 
 void launch_decide(const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
@@ -577,12 +596,7 @@ void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const Ru
     if (g.n == 0)
         return;
     int nb = blocks_for(g.n, BLOCK);
-    if (dtype == DT_F64)
-        k_commit_rnbp<double><<<nb, BLOCK, 0, s>>>(g, dr, rp);
-    else if (dtype == DT_F32)
-        k_commit_rnbp<float><<<nb, BLOCK, 0, s>>>(g, dr, rp);
-    else
-        k_commit_rnbp<__nv_bfloat16><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+    BPG_DISPATCH4(dtype, (k_commit_rnbp<S><<<nb, BLOCK, 0, s>>>(g, dr, rp)));
 }
 
 void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s)
@@ -597,29 +611,16 @@ void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int le
     if (g.n == 0)
         return;
     int nb = blocks_for(g.n, BLOCK);
-    if (dtype == DT_F64)
-        k_splash_commit<double><<<nb, BLOCK, 0, s>>>(g, dr, level_L);
-    else if (dtype == DT_F32)
-        k_splash_commit<float><<<nb, BLOCK, 0, s>>>(g, dr, level_L);
-    else
-        k_splash_commit<__nv_bfloat16><<<nb, BLOCK, 0, s>>>(g, dr, level_L);
+    BPG_DISPATCH4(dtype, (k_splash_commit<S><<<nb, BLOCK, 0, s>>>(g, dr, level_L)));
 }
 
 void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s)
 {
-    size_t count = (size_t)g.M * (size_t)g.k;
-    double v = (g.k == 2 && g.pair_kind == 0) ? 0.0 : -log((double)g.k);
+    size_t count = (size_t)g.M * (size_t)g.epm;
+    double v = (g.epm == 1) ? 0.0 : -log((double)g.k);
     if (count) {
-        int nb = (int)((count + BLOCK - 1) / BLOCK);
-        nb = nb > 152 * 16 ? 152 * 16 : nb;
-        if (dtype == DT_F64)
-            k_init_msgs<double><<<nb, BLOCK, 0, s>>>((double *)dr.msg[0], (double *)dr.msg[1], count,
-                                                    v);
-        else if (dtype == DT_F32)
-            k_init_msgs<float><<<nb, BLOCK, 0, s>>>((float *)dr.msg[0], (float *)dr.msg[1], count, v);
-        else
-            k_init_msgs<__nv_bfloat16><<<nb, BLOCK, 0, s>>>((__nv_bfloat16 *)dr.msg[0],
-                                                           (__nv_bfloat16 *)dr.msg[1], count, v);
+        int nb = (int)std::min<size_t>((count + BLOCK - 1) / BLOCK, 152 * 16);
+        BPG_DISPATCH4(dtype, (k_init_msgs<S><<<nb, BLOCK, 0, s>>>((S *)dr.msg[0], (S *)dr.msg[1], count, v)));
     }
     int nb2 = blocks_for(g.G * NSUB, BLOCK);
     k_init_state<<<nb2, BLOCK, 0, s>>>(dr, g.G);
@@ -634,62 +635,38 @@ void launch_beliefs(int dtype, const DevGraph &g, const DevRun &dr, int kp, cuda
 {
     if (g.n == 0)
         return;
-    if (g.k == 2 && g.pair_kind == 0) {
+    if (g.epm == 1) {
         int nb = blocks_for(g.n, BLOCK);
-        if (dtype == DT_F64)
-            k_beliefs_bin<double><<<nb, BLOCK, 0, s>>>(g, dr);
-        else if (dtype == DT_F32)
-            k_beliefs_bin<float><<<nb, BLOCK, 0, s>>>(g, dr);
-        else
-            k_beliefs_bin<__nv_bfloat16><<<nb, BLOCK, 0, s>>>(g, dr);
+        BPG_DISPATCH4(dtype, (k_beliefs_bin<S><<<nb, BLOCK, 0, s>>>(g, dr)));
         return;
     }
-#define BPG_B(KPV)                                                                   \
-    {                                                                                \
-        int nb = blocks_for(g.n, BLOCK / KPV);                                       \
-        if (dtype == DT_F64)                                                         \
-            k_beliefs_gen<double, KPV><<<nb, BLOCK, 0, s>>>(g, dr);                  \
-        else if (dtype == DT_F32)                                                    \
-            k_beliefs_gen<float, KPV><<<nb, BLOCK, 0, s>>>(g, dr);                   \
-        else                                                                         \
-            k_beliefs_gen<__nv_bfloat16, KPV><<<nb, BLOCK, 0, s>>>(g, dr);           \
-    }
-    if (kp == 4) BPG_B(4)
-    else if (kp == 8) BPG_B(8)
-    else if (kp == 16) BPG_B(16)
-    else BPG_B(32)
-#undef BPG_B
+    if (kp == 4)
+        BPG_DISPATCH3(dtype, (k_beliefs_gen<S, 4><<<blocks_for(g.n, BLOCK / 4), BLOCK, 0, s>>>(g, dr)))
+    else if (kp == 8)
+        BPG_DISPATCH3(dtype, (k_beliefs_gen<S, 8><<<blocks_for(g.n, BLOCK / 8), BLOCK, 0, s>>>(g, dr)))
+    else if (kp == 16)
+        BPG_DISPATCH3(dtype, (k_beliefs_gen<S, 16><<<blocks_for(g.n, BLOCK / 16), BLOCK, 0, s>>>(g, dr)))
+    else
+        BPG_DISPATCH3(dtype, (k_beliefs_gen<S, 32><<<blocks_for(g.n, BLOCK / 32), BLOCK, 0, s>>>(g, dr)))
 }
 
 void launch_messages(int dtype, const DevGraph &g, const DevRun &dr, int kp, double *out, cudaStream_t s)
 {
     if (g.n == 0)
         return;
-    if (g.k == 2 && g.pair_kind == 0) {
+    if (g.epm == 1) {
         int nb = blocks_for(g.n, BLOCK);
-        if (dtype == DT_F64)
-            k_messages_bin<double><<<nb, BLOCK, 0, s>>>(g, dr, out);
-        else if (dtype == DT_F32)
-            k_messages_bin<float><<<nb, BLOCK, 0, s>>>(g, dr, out);
-        else
-            k_messages_bin<__nv_bfloat16><<<nb, BLOCK, 0, s>>>(g, dr, out);
+        BPG_DISPATCH4(dtype, (k_messages_bin<S><<<nb, BLOCK, 0, s>>>(g, dr, out)));
         return;
     }
-#define BPG_M(KPV)                                                                   \
-    {                                                                                \
-        int nb = blocks_for(g.n, BLOCK / KPV);                                       \
-        if (dtype == DT_F64)                                                         \
-            k_messages_gen<double, KPV><<<nb, BLOCK, 0, s>>>(g, dr, out);            \
-        else if (dtype == DT_F32)                                                    \
-            k_messages_gen<float, KPV><<<nb, BLOCK, 0, s>>>(g, dr, out);             \
-        else                                                                         \
-            k_messages_gen<__nv_bfloat16, KPV><<<nb, BLOCK, 0, s>>>(g, dr, out);     \
-    }
-    if (kp == 4) BPG_M(4)
-    else if (kp == 8) BPG_M(8)
-    else if (kp == 16) BPG_M(16)
-    else BPG_M(32)
-#undef BPG_M
+    if (kp == 4)
+        BPG_DISPATCH3(dtype, (k_messages_gen<S, 4><<<blocks_for(g.n, BLOCK / 4), BLOCK, 0, s>>>(g, dr, out)))
+    else if (kp == 8)
+        BPG_DISPATCH3(dtype, (k_messages_gen<S, 8><<<blocks_for(g.n, BLOCK / 8), BLOCK, 0, s>>>(g, dr, out)))
+    else if (kp == 16)
+        BPG_DISPATCH3(dtype, (k_messages_gen<S, 16><<<blocks_for(g.n, BLOCK / 16), BLOCK, 0, s>>>(g, dr, out)))
+    else
+        BPG_DISPATCH3(dtype, (k_messages_gen<S, 32><<<blocks_for(g.n, BLOCK / 32), BLOCK, 0, s>>>(g, dr, out)))
 }
 
 }  // namespace bpg

@@ -7,7 +7,7 @@ namespace bpg {
 
 enum { MODE_LBP = 0, MODE_CAND = 1, MODE_SPLASH = 2 };
 enum { SCHED_LBP = 0, SCHED_RBP = 1, SCHED_RS = 2, SCHED_RNBP = 3 };
-enum { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2 };
+enum { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2, DT_Q16 = 3 };
 
 void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s);
 void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,

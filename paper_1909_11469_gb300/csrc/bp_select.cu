@@ -142,14 +142,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_rbp(DevGraph g, DevRun d
     block_select_threshold<KeyT>(cnt, st.k_sel, key, thr, take_eq);
     S *dst = (S *)dr.msg[0];
     const S *src = (const S *)dr.msg[1];
-    const int k = g.k;
+    const int epm = g.epm;
     const bool tr = rp.record_trace && st.rounds <= rp.trace_capacity;
     block_select_apply<KeyT>(cnt, thr, take_eq, key, [&](int idx, bool take) {
         if (!take)
             return;
         const int e = e0 + idx;
-        for (int x = 0; x < k; ++x)
-            dst[(size_t)e * k + x] = src[(size_t)e * k + x];
+        for (int x = 0; x < epm; ++x)
+            dst[(size_t)e * epm + x] = src[(size_t)e * epm + x];
         if (tr)
             atomicOr(&dr.trace[(size_t)(st.rounds - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
     });
@@ -197,22 +197,21 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_rs(DevGraph g, DevRun dr
 
 void launch_select_rbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
 {
-    if (dtype == DT_F64)
-        k_select_rbp<double><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp);
-    else if (dtype == DT_F32)
-        k_select_rbp<float><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp);
-    else
-        k_select_rbp<__nv_bfloat16><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp);
+    switch (dtype) {
+    case DT_F64: k_select_rbp<double><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp); break;
+    case DT_F32: k_select_rbp<float><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp); break;
+    case DT_BF16: k_select_rbp<__nv_bfloat16><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp); break;
+    default: k_select_rbp<int16_t><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp); break;
+    }
 }
 
 void launch_select_rs(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
 {
+    // selection reads residuals only: FP64 runs keep double residuals, the others float
     if (dtype == DT_F64)
         k_select_rs<double><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp);
-    else if (dtype == DT_F32)
-        k_select_rs<float><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp);
     else
-        k_select_rs<__nv_bfloat16><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp);
+        k_select_rs<float><<<g.G, SEL_THREADS, 0, s>>>(g, dr, rp);
 }
 
 }  // namespace bpg

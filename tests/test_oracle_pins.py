@@ -283,3 +283,46 @@ def test_trace_follow_reproduces_run(orc):
         assert b["rounds"] == a["rounds"]
         assert np.array_equal(a["beliefs"], b["beliefs"])
         assert a["committed_updates"] == b["committed_updates"]
+
+
+# --------------------------------------------------------------------------- storage emulation
+def _bf16_exact(x):
+    f = np.asarray(x, dtype=np.float32)
+    return np.all(f.astype(np.float64) == np.asarray(x)) and np.all((f.view(np.uint32) & 0xFFFF) == 0)
+
+
+def test_bf16_storage_values_are_bf16(orc):
+    """Under BF16 storage every stored Ising log-odds is a bfloat16 value, and
+    every stored k-state log is one too."""
+    prob = synth.ising_grid(6, 1.5, seed=1)
+    res = orc.run(prob, "rnbp", parallelism=0.5, eps=1e-4, max_rounds=30, storage="bf16")
+    u = np.log(res["messages"][:, 1]) - np.log(res["messages"][:, 0])
+    assert _bf16_exact(np.float32(u)) and np.abs(np.float32(u) - u).max() < 1e-12
+    prob = synth.potts_grid(4, 5, seed=1)
+    res = orc.run(prob, "lbp", eps=1e-4, max_rounds=10, storage="bf16")
+    lg = np.log(res["messages"])
+    assert _bf16_exact(np.float32(lg)) and np.abs(np.float32(lg) - lg).max() < 1e-12
+
+
+def test_q16_storage_grid_and_bound(orc):
+    """Q16 log-odds are integer multiples of the step, |q| <= 32767, and the
+    rounding moves beliefs by far less than the step bound 4 * step / 4 per vertex
+    would allow for a contracting run."""
+    prob = synth.ising_grid(6, 1.5, seed=2)
+    beta_max = float(np.abs(prob.pair_log).max())
+    step = float(np.float32(2 * beta_max / 32767))
+    res = orc.run(prob, "lbp", eps=1e-6, max_rounds=40, storage="q16", q16_scale=step)
+    u = np.log(res["messages"][:, 1]) - np.log(res["messages"][:, 0])
+    q = u / step
+    assert np.abs(q - np.round(q)).max() < 1e-6 and np.abs(q).max() <= 32767
+    exact = orc.run(prob, "lbp", eps=1e-6, max_rounds=40)
+    assert np.abs(res["beliefs"] - exact["beliefs"]).max() < 2e-3
+
+
+def test_rounded_storage_residual_zero_when_unchanged(orc):
+    """With rounded storage a converged state is a fixed point of rounding: every
+    candidate rounds back to the stored word, so the final residual is exactly 0
+    or below eps (bf16 limit cycles aside, reported as not converged)."""
+    prob = synth.ising_tree(12, 1.0, seed=2)
+    res = orc.run(prob, "lbp", eps=1e-12, max_rounds=200, storage="bf16")
+    assert res["converged"] and res["final_max_residual"] == 0.0
