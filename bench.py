@@ -49,12 +49,17 @@ BYTES_PER_MSG = {"lbp": 20, "rnbp": 24, "rbp": 24, "rs": 24}
 BYTES_PER_VERTEX = 12
 
 
+ROUNDS_SCALE = 1.0
+
+
 def round_cap(sched: str, p: float) -> int:
     """Round caps where the configuration is silent: LBP 1000, RnBP ceil(1000/LowP),
-    RBP/RS ceil(1000/p) (about 1000 sweeps' worth of commits)."""
-    if sched == "lbp":
-        return 1000
-    return int(np.ceil(1000.0 / p))
+    RBP/RS ceil(1000/p) (about 1000 sweeps' worth of commits). --rounds-scale
+    shrinks every cap by the same factor (used for profiler passes only: no graph
+    of the default workload converges before its cap, so the kernel mix stays the
+    same)."""
+    base = 1000 if sched == "lbp" else int(np.ceil(1000.0 / p))
+    return max(1, int(round(base * ROUNDS_SCALE)))
 
 
 def make_batch(wl, rank: int):
@@ -170,7 +175,13 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile-step", action="store_true",
+                    help="skip the extra step with per-phase CUDA events")
+    ap.add_argument("--rounds-scale", type=float, default=1.0,
+                    help="scale every round cap (profiler passes only)")
     args = ap.parse_args()
+    global ROUNDS_SCALE
+    ROUNDS_SCALE = args.rounds_scale
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
@@ -250,7 +261,7 @@ def main():
     # Roofline of the message-update (full evaluation) kernel: one more step of
     # the same workload with per-phase CUDA events on the launching stream.
     flush.zero_()
-    prof_step = one_step(1)
+    prof_step = [] if args.no_profile_step else one_step(1)
     torch.cuda.synchronize()
     alg_bytes, eval_ms, eval_launches = 0.0, 0.0, 0
     phase = {"eval_ms": 0.0, "decide_ms": 0.0, "frontier_ms": 0.0}
@@ -325,6 +336,7 @@ def main():
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
             "config": {"workload": args.workload, "graphs_per_gpu": G,
+                       "rounds_scale": args.rounds_scale,
                        "vertices_per_graph": wl["side"] ** 2, "messages_per_graph": int(prob.m // G),
                        "eps": wl["eps"], "schedules": [f"{s}:{p}" for s, p in wl["schedules"]],
                        "l2": "flushed between steps (512 MB write)",

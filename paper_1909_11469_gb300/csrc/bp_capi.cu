@@ -69,6 +69,8 @@ void destroy_cached(CachedGraph &c) { cudaGraphExecDestroy(c.exec); }
 
 }  // namespace
 
+void bpg::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 struct bp_graph {
     int32_t n = 0, k = 0, G = 0;
     int64_t M = 0;

@@ -3,6 +3,8 @@
 
 #include "bp_internal.cuh"
 
+#include <string>
+
 namespace bpg {
 
 enum { MODE_LBP = 0, MODE_CAND = 1, MODE_SPLASH = 2 };
@@ -21,5 +23,8 @@ void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int le
 void launch_stop_running(const DevGraph &g, const DevRun &dr, cudaStream_t s);
 void launch_beliefs(int dtype, const DevGraph &g, const DevRun &dr, int kp, cudaStream_t s);
 void launch_messages(int dtype, const DevGraph &g, const DevRun &dr, int kp, double *out, cudaStream_t s);
+
+// Sets the calling thread's message returned by bp_last_error().
+void set_last_error(const std::string &msg);
 
 }  // namespace bpg
