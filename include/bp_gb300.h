@@ -193,6 +193,38 @@ int bp_get_graph_stats(const bp_graph *g, bp_run_stats *out);
  */
 int bp_get_trace(const bp_graph *g, uint32_t *out, int64_t capacity_words, int32_t *rounds_out);
 
+/*
+ * bp_lbp_run_noalloc - synchronous LBP (FP32 messages) on one binary Ising
+ * graph without allocating any memory. The paper has no counterpart: this is a
+ * service entry point for callers that cannot allocate device memory, such as
+ * code running under another framework's caching allocator that has already
+ * reserved the GPU, latency-critical paths where cudaMalloc/cudaFree would
+ * synchronise the device, or plug-ins that must leave the allocation state
+ * alone.
+ *
+ * Every pointer argument except rounds_out and converged_out is a DEVICE
+ * pointer owned by the caller: row_ptr [n_vars + 1] (int32), col and rev
+ * [n_dir_edges], unary_log [n_vars * 2], beta [n_dir_edges] (layouts as for
+ * bp_create_graph / BP_PAIR_ISING_BETA), beliefs [n_vars * 2] float64 output.
+ * rounds_out / converged_out are optional HOST outputs. The run uses the same
+ * kernels, rounds and convergence test as bp_run(BP_LBP) with msg_dtype BP_F32
+ * and writes the same beliefs.
+ *
+ * Scratch: one static device array of about 5.0 MiB in the library, reserved
+ * on every GPU that loads the library and held until the process exits. It
+ * bounds the graph to at most 131072 vertices and 262144 directed edges
+ * (larger graphs fail with BP_ERR_UNSUPPORTED). The first call on a device
+ * looks up the array's device address with that device current (make that
+ * first call before any stream capture). Each call resets the scratch it reads
+ * and runs on cuda_stream (NULL = legacy default stream), synchronising it;
+ * calls whose work overlaps on the GPU share the one array and race.
+ * Inputs are validated on the device (BP_ERR_BAD_GRAPH, BP_ERR_NONFINITE).
+ */
+int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_ptr, const int32_t *col,
+                       const int32_t *rev, const float *unary_log, const float *beta, double eps,
+                       int32_t max_rounds, double *beliefs, int32_t *rounds_out, int32_t *converged_out,
+                       void *cuda_stream);
+
 /* Copies the phase profile of the last bp_run (see bp_profile). */
 int bp_get_profile(const bp_graph *g, bp_profile *out);
 

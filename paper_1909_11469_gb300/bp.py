@@ -83,6 +83,8 @@ _SIGNATURES = {
     "bp_get_graph_stats": (ctypes.c_int, [_P, _P]),
     "bp_get_trace": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "bp_get_profile": (ctypes.c_int, [_P, _P]),
+    "bp_lbp_run_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
+                                          ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P]),
     "bp_graph_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "bp_destroy_graph": (None, [_P]),
     "bp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -243,6 +245,22 @@ def bp_get_profile(handle) -> dict:
     p = bp_profile()
     _check(lib().bp_get_profile(handle, ctypes.byref(p)), "bp_get_profile")
     return p.as_dict()
+
+
+def bp_lbp_run_noalloc(n_vars, n_dir_edges, row_ptr, col, rev, unary_log, beta, eps, max_rounds,
+                       beliefs, cuda_stream=None):
+    """LBP on one binary Ising graph without any allocation by the library.
+    Every array is a CUDA tensor (or a device address) the caller owns: row_ptr
+    int32 [n+1], col / rev int32 [M], unary_log float32 [n*2], beta float32 [M],
+    beliefs float64 [n*2] (written). Returns (rounds, converged)."""
+    def dp(t):
+        return t if isinstance(t, int) or t is None else t.data_ptr()
+    rounds, conv = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().bp_lbp_run_noalloc(int(n_vars), int(n_dir_edges), dp(row_ptr), dp(col), dp(rev),
+                                    dp(unary_log), dp(beta), float(eps), int(max_rounds), dp(beliefs),
+                                    ctypes.byref(rounds), ctypes.byref(conv), cuda_stream),
+           "bp_lbp_run_noalloc")
+    return rounds.value, bool(conv.value)
 
 
 def bp_destroy_graph(handle) -> None:
