@@ -35,18 +35,32 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    # the configuration the metric is quoted on: 100x100, beta ~ U[-2.5, 2.5], 50 seeds
     "ising100x100_b2.5_50seeds": dict(
-        side=100, beta_max=2.5, lam_max=1.0, n_seeds=50, eps=1e-4, dtype="f32",
+        kind="grid_batch", side=100, beta_max=2.5, lam_max=1.0, n_seeds=50, eps=1e-4, dtype="f32",
         schedules=[("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.1), ("rs", 0.1)]),
+    # 1000x1000, beta ~ U[-3, 3]: one graph of 4M messages, LBP and RnBP
+    "ising1000x1000_b3": dict(
+        kind="grid_batch", side=1000, beta_max=3.0, lam_max=1.0, n_seeds=1, eps=1e-4, dtype="f32",
+        schedules=[("lbp", 1.0), ("rnbp", 0.5)]),
+    # 4096 Erdos-Renyi graphs, n log-uniform in [50, 5000], mean degree 4, beta ~ U[-3, 3]
+    "er4096_b3": dict(
+        kind="er_batch", n_graphs=4096, beta_max=3.0, lam_max=1.0, eps=1e-4, dtype="f32",
+        schedules=[("rnbp", 0.5), ("lbp", 1.0)]),
 }
 DEFAULT_WORKLOAD = "ising100x100_b2.5_50seeds"
 L2_FLUSH_BYTES = 512 << 20          # > 126 MB of L2
-# algorithmic bytes per evaluated message / per processed vertex of the
-# full-evaluation kernel (binary Ising, FP32 messages): rev, incoming message,
-# exp(-2 beta), old message, new message (+ residual for the frontier modes);
-# per vertex row_ptr, unary log-odds, graph id.
-BYTES_PER_MSG = {"lbp": 20, "rnbp": 24, "rbp": 24, "rs": 24}
+# Algorithmic bytes of the full-evaluation kernel (binary Ising): per evaluated
+# message rev (4), incoming message (s), exp(-2 beta) (4), old message (s), new
+# message (s), + residual (4) in the frontier modes; per processed vertex
+# row_ptr, unary log-odds and graph id (12). s = 4 (FP32) or 2 (BF16, Q16).
+MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
 BYTES_PER_VERTEX = 12
+
+
+def bytes_per_msg(sched: str, dtype: str) -> int:
+    s = MSG_BYTES[dtype]
+    return 8 + 3 * s + (0 if sched == "lbp" else (8 if dtype == "f64" else 4))
 
 
 ROUNDS_SCALE = 1.0
@@ -64,7 +78,12 @@ def round_cap(sched: str, p: float) -> int:
 
 def make_batch(wl, rank: int):
     from paper_1909_11469_gb300 import synth
+    if wl["kind"] == "er_batch":
+        return synth.er_batch(wl["n_graphs"], seed=rank, beta_max=wl["beta_max"],
+                              lam_max=wl["lam_max"])
     seeds = range(rank * wl["n_seeds"], (rank + 1) * wl["n_seeds"])
+    if wl["n_seeds"] == 1:
+        return synth.ising_grid(wl["side"], wl["beta_max"], rank, wl["lam_max"])
     return synth.ising_grid_batch(wl["side"], wl["beta_max"], seeds, wl["lam_max"])
 
 
@@ -123,7 +142,10 @@ def oracle_sample(wl, budget_rounds: int, seed: int = 0):
     budget_rounds rounds. Returns (committed updates, seconds)."""
     import oracle
     from paper_1909_11469_gb300 import synth
-    prob = synth.ising_grid(wl["side"], wl["beta_max"], seed, wl["lam_max"])
+    if wl["kind"] == "er_batch":
+        prob = synth.er_batch(1, seed=seed, beta_max=wl["beta_max"], lam_max=wl["lam_max"])
+    else:
+        prob = synth.ising_grid(wl["side"], wl["beta_max"], seed, wl["lam_max"])
     committed, t = 0, 0.0
     for sched, p in wl["schedules"]:
         t0 = time.perf_counter()
@@ -179,10 +201,19 @@ def main():
                     help="skip the extra step with per-phase CUDA events")
     ap.add_argument("--rounds-scale", type=float, default=1.0,
                     help="scale every round cap (profiler passes only)")
+    ap.add_argument("--direct-launch", action="store_true",
+                    help="timed steps launch kernels directly instead of replaying CUDA graphs "
+                         "(profiler passes only)")
+    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2],
+                    help="binary update mapping (0 = library's choice)")
+    ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "q16", "f64"],
+                    help="message storage (default: the workload's)")
     args = ap.parse_args()
     global ROUNDS_SCALE
     ROUNDS_SCALE = args.rounds_scale
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.dtype:
+        wl["dtype"] = args.dtype
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -212,7 +243,7 @@ def main():
 
     def opts(**kw):
         return bp.bp_default_options(msg_dtype=wl["dtype"], cuda_stream=stream.cuda_stream,
-                                     graph_id_base=rank * G, **kw)
+                                     graph_id_base=rank * G, kernel_variant=args.kernel_variant, **kw)
 
     def one_step(profile: int):
         out = []
@@ -236,7 +267,7 @@ def main():
     for i in range(args.steps):
         flush.zero_()                     # L2 flush between timed steps (outside the events)
         starts[i].record(stream)
-        results.append(one_step(0))
+        results.append(one_step(1 if args.direct_launch else 0))
         ends[i].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -266,7 +297,8 @@ def main():
     alg_bytes, eval_ms, eval_launches = 0.0, 0.0, 0
     phase = {"eval_ms": 0.0, "decide_ms": 0.0, "frontier_ms": 0.0}
     for sched, p, st, pr, gst in prof_step:
-        alg_bytes += BYTES_PER_MSG[sched] * pr["full_evals"] + BYTES_PER_VERTEX * pr["active_vertices"]
+        alg_bytes += (bytes_per_msg(sched, wl["dtype"]) * pr["full_evals"] +
+                      BYTES_PER_VERTEX * pr["active_vertices"])
         eval_ms += pr["eval_ms"]
         eval_launches += pr["eval_launches"]
         for k in phase:
@@ -290,7 +322,7 @@ def main():
         peaks = json.load(open(pk_path))
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
-    roofline = {"bound": "hbm", "kernel": "k_eval_bin<float> (Eq. 2 + Eq. 4 + reduction)",
+    roofline = {"bound": "hbm", "kernel": f"k_eval_bin ({wl['dtype']} messages; Eq. 2 + Eq. 4 + reduction)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
@@ -303,7 +335,7 @@ def main():
     if not args.no_e2e:
         unary_h = torch.from_numpy(prob.unary_log).pin_memory()
         pair_h = torch.from_numpy(prob.pair_log).pin_memory()
-        bel_h = torch.empty((prob.n, 2), dtype=torch.float64).pin_memory()
+        bel_h = torch.empty((prob.n, prob.k), dtype=torch.float64).pin_memory()
         e2e_committed, e2e_s = 0, 0.0
         for it in range(args.steps + 1):
             torch.cuda.synchronize()
@@ -336,8 +368,8 @@ def main():
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
             "config": {"workload": args.workload, "graphs_per_gpu": G,
-                       "rounds_scale": args.rounds_scale,
-                       "vertices_per_graph": wl["side"] ** 2, "messages_per_graph": int(prob.m // G),
+                       "rounds_scale": args.rounds_scale, "direct_launch": bool(args.direct_launch),
+                       "vertices": int(prob.n), "directed_messages": int(prob.m),
                        "eps": wl["eps"], "schedules": [f"{s}:{p}" for s, p in wl["schedules"]],
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"dp{world}" if world > 1 else "single"},

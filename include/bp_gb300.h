@@ -105,7 +105,8 @@ typedef struct {
     void *cuda_stream;        /* cudaStream_t to run on (NULL = the legacy default stream) */
     double time_budget_ms;    /* wall-clock budget of bp_run, 0 = none */
     uint32_t graph_id_base;   /* Philox graph id of graph 0 of the handle (default 0) */
-    int32_t kernel_variant;   /* 0 = automatic choice; others reserved for tuning */
+    int32_t kernel_variant;   /* binary update mapping: 0 = automatic, 1 = one thread per
+                                 vertex, 2 = 256-vertex tiles with 4-edge quads */
     int32_t profile;          /* 1: time every round's phases with CUDA events (default 0) */
 } bp_options;
 

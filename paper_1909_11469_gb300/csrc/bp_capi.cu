@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -84,6 +85,7 @@ struct bp_graph {
     int pair_kind = -1;
     bool has_pot = false;
     float qscale = 1.0f;   // Q16 log-odds step: 2 max|beta| / 32767
+    int32_t sel_smem_bytes = 0;   // staged keys of the largest graph, capped
     float *d_unary = nullptr, *d_udiff32 = nullptr, *d_q32 = nullptr, *d_pair = nullptr,
           *d_psi_shared = nullptr;
     double *d_udiff64 = nullptr, *d_q64 = nullptr;
@@ -146,6 +148,8 @@ DevGraph dev_graph(const bp_graph *g)
     d.M = (int32_t)g->M;
     d.epm = epm_of(g);
     d.qscale = g->qscale;
+    d.vec_ok = 1;   // every device array of a handle comes from cudaMalloc (256-byte aligned)
+    d.sel_smem_bytes = g->sel_smem_bytes;
     d.row_ptr = g->d_row_ptr;
     d.col = g->d_col;
     d.rev = g->d_rev;
@@ -263,6 +267,7 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     }
     // Everything above is host-side validation; device work starts here.
     cudaGetDevice(&g->dev);
+    prepare_select_kernels();
     g->n = n;
     g->k = k;
     g->M = M;
@@ -271,6 +276,11 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     g->h_rev.assign(rev, rev + M);
     g->h_gv_off = gv;
     g->h_ge_off = ge;
+    int64_t max_keys = 1;
+    for (int32_t q = 0; q < n_graphs; ++q)
+        max_keys = std::max<int64_t>(max_keys, std::max<int64_t>(ge[(size_t)q + 1] - ge[(size_t)q],
+                                                                 gv[(size_t)q + 1] - gv[(size_t)q]));
+    g->sel_smem_bytes = (int32_t)std::min<int64_t>(max_keys * 8, select_smem_limit());
     std::vector<int32_t> rp32((size_t)n + 1);
     for (int32_t i = 0; i <= n; ++i)
         rp32[(size_t)i] = (int32_t)row_ptr[i];
@@ -407,6 +417,15 @@ int get_graph_exec(bp_graph *g, int dtype, const RunParams &rp, int rounds, Cach
     g->cache.push_back(c);
     *out = &g->cache.back();
     return BP_OK;
+}
+
+// Smallest float whose value is >= x (x > 0, finite).
+float float_at_least(double x)
+{
+    float f = (float)x;
+    if ((double)f < x)
+        f = std::nextafter(f, std::numeric_limits<float>::infinity());
+    return f;
 }
 
 bool all_finite(const float *p, size_t n)
@@ -593,6 +612,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_UNSUPPORTED, "Q16 storage needs the binary Ising layout");
     if (!(opt.high_p >= 0.0) || !std::isfinite(opt.high_p) || !std::isfinite(opt.ratio_threshold))
         return fail(BP_ERR_INVALID_ARG, "bad high_p or ratio_threshold");
+    if (opt.kernel_variant < 0 || opt.kernel_variant > 2)
+        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be 0, 1 or 2");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
         return fail(BP_ERR_INVALID_ARG, "splash_depth must be in [0, 16]");
     if (opt.record_trace && opt.trace_capacity < 0)
@@ -619,6 +640,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     rp.trace_capacity = rp.record_trace ? opt.trace_capacity : 0;
     const int64_t trace_count = schedule == BP_RS ? g->n : g->M;
     rp.trace_words = (int32_t)((trace_count + 31) / 32);
+    rp.variant = opt.kernel_variant == 2 ? 2 : 1;
+    rp.eps_f = float_at_least(eps);
     if (rp.record_trace) {
         size_t words = (size_t)rp.trace_capacity * (size_t)rp.trace_words;
         if (words > g->trace_alloc_words) {

@@ -36,6 +36,8 @@ struct DevGraph {
     int32_t M;
     int32_t epm;              // stored elements per message: 1 (binary log-odds) or k
     float qscale;             // Q16 storage: log-odds per integer step
+    int32_t vec_ok;           // 1: rev, q and message buffers are 16-byte aligned
+    int32_t sel_smem_bytes;   // dynamic shared memory of the selection kernels
     const int32_t *row_ptr;   // [n+1]
     const int32_t *col;       // [M]
     const int32_t *rev;       // [M]
@@ -68,7 +70,13 @@ struct RunParams {
     int32_t record_trace;
     int32_t trace_capacity;
     int32_t trace_words;      // words per recorded round
+    int32_t variant;          // binary update mapping: 1 thread per vertex, 2 tiled edge quads
+    float eps_f;              // smallest float >= eps: (double)r >= eps  <=>  r >= eps_f for float r
 };
+
+// eps in the residual type, chosen so that the comparison equals the FP64 test.
+__device__ __forceinline__ float eps_in(const RunParams &rp, float) { return rp.eps_f; }
+__device__ __forceinline__ double eps_in(const RunParams &rp, double) { return rp.eps; }
 
 // Mutable per-run device buffers.
 struct DevRun {
@@ -84,6 +92,10 @@ struct DevRun {
     double *beliefs;              // [n*k]
 };
 
+// Message buffer b (0 or 1). A select instead of msg[b]: indexing the kernel
+// parameter array with a runtime value would copy the whole struct to local memory.
+__device__ __forceinline__ void *msg_buf(const DevRun &dr, int b) { return b ? dr.msg[1] : dr.msg[0]; }
+
 // ---------------------------------------------------------------------------
 // Storage traits: message element type S, arithmetic type A. sc is the Q16
 // step (log-odds per integer unit); the floating formats ignore it.
@@ -91,18 +103,21 @@ template <typename S> struct Store;
 template <> struct Store<double> {
     using A = double;
     static __device__ __forceinline__ double ld(const double *p, float) { return *p; }
+    static __device__ __forceinline__ double val(double x, float) { return x; }
     static __device__ __forceinline__ void st(double *p, double v, float) { *p = v; }
     static __device__ __forceinline__ double quant(double v, float) { return v; }
 };
 template <> struct Store<float> {
     using A = float;
     static __device__ __forceinline__ float ld(const float *p, float) { return *p; }
+    static __device__ __forceinline__ float val(float x, float) { return x; }
     static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
     static __device__ __forceinline__ float quant(float v, float) { return v; }
 };
 template <> struct Store<__nv_bfloat16> {
     using A = float;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ float val(__nv_bfloat16 x, float) { return __bfloat162float(x); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ float quant(float v, float)
     {
@@ -118,6 +133,7 @@ template <> struct Store<int16_t> {
         return fminf(fmaxf(q, -32767.0f), 32767.0f);
     }
     static __device__ __forceinline__ float ld(const int16_t *p, float sc) { return (float)*p * sc; }
+    static __device__ __forceinline__ float val(int16_t x, float sc) { return (float)x * sc; }
     static __device__ __forceinline__ void st(int16_t *p, float v, float sc) { *p = (int16_t)code(v, sc); }
     static __device__ __forceinline__ float quant(float v, float sc) { return code(v, sc) * sc; }
 };

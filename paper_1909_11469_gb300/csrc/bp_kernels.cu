@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
     const int i = first + threadIdx.x;
     bool valid = false;
     int gg = g0;
-    double maxr = 0.0;
+    A maxa = 0;
+    const A eps_a = eps_in(rp, (A)0);
     unsigned int cnt = 0;
     if (i < g.n) {
         gg = g.gid[i];
@@ -48,8 +49,8 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
         if (act) {
             valid = true;
             const int cur_idx = dr.gs[gg].cur;
-            const S *cur = (const S *)dr.msg[cur_idx];
-            S *out = (S *)dr.msg[cur_idx ^ 1];
+            const S *cur = (const S *)msg_buf(dr, cur_idx);
+            S *out = (S *)msg_buf(dr, cur_idx ^ 1);
             const int beg = g.row_ptr[i], end = g.row_ptr[i + 1];
             const int deg = end - beg;
             A h;
@@ -84,9 +85,8 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
                 Store<S>::st(out + e, unew, g.qscale);
                 if (MODE == MODE_CAND)
                     R[e] = (RT)r;
-                double rd = (double)r;
-                maxr = rd > maxr ? rd : maxr;
-                cnt += (rd >= rp.eps) ? 1u : 0u;
+                maxa = r > maxa ? r : maxa;
+                cnt += (r >= eps_a) ? 1u : 0u;
             };
 #pragma unroll
             for (int c = 0; c < CACHE; ++c)
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
         }
     }
     if (MODE != MODE_SPLASH)
-        reduce_to_graph(dr, uniform, g0, valid, gg, maxr, cnt);
+        reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
 }
 
 // --------------------------------------------------------------------------
@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(BLOCK) k_eval_gen(DevGraph g, DevRun dr, RunPa
     const bool lane_ok = lane < k;
     bool valid = false;
     int gg = g0;
-    double maxr = 0.0;
+    A maxa = 0;
+    const A eps_a = eps_in(rp, (A)0);
     unsigned int cnt = 0;
     bool act = false;
     if (i < g.n) {
@@ -175,8 +176,8 @@ __global__ void __launch_bounds__(BLOCK) k_eval_gen(DevGraph g, DevRun dr, RunPa
         const unsigned gm = grp_mask<KP>();
         valid = (lane == 0);
         const int cur_idx = dr.gs[gg].cur;
-        const S *cur = (const S *)dr.msg[cur_idx];
-        S *out = (S *)dr.msg[cur_idx ^ 1];
+        const S *cur = (const S *)msg_buf(dr, cur_idx);
+        S *out = (S *)msg_buf(dr, cur_idx ^ 1);
         const int beg = g.row_ptr[i], end = g.row_ptr[i + 1];
         A Sx = lane_ok ? (A)g.unary[(size_t)i * k + lane] : (A)0;
         for (int e = beg; e < end; ++e)
@@ -218,13 +219,12 @@ __global__ void __launch_bounds__(BLOCK) k_eval_gen(DevGraph g, DevRun dr, RunPa
                 Store<S>::st(out + (size_t)e * k + lane, lnew, g.qscale);
             if (MODE == MODE_CAND && lane == 0)
                 R[e] = (RT)r;
-            double rd = (double)r;
-            maxr = rd > maxr ? rd : maxr;
-            cnt += (rd >= rp.eps) ? 1u : 0u;
+            maxa = r > maxa ? r : maxa;
+            cnt += (r >= eps_a) ? 1u : 0u;
         }
     }
     if (MODE != MODE_SPLASH)
-        reduce_to_graph(dr, uniform, g0, valid, gg, maxr, cnt);
+        reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
 }
 
 // --------------------------------------------------------------------------
@@ -317,45 +317,318 @@ __device__ __forceinline__ void add_commit_counts(const DevRun &dr, bool uniform
     }
 }
 
-// RnBP commit: keep messages with residual >= eps, then a Philox Bernoulli(p_t)
-// draw keyed by (seed; local edge id, round, graph id) (Section IV-A).
-template <typename S>
-__global__ void __launch_bounds__(BLOCK) k_commit_rnbp(DevGraph g, DevRun dr, RunParams rp)
+// --------------------------------------------------------------------------
+// Tiled form of the binary update for full evaluations (LBP and frontier
+// modes). A block owns 256 consecutive vertices and their contiguous edge
+// range [e0, e1) (CSR rows are adjacent). Every thread owns up to two quads of
+// 4 consecutive edges of that range, aligned to 4 elements, and issues their
+// 16-byte loads of rev, exp(-2 beta) and the old message at entry, in parallel
+// with the vertex pass; then
+//   0. vertex pass: graph state, local source vertex of every edge (shared)
+//   1. quad pass:   incoming log-odds cur[rev[e]] (the only scattered loads)
+//   2. vertex pass: field h_i = unary log-odds + sum of incoming
+//   3. quad pass:   cavity h_i - u_{j->i}, new message, residual, quad stores
+// Tiles whose edge range exceeds the two quads per thread use a per-vertex
+// loop instead.
+constexpr int TILE_V = 256;
+constexpr int QUADS = 2;
+constexpr int TILE_E = 4 * TILE_V * QUADS - 8;   // staged edges per tile (alignment slack)
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using V = float4; };
+template <> struct Vec4<int32_t> { using V = int4; };
+
+// Loads elements [base, base + 4) of p (base a multiple of 4) into out[],
+// vectorised when p is 16-byte aligned and the quad lies inside [0, count).
+template <typename T> __device__ __forceinline__ void load_quad(const T *p, int base, int count, bool vec, T out[4])
 {
+    if constexpr (sizeof(T) == 4) {
+        if (vec && base >= 0 && base + 3 < count) {
+            typename Vec4<T>::V v = *reinterpret_cast<const typename Vec4<T>::V *>(p + base);
+            out[0] = v.x;
+            out[1] = v.y;
+            out[2] = v.z;
+            out[3] = v.w;
+            return;
+        }
+    } else if constexpr (sizeof(T) == 8) {
+        if (vec && base >= 0 && base + 3 < count) {
+            double2 a = *reinterpret_cast<const double2 *>(p + base);
+            double2 b = *reinterpret_cast<const double2 *>(p + base + 2);
+            out[0] = a.x;
+            out[1] = a.y;
+            out[2] = b.x;
+            out[3] = b.y;
+            return;
+        }
+    } else {   // 2-byte storage
+        if (vec && base >= 0 && base + 3 < count) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(p + base);
+            const unsigned short w[4] = {(unsigned short)(v.x & 0xffffu), (unsigned short)(v.x >> 16),
+                                         (unsigned short)(v.y & 0xffffu), (unsigned short)(v.y >> 16)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                T t;
+                memcpy(&t, &w[k], sizeof(T));
+                out[k] = t;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k >= 0 && base + k < count)
+            out[k] = p[base + k];
+}
+
+// One thread's (max residual, count) of graph gg into a reduction sub-slot.
+__device__ __forceinline__ void flush_to_graph(const DevRun &dr, int gg, double maxr, unsigned int cnt)
+{
+    if (gg < 0)
+        return;
+    const int slot = blockIdx.x & (NSUB - 1);
+    if (maxr > 0.0)
+        atomicMax(&dr.red_max[(size_t)gg * NSUB + slot], (unsigned long long)__double_as_longlong(maxr));
+    if (cnt)
+        atomicAdd(&dr.red_cnt[(size_t)gg * NSUB + slot], cnt);
+}
+
+template <typename S, int MODE>
+__global__ void __launch_bounds__(TILE_V) k_eval_bin_tiled(DevGraph g, DevRun dr, RunParams rp)
+{
+    using A = typename Store<S>::A;
     using RT = typename ResidT<S>::T;
-    const int first = blockIdx.x * blockDim.x;
-    const int last = min(g.n - 1, first + (int)blockDim.x - 1);
-    const int g0 = g.gid[first];
-    const bool uniform = (g0 == g.gid[last]);
-    const int i = first + threadIdx.x;
-    bool valid = false;
-    int gg = g0;
-    unsigned int c = 0;
-    if (i < g.n) {
-        gg = g.gid[i];
-        const GState st = dr.gs[gg];
-        if (st.status == ST_RUNNING) {
-            valid = true;
-            const RT *R = (const RT *)dr.resid;
-            S *dst = (S *)dr.msg[0];
-            const S *src = (const S *)dr.msg[1];
-            const int e0 = g.ge_off[gg];
-            const int epm = g.epm;
-            const bool tr = rp.record_trace && st.rounds <= rp.trace_capacity;
-            for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
-                if ((double)R[e] >= rp.eps && rnbp_pick(rp, (uint32_t)(e - e0), (uint32_t)st.rounds,
-                                                        (uint32_t)gg, st)) {
-                    for (int x = 0; x < epm; ++x)
-                        dst[(size_t)e * epm + x] = src[(size_t)e * epm + x];
-                    ++c;
-                    if (tr)
-                        atomicOr(&dr.trace[(size_t)(st.rounds - 1) * rp.trace_words + (e >> 5)],
-                                 1u << (e & 31));
+    __shared__ A s_uin[TILE_E];
+    __shared__ A s_h[TILE_V];
+    __shared__ uint8_t s_src[TILE_E];
+    __shared__ int8_t s_cur[TILE_V];
+    const int v0 = blockIdx.x * TILE_V;
+    const int nv = min(TILE_V, g.n - v0);
+    const int e0 = g.row_ptr[v0];
+    const int e1 = g.row_ptr[v0 + nv];
+    const int ne = e1 - e0;
+    const int g0 = g.gid[v0];
+    const bool uniform = (g0 == g.gid[v0 + nv - 1]);
+    const int vl = threadIdx.x;
+    const int v = v0 + vl;
+    const A *q;
+    const A *udiff;
+    if constexpr (sizeof(A) == 8) {
+        q = (const A *)g.q64;
+        udiff = (const A *)g.udiff64;
+    } else {
+        q = (const A *)g.q32;
+        udiff = (const A *)g.udiff32;
+    }
+    RT *R = (RT *)dr.resid;
+    A maxa = 0;
+    const A eps_a = eps_in(rp, (A)0);
+    unsigned int cnt = 0;
+
+    if (ne > TILE_E) {
+        // rare dense tile: per-vertex loop
+        bool valid = false;
+        int gg = g0;
+        if (vl < nv) {
+            gg = g.gid[v];
+            if (dr.gs[gg].status == ST_RUNNING) {
+                valid = true;
+                const int c = dr.gs[gg].cur;
+                const S *cur = (const S *)msg_buf(dr, c);
+                S *out = (S *)msg_buf(dr, c ^ 1);
+                A h = udiff[v];
+                for (int e = g.row_ptr[v]; e < g.row_ptr[v + 1]; ++e)
+                    h += Store<S>::ld(cur + g.rev[e], g.qscale);
+                for (int e = g.row_ptr[v]; e < g.row_ptr[v + 1]; ++e) {
+                    A unew = ising_logodds(q[e], h - Store<S>::ld(cur + g.rev[e], g.qscale));
+                    A r = fabs(m_sigmoid(Store<S>::quant(unew, g.qscale)) -
+                               m_sigmoid(Store<S>::ld(cur + e, g.qscale)));
+                    Store<S>::st(out + e, unew, g.qscale);
+                    if (MODE == MODE_CAND)
+                        R[e] = (RT)r;
+                    maxa = r > maxa ? r : maxa;
+                    cnt += (r >= eps_a) ? 1u : 0u;
+                }
+            }
+        }
+        reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
+        return;
+    }
+
+    // Edge quads of this thread: elements [qb, qb + 4) with qb = e0a + 4 (vl + 256 j).
+    const int e0a = e0 & ~3;
+    const bool vec = g.vec_ok != 0;
+    // buffer of the tile's first graph; edges of a graph in the other buffer
+    // (possible only in LBP tiles that straddle graphs) reload their old value
+    const int c_tile = (MODE == MODE_LBP) ? dr.gs[g0].cur : 0;
+    int rv[QUADS][4];
+    A qv[QUADS][4];
+    S ov[QUADS][4];
+#pragma unroll
+    for (int j = 0; j < QUADS; ++j) {
+        const int qb = e0a + 4 * (vl + TILE_V * j);
+        if (qb < e1) {
+            load_quad(g.rev, qb, g.M, vec, rv[j]);
+            load_quad(q, qb, g.M, vec, qv[j]);
+            load_quad((const S *)msg_buf(dr, c_tile), qb, g.M, vec, ov[j]);
+        }
+    }
+
+    // 0. vertex pass
+    int beg = 0, end = 0;
+    bool act = false;
+    if (vl < nv) {
+        const int gg = g.gid[v];
+        act = dr.gs[gg].status == ST_RUNNING;
+        s_cur[vl] = act ? (int8_t)dr.gs[gg].cur : (int8_t)-1;
+        beg = g.row_ptr[v] - e0;
+        end = g.row_ptr[v + 1] - e0;
+        for (int t = beg; t < end; ++t)
+            s_src[t] = (uint8_t)vl;
+    }
+    __syncthreads();
+    // 1. gather the incoming messages
+    A uin[QUADS][4];
+#pragma unroll
+    for (int j = 0; j < QUADS; ++j) {
+        const int qb = e0a + 4 * (vl + TILE_V * j);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = qb + k;
+            if (e >= e0 && e < e1) {
+                const int c = s_cur[s_src[e - e0]];
+                if (c >= 0) {
+                    uin[j][k] = Store<S>::ld((const S *)msg_buf(dr, c) + rv[j][k], g.qscale);
+                    s_uin[e - e0] = uin[j][k];
                 }
             }
         }
     }
-    add_commit_counts(dr, uniform, g0, valid, gg, c, false);
+    __syncthreads();
+    // 2. vertex fields
+    if (act) {
+        A h = udiff[v];
+        for (int t = beg; t < end; ++t)
+            h += s_uin[t];
+        s_h[vl] = h;
+    }
+    __syncthreads();
+    // 3. new messages, residuals, reductions. In a tile that spans graphs each
+    // thread accumulates per graph and flushes when its graph changes.
+    int acc_g = -1;
+#pragma unroll
+    for (int j = 0; j < QUADS; ++j) {
+        const int qb = e0a + 4 * (vl + TILE_V * j);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = qb + k;
+            if (e < e0 || e >= e1)
+                continue;
+            const int src = s_src[e - e0];
+            const int c = s_cur[src];
+            if (c < 0)
+                continue;
+            const A unew = ising_logodds(qv[j][k], s_h[src] - uin[j][k]);
+            const A old = (c == c_tile) ? Store<S>::val(ov[j][k], g.qscale)
+                                        : Store<S>::ld((const S *)msg_buf(dr, c) + e, g.qscale);
+            const A r = fabs(m_sigmoid(Store<S>::quant(unew, g.qscale)) - m_sigmoid(old));
+            Store<S>::st((S *)msg_buf(dr, c ^ 1) + e, unew, g.qscale);
+            if (MODE == MODE_CAND)
+                R[e] = (RT)r;
+            if (!uniform) {
+                const int gg = g.gid[v0 + src];
+                if (gg != acc_g) {
+                    flush_to_graph(dr, acc_g, (double)maxa, cnt);
+                    acc_g = gg;
+                    maxa = 0;
+                    cnt = 0;
+                }
+            }
+            maxa = r > maxa ? r : maxa;
+            cnt += (r >= eps_a) ? 1u : 0u;
+        }
+    }
+    if (!uniform)
+        flush_to_graph(dr, acc_g, (double)maxa, cnt);
+    reduce_to_graph(dr, uniform, g0, uniform, g0, (double)maxa, cnt);
+}
+
+// RnBP commit, tiled like the update: a vertex pass stages the source of each
+// edge and its graph's round state; an edge pass reads the residuals
+// contiguously, draws Philox for the messages with residual >= eps and copies
+// the selected candidates.
+template <typename S>
+__global__ void __launch_bounds__(TILE_V) k_commit_rnbp_tiled(DevGraph g, DevRun dr, RunParams rp)
+{
+    using RT = typename ResidT<S>::T;
+    __shared__ uint8_t s_src[TILE_E];
+    __shared__ int s_g[TILE_V];
+    const int v0 = blockIdx.x * TILE_V;
+    const int nv = min(TILE_V, g.n - v0);
+    const int e0 = g.row_ptr[v0];
+    const int ne = g.row_ptr[v0 + nv] - e0;
+    const int g0 = g.gid[v0];
+    const bool uniform = (g0 == g.gid[v0 + nv - 1]);
+    const int vl = threadIdx.x;
+    const int v = v0 + vl;
+    const RT *R = (const RT *)dr.resid;
+    S *dst = (S *)dr.msg[0];
+    const S *src = (const S *)dr.msg[1];
+    const int epm = g.epm;
+    unsigned int c = 0;
+    if (ne > TILE_E) {
+        bool valid = false;
+        int gg = g0;
+        if (vl < nv) {
+            gg = g.gid[v];
+            const GState st = dr.gs[gg];
+            if (st.status == ST_RUNNING) {
+                valid = true;
+                const int ge0 = g.ge_off[gg];
+                const bool tr = rp.record_trace && st.rounds <= rp.trace_capacity;
+                for (int e = g.row_ptr[v]; e < g.row_ptr[v + 1]; ++e) {
+                    if (R[e] >= eps_in(rp, (RT)0) &&
+                        rnbp_pick(rp, (uint32_t)(e - ge0), (uint32_t)st.rounds, (uint32_t)gg, st)) {
+                        for (int x = 0; x < epm; ++x)
+                            dst[(size_t)e * epm + x] = src[(size_t)e * epm + x];
+                        ++c;
+                        if (tr)
+                            atomicOr(&dr.trace[(size_t)(st.rounds - 1) * rp.trace_words + (e >> 5)],
+                                     1u << (e & 31));
+                    }
+                }
+            }
+        }
+        add_commit_counts(dr, uniform, g0, valid, gg, c, false);
+        return;
+    }
+    if (vl < nv) {
+        const int gg = g.gid[v];
+        s_g[vl] = dr.gs[gg].status == ST_RUNNING ? gg : -1;
+        for (int t = g.row_ptr[v] - e0; t < g.row_ptr[v + 1] - e0; ++t)
+            s_src[t] = (uint8_t)vl;
+    }
+    __syncthreads();
+    for (int t = vl; t < ne; t += TILE_V) {
+        const int gg = s_g[s_src[t]];
+        if (gg < 0)
+            continue;
+        const int e = e0 + t;
+        if (R[e] < eps_in(rp, (RT)0))
+            continue;
+        const GState &st = dr.gs[gg];
+        if (!rnbp_pick(rp, (uint32_t)(e - g.ge_off[gg]), (uint32_t)st.rounds, (uint32_t)gg, st))
+            continue;
+        for (int x = 0; x < epm; ++x)
+            dst[(size_t)e * epm + x] = src[(size_t)e * epm + x];
+        if (uniform)
+            ++c;
+        else
+            atomicAdd(&dr.gs[gg].committed, 1ull);
+        if (rp.record_trace && st.rounds <= rp.trace_capacity)
+            atomicOr(&dr.trace[(size_t)(st.rounds - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
+    }
+    add_commit_counts(dr, uniform, g0, uniform, g0, c, false);
 }
 
 // Residual Splash: one BFS level (pull): an unreached vertex next to a vertex of
@@ -461,7 +734,7 @@ __global__ void __launch_bounds__(BLOCK) k_beliefs_bin(DevGraph g, DevRun dr)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n)
         return;
-    const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
+    const S *cur = (const S *)msg_buf(dr, dr.gs[g.gid[i]].cur);
     double h = g.udiff64[i];
     for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
         h += (double)Store<S>::ld(cur + g.rev[e], g.qscale);
@@ -479,7 +752,7 @@ __global__ void __launch_bounds__(BLOCK) k_beliefs_gen(DevGraph g, DevRun dr)
         return;
     const int k = g.k;
     const bool ok = lane < k;
-    const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
+    const S *cur = (const S *)msg_buf(dr, dr.gs[g.gid[i]].cur);
     double s = ok ? (double)g.unary[(size_t)i * k + lane] : -1e300;
     for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
         if (ok)
@@ -498,7 +771,7 @@ __global__ void __launch_bounds__(BLOCK) k_messages_bin(DevGraph g, DevRun dr, d
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n)
         return;
-    const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
+    const S *cur = (const S *)msg_buf(dr, dr.gs[g.gid[i]].cur);
     for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
         double u = (double)Store<S>::ld(cur + e, g.qscale);
         out[2 * (size_t)e + 1] = 1.0 / (1.0 + exp(-u));
@@ -515,7 +788,7 @@ __global__ void __launch_bounds__(BLOCK) k_messages_gen(DevGraph g, DevRun dr, d
     if (i >= g.n)
         return;
     const int k = g.k;
-    const S *cur = (const S *)dr.msg[dr.gs[g.gid[i]].cur];
+    const S *cur = (const S *)msg_buf(dr, dr.gs[g.gid[i]].cur);
     if (lane < k)
         for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
             out[(size_t)e * k + lane] = exp((double)Store<S>::ld(cur + (size_t)e * k + lane, g.qscale));
@@ -546,12 +819,21 @@ static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams
                             cudaStream_t s)
 {
     int nb = blocks_for(g.n, BLOCK);
-    if (mode == MODE_LBP)
-        k_eval_bin<S, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
-    else if (mode == MODE_CAND)
-        k_eval_bin<S, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
-    else
+    // mapping: thread per vertex (variant 1) or 256-vertex tiles with edge quads (variant 2)
+    const bool tiled = rp.variant == 2;
+    if (mode == MODE_LBP) {
+        if (tiled)
+            k_eval_bin_tiled<S, MODE_LBP><<<blocks_for(g.n, TILE_V), TILE_V, 0, s>>>(g, dr, rp);
+        else
+            k_eval_bin<S, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+    } else if (mode == MODE_CAND) {
+        if (tiled)
+            k_eval_bin_tiled<S, MODE_CAND><<<blocks_for(g.n, TILE_V), TILE_V, 0, s>>>(g, dr, rp);
+        else
+            k_eval_bin<S, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+    } else {
         k_eval_bin<S, MODE_SPLASH><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+    }
 }
 
 template <typename S, int KP>
@@ -576,6 +858,7 @@ void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams
         BPG_DISPATCH4(dtype, (launch_eval_bin<S>(g, dr, rp, mode, level_L, s)));
         return;
     }
+    // (k-state messages use one KP-lane group per vertex)
     if (kp == 4)
         BPG_DISPATCH3(dtype, (launch_eval_gen<S, 4>(g, dr, rp, mode, level_L, s)))
     else if (kp == 8)
@@ -595,8 +878,7 @@ void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const Ru
 {
     if (g.n == 0)
         return;
-    int nb = blocks_for(g.n, BLOCK);
-    BPG_DISPATCH4(dtype, (k_commit_rnbp<S><<<nb, BLOCK, 0, s>>>(g, dr, rp)));
+    BPG_DISPATCH4(dtype, (k_commit_rnbp_tiled<S><<<blocks_for(g.n, TILE_V), TILE_V, 0, s>>>(g, dr, rp)));
 }
 
 void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s)

@@ -16,6 +16,9 @@ void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams
                  int kp, cudaStream_t s);
 void launch_decide(const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
 void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
+// One-time attribute set-up of the selection kernels (dynamic shared memory).
+void prepare_select_kernels();
+int select_smem_limit();
 void launch_select_rbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
 void launch_select_rs(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
 void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s);

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -216,6 +217,8 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
     g.M = M;
     g.epm = 1;
     g.qscale = 1.0f;
+    // the caller's rev may sit at any address; the scratch arrays are aligned
+    g.vec_ok = ((reinterpret_cast<uintptr_t>(rev) & 15u) == 0) ? 1 : 0;
     g.row_ptr = row_ptr;
     g.col = col;
     g.rev = rev;
@@ -243,6 +246,13 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
     rp.eps = eps;
     rp.low_p = 1.0;
     rp.high_p = 1.0;
+    rp.variant = 1;
+    {
+        float f = (float)eps;   // smallest float >= eps
+        if ((double)f < eps)
+            f = std::nextafter(f, 3.0e38f);
+        rp.eps_f = f;
+    }
 
     // Rounds are launched directly; the host reads the running flag every
     // `chunk` rounds (rounds after convergence are no-ops on the device).
