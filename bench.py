@@ -66,6 +66,41 @@ def bytes_per_msg(sched: str, dtype: str) -> int:
 ROUNDS_SCALE = 1.0
 
 
+def batch_kernel_bytes(sched: str, dtype: str, st: dict, pr: dict) -> float:
+    """Algorithmic bytes of the persistent batch kernel for one run: the full
+    evaluations (as bytes_per_msg) plus the frontier work: RnBP and RBP read
+    every residual once per round (4 B) and copy each committed message (read +
+    write, 2 s); RS pulls the incoming residuals of every vertex (rev + residual,
+    8 B per message per round) and per splash-updated message reads rev, col,
+    the source level, the incoming message and exp(-2 beta) and writes the
+    candidate (13 + 2 s B), then commits it (2 s B)."""
+    s = MSG_BYTES[dtype]
+    b = bytes_per_msg(sched, dtype) * pr["full_evals"] + BYTES_PER_VERTEX * pr["active_vertices"]
+    if sched in ("rnbp", "rbp"):
+        b += 4 * pr["full_evals"] + 2 * s * st["committed_updates"]
+    elif sched == "rs":
+        b += 8 * pr["full_evals"] + (13 + 4 * s) * st["committed_updates"]   # 4+4+1+4 + s + s, + 2 s
+    return b
+
+
+def eval_roofline(step, dtype: str, peak: float, peak_src: str):
+    """Roofline of the per-round message-update kernel from a profiled step."""
+    alg_bytes, eval_ms, eval_launches = 0.0, 0.0, 0
+    phase = {"eval_ms": 0.0, "decide_ms": 0.0, "frontier_ms": 0.0}
+    for sched, p, st, pr, gst in step:
+        alg_bytes += bytes_per_msg(sched, dtype) * pr["full_evals"] + BYTES_PER_VERTEX * pr["active_vertices"]
+        eval_ms += pr["eval_ms"]
+        eval_launches += pr["eval_launches"]
+        for k in phase:
+            phase[k] += pr[k]
+    achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
+    return ({"bound": "hbm", "kernel": f"k_eval_bin ({dtype} messages; Eq. 2 + Eq. 4 + reduction)",
+             "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_source": peak_src,
+             "frac": (achieved / peak) if achieved else None, "traffic": None,
+             "launches": eval_launches, "bytes_per_launch": alg_bytes / max(eval_launches, 1),
+             "avg_launch_us": 1e3 * eval_ms / max(eval_launches, 1)}, phase)
+
+
 def round_cap(sched: str, p: float) -> int:
     """Round caps where the configuration is silent: LBP 1000, RnBP ceil(1000/LowP),
     RBP/RS ceil(1000/p) (about 1000 sweeps' worth of commits). --rounds-scale
@@ -289,20 +324,40 @@ def main():
         committed, evals, launches = (int(x) for x in t.tolist())
     value = committed / (total_ms / 1e3)
 
-    # Roofline of the message-update (full evaluation) kernel: one more step of
-    # the same workload with per-phase CUDA events on the launching stream.
+    # Roofline. One more step of the same workload with profiling: the
+    # persistent batch kernel is timed as a whole; the per-round path times
+    # every phase with CUDA events on the launching stream.
     flush.zero_()
     prof_step = [] if args.no_profile_step else one_step(1)
     torch.cuda.synchronize()
-    alg_bytes, eval_ms, eval_launches = 0.0, 0.0, 0
-    phase = {"eval_ms": 0.0, "decide_ms": 0.0, "frontier_ms": 0.0}
-    for sched, p, st, pr, gst in prof_step:
-        alg_bytes += (bytes_per_msg(sched, wl["dtype"]) * pr["full_evals"] +
-                      BYTES_PER_VERTEX * pr["active_vertices"])
-        eval_ms += pr["eval_ms"]
-        eval_launches += pr["eval_launches"]
-        for k in phase:
-            phase[k] += pr[k]
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    roofline, update_roofline, phase = None, None, None
+    if prof_step and prof_step[0][3]["batch_kernel_ms"] > 0:
+        b, ms = 0.0, 0.0
+        for sched, p, st, pr, gst in prof_step:
+            b += batch_kernel_bytes(sched, wl["dtype"], st, pr)
+            ms += pr["batch_kernel_ms"]
+        roofline = {"bound": "hbm", "kernel": f"k_persistent ({wl['dtype']} messages; all rounds of every "
+                    "graph: Eq. 2 + Eq. 4 update, reduction, frontier)",
+                    "achieved": b / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                    "peak_source": peak_src, "frac": b / (ms / 1e3) / 1e9 / peak, "traffic": None,
+                    "launches": len(prof_step), "bytes_per_launch": b / len(prof_step),
+                    "avg_launch_us": 1e3 * ms / len(prof_step)}
+        # the message-update kernel of the per-round path on the same workload
+        saved = args.kernel_variant
+        args.kernel_variant = 1
+        flush.zero_()
+        upd_step = one_step(1)
+        torch.cuda.synchronize()
+        args.kernel_variant = saved
+        update_roofline, phase = eval_roofline(upd_step, wl["dtype"], peak, peak_src)
+    elif prof_step:
+        roofline, phase = eval_roofline(prof_step, wl["dtype"], peak, peak_src)
     per_sched = {}
     for step in results:
         for sched, p, st, pr, gst in step:
@@ -316,19 +371,6 @@ def main():
     for d in per_sched.values():
         d["batch_ms"] = float(np.median(d.pop("ms")))
         d["committed_updates"] //= args.steps
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
-    roofline = {"bound": "hbm", "kernel": f"k_eval_bin ({wl['dtype']} messages; Eq. 2 + Eq. 4 + reduction)",
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "launches": eval_launches,
-                "bytes_per_launch": alg_bytes / max(eval_launches, 1),
-                "avg_launch_us": 1e3 * eval_ms / max(eval_launches, 1)}
 
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
@@ -376,7 +418,8 @@ def main():
             "candidate_evals_per_s": evals / (total_ms / 1e3),
             "schedules": per_sched,
             "profiled_step_phase_ms": phase,
-            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roofline, "update_kernel_roofline": update_roofline,
+            "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(line))

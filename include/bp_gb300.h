@@ -105,8 +105,11 @@ typedef struct {
     void *cuda_stream;        /* cudaStream_t to run on (NULL = the legacy default stream) */
     double time_budget_ms;    /* wall-clock budget of bp_run, 0 = none */
     uint32_t graph_id_base;   /* Philox graph id of graph 0 of the handle (default 0) */
-    int32_t kernel_variant;   /* binary update mapping: 0 = automatic, 1 = one thread per
-                                 vertex, 2 = 256-vertex tiles with 4-edge quads */
+    int32_t kernel_variant;   /* binary Ising path: 0 = automatic (currently 1), 1 =
+                                 per-round kernels, one thread per vertex, 2 = per-round,
+                                 256-vertex tiles with 4-edge quads, 3 = persistent batch
+                                 kernel: one thread-block cluster per graph runs all of
+                                 its rounds in a single launch */
     int32_t profile;          /* 1: time every round's phases with CUDA events (default 0) */
 } bp_options;
 
@@ -126,6 +129,8 @@ typedef struct {
     double eval_ms;            /* summed duration of those launches */
     double decide_ms;          /* summed duration of the per-graph decisions */
     double frontier_ms;        /* summed duration of selection / splash / commit */
+    double batch_kernel_ms;    /* duration of the persistent batch kernel (always recorded
+                                  when that kernel ran; 0 otherwise) */
 } bp_profile;
 
 /* Fills *opt with the defaults listed above. */

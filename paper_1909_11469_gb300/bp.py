@@ -65,7 +65,7 @@ class bp_profile(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("eval_launches", ctypes.c_int64),
                 ("full_evals", ctypes.c_int64), ("active_vertices", ctypes.c_int64),
                 ("eval_ms", ctypes.c_double), ("decide_ms", ctypes.c_double),
-                ("frontier_ms", ctypes.c_double)]
+                ("frontier_ms", ctypes.c_double), ("batch_kernel_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -99,12 +99,14 @@ struct bp_graph {
     unsigned long long *d_red_max = nullptr;
     unsigned int *d_red_cnt = nullptr;
     int32_t *d_running = nullptr;
+    int32_t *d_queue = nullptr;
+    int32_t max_graph_vertices = 0;
     uint32_t *d_trace = nullptr;
     size_t trace_alloc_words = 0;
     double *d_beliefs = nullptr;
     int32_t *h_running = nullptr;   // pinned
     cudaStream_t cap_stream = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_pt0 = nullptr, ev_pt1 = nullptr;
     std::vector<cudaEvent_t> prof_events;   // profile mode: 4 per round of a chunk
     std::vector<CachedGraph> cache;
     // last result
@@ -181,6 +183,7 @@ DevRun dev_run(const bp_graph *g)
     r.n_running = g->d_running;
     r.trace = g->d_trace;
     r.beliefs = g->d_beliefs;
+    r.queue = g->d_queue;
     return r;
 }
 
@@ -278,6 +281,8 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     g->h_ge_off = ge;
     int64_t max_keys = 1;
     for (int32_t q = 0; q < n_graphs; ++q)
+        g->max_graph_vertices = std::max(g->max_graph_vertices, gv[(size_t)q + 1] - gv[(size_t)q]);
+    for (int32_t q = 0; q < n_graphs; ++q)
         max_keys = std::max<int64_t>(max_keys, std::max<int64_t>(ge[(size_t)q + 1] - ge[(size_t)q],
                                                                  gv[(size_t)q + 1] - gv[(size_t)q]));
     g->sel_smem_bytes = (int32_t)std::min<int64_t>(max_keys * 8, select_smem_limit());
@@ -300,6 +305,7 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     // per-graph state, reductions, beliefs
     if ((rc = dalloc(&g->d_gs, (size_t)n_graphs)) || (rc = dalloc(&g->d_red_max, (size_t)n_graphs * NSUB)) ||
         (rc = dalloc(&g->d_red_cnt, (size_t)n_graphs * NSUB)) || (rc = dalloc(&g->d_running, 1)) ||
+        (rc = dalloc(&g->d_queue, 1)) ||
         (rc = dalloc(&g->d_level, (size_t)std::max(n, 1))) ||
         (rc = dalloc(&g->d_beliefs, (size_t)n * (size_t)k)))
         return rc;
@@ -307,6 +313,8 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     BP_CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     BP_CK(cudaEventCreate(&g->ev0));
     BP_CK(cudaEventCreate(&g->ev1));
+    BP_CK(cudaEventCreate(&g->ev_pt0));
+    BP_CK(cudaEventCreate(&g->ev_pt1));
     return BP_OK;
 }
 
@@ -366,11 +374,21 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
         for (int d = 1; d <= h; ++d)
             launch_bfs_level(dg, dr, d, s);
         kernels += any ? h : 0;
-        for (int step = 0; step <= 2 * h; ++step) {
-            const int L = step <= h ? h - step : step - h;
-            launch_eval(dtype, dg, dr, rp, MODE_SPLASH, L, g->kp, s);
-            launch_splash_commit(dtype, dg, dr, L, s);
-            kernels += any ? 2 : 0;
+        auto level_of = [h](int step) { return step <= h ? h - step : step - h; };
+        if (dg.epm == 1) {
+            // binary messages: each sub-step's commit fused with the next evaluation
+            launch_splash_step(dtype, dg, dr, -1, level_of(0), s);
+            for (int step = 0; step < 2 * h; ++step)
+                launch_splash_step(dtype, dg, dr, level_of(step), level_of(step + 1), s);
+            launch_splash_step(dtype, dg, dr, level_of(2 * h), -1, s);
+            kernels += any ? 2 * h + 2 : 0;
+        } else {
+            for (int step = 0; step <= 2 * h; ++step) {
+                const int L = level_of(step);
+                launch_eval(dtype, dg, dr, rp, MODE_SPLASH, L, g->kp, s);
+                launch_splash_commit(dtype, dg, dr, L, s);
+                kernels += any ? 2 : 0;
+            }
         }
     }
     }
@@ -612,8 +630,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_UNSUPPORTED, "Q16 storage needs the binary Ising layout");
     if (!(opt.high_p >= 0.0) || !std::isfinite(opt.high_p) || !std::isfinite(opt.ratio_threshold))
         return fail(BP_ERR_INVALID_ARG, "bad high_p or ratio_threshold");
-    if (opt.kernel_variant < 0 || opt.kernel_variant > 2)
-        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be 0, 1 or 2");
+    if (opt.kernel_variant < 0 || opt.kernel_variant > 3)
+        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be 0, 1, 2 or 3");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
         return fail(BP_ERR_INVALID_ARG, "splash_depth must be in [0, 16]");
     if (opt.record_trace && opt.trace_capacity < 0)
@@ -666,64 +684,78 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         BP_CK(cudaMemsetAsync(g->d_trace, 0, sizeof(uint32_t) * (size_t)rp.trace_capacity * rp.trace_words, s));
     BP_CK(cudaGetLastError());
 
-    const int max_chunk = opt.rounds_per_launch > 0 ? opt.rounds_per_launch
-                          : (schedule == BP_RS ? 16 : 64);
-    int chunk = opt.rounds_per_launch > 0 ? opt.rounds_per_launch : 2;
-    int64_t rounds_launched = 0;
+    // The persistent batch kernel (one cluster per graph, all rounds inside one
+    // launch) is taken on request; the automatic choice replays captured rounds,
+    // which measured faster on every workload here (the per-round kernels keep
+    // 64 warps per SM over the whole batch, a cluster only 32 per SM).
+    const bool persistent = epm_of(g) == 1 && opt.kernel_variant == 3;
+    float batch_ms = 0.f;
     bool stopped = false;
     std::vector<float> t_eval, t_decide, t_front;   // per global round (profile)
-    // Each replay runs `chunk` rounds (evaluations); graphs that finish turn the
-    // rest of their kernels into no-ops. The host polls the running count once
-    // per replay.
-    for (;;) {
-        if (opt.profile) {
-            // direct launches with events between the phases of every round
-            if (g->prof_events.size() < (size_t)chunk * 4) {
-                size_t old = g->prof_events.size();
-                g->prof_events.resize((size_t)chunk * 4);
-                for (size_t q = old; q < g->prof_events.size(); ++q)
-                    BP_CK(cudaEventCreate(&g->prof_events[q]));
+    if (persistent) {
+        const long long budget_ns = opt.time_budget_ms > 0.0 ? (long long)(opt.time_budget_ms * 1e6) : 0;
+        BP_CK(cudaEventRecord(g->ev_pt0, s));
+        BP_CK(launch_persistent(dtype, dg, dr, rp, budget_ns, s));
+        BP_CK(cudaEventRecord(g->ev_pt1, s));
+        kernels += 1;
+    } else {
+        const int max_chunk = opt.rounds_per_launch > 0 ? opt.rounds_per_launch
+                              : (schedule == BP_RS ? 16 : 64);
+        int chunk = opt.rounds_per_launch > 0 ? opt.rounds_per_launch : 2;
+        int64_t rounds_launched = 0;
+        // Each replay runs `chunk` rounds (evaluations); graphs that finish turn the
+        // rest of their kernels into no-ops. The host polls the running count once
+        // per replay.
+        for (;;) {
+            if (opt.profile) {
+                // direct launches with events between the phases of every round
+                if (g->prof_events.size() < (size_t)chunk * 4) {
+                    size_t old = g->prof_events.size();
+                    g->prof_events.resize((size_t)chunk * 4);
+                    for (size_t q = old; q < g->prof_events.size(); ++q)
+                        BP_CK(cudaEventCreate(&g->prof_events[q]));
+                }
+                for (int r = 0; r < chunk; ++r)
+                    kernels += record_round(g, dtype, dg, dr, rp, s, &g->prof_events[(size_t)r * 4]);
+                BP_CK(cudaGetLastError());
+            } else {
+                CachedGraph *cg = nullptr;
+                if ((rc = get_graph_exec(g, dtype, rp, chunk, &cg)) != BP_OK)
+                    return rc;
+                BP_CK(cudaGraphLaunch(cg->exec, s));
+                kernels += cg->kernels;
             }
-            for (int r = 0; r < chunk; ++r)
-                kernels += record_round(g, dtype, dg, dr, rp, s, &g->prof_events[(size_t)r * 4]);
-            BP_CK(cudaGetLastError());
-        } else {
-            CachedGraph *cg = nullptr;
-            if ((rc = get_graph_exec(g, dtype, rp, chunk, &cg)) != BP_OK)
-                return rc;
-            BP_CK(cudaGraphLaunch(cg->exec, s));
-            kernels += cg->kernels;
-        }
-        rounds_launched += chunk;
-        BP_CK(cudaMemcpyAsync(g->h_running, g->d_running, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        BP_CK(cudaStreamSynchronize(s));
-        if (opt.profile) {
-            for (int r = 0; r < chunk; ++r) {
-                float a = 0.f, b = 0.f, c = 0.f;
-                cudaEvent_t *ev = &g->prof_events[(size_t)r * 4];
-                BP_CK(cudaEventElapsedTime(&a, ev[0], ev[1]));
-                BP_CK(cudaEventElapsedTime(&b, ev[1], ev[2]));
-                BP_CK(cudaEventElapsedTime(&c, ev[2], ev[3]));
-                t_eval.push_back(a);
-                t_decide.push_back(b);
-                t_front.push_back(c);
+            rounds_launched += chunk;
+            BP_CK(cudaMemcpyAsync(g->h_running, g->d_running, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            BP_CK(cudaStreamSynchronize(s));
+            if (opt.profile) {
+                for (int r = 0; r < chunk; ++r) {
+                    float a = 0.f, b = 0.f, c = 0.f;
+                    cudaEvent_t *ev = &g->prof_events[(size_t)r * 4];
+                    BP_CK(cudaEventElapsedTime(&a, ev[0], ev[1]));
+                    BP_CK(cudaEventElapsedTime(&b, ev[1], ev[2]));
+                    BP_CK(cudaEventElapsedTime(&c, ev[2], ev[3]));
+                    t_eval.push_back(a);
+                    t_decide.push_back(b);
+                    t_front.push_back(c);
+                }
             }
-        }
-        if (*g->h_running <= 0)
-            break;
-        if (rounds_launched > (int64_t)max_rounds + 1) {
-            // cannot happen: every running graph stops after max_rounds + 1 evaluations
-            return fail(BP_ERR_CUDA, "round loop did not terminate");
-        }
-        if (opt.time_budget_ms > 0.0) {
-            double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-            if (el > opt.time_budget_ms) {
-                launch_stop_running(dg, dr, s);
-                stopped = true;
+            if (*g->h_running <= 0)
                 break;
+            if (rounds_launched > (int64_t)max_rounds + 1) {
+                // cannot happen: every running graph stops after max_rounds + 1 evaluations
+                return fail(BP_ERR_CUDA, "round loop did not terminate");
             }
+            if (opt.time_budget_ms > 0.0) {
+                double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+                if (el > opt.time_budget_ms) {
+                    launch_stop_running(dg, dr, s);
+                    stopped = true;
+                    break;
+                }
+            }
+            chunk = std::min(chunk * 2, max_chunk);
         }
-        chunk = std::min(chunk * 2, max_chunk);
     }
     if (stopped)
         kernels += 1;
@@ -736,6 +768,11 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     BP_CK(cudaStreamSynchronize(s));
     float ms = 0.f;
     BP_CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    if (persistent) {
+        BP_CK(cudaEventElapsedTime(&batch_ms, g->ev_pt0, g->ev_pt1));
+        for (const GState &st : hs)
+            stopped = stopped || st.status == ST_STOPPED;
+    }
 
     g->last_stats.assign((size_t)g->G, bp_run_stats());
     bp_run_stats tot;
@@ -747,6 +784,7 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     bp_profile prof;
     memset(&prof, 0, sizeof(prof));
     prof.kernel_launches = kernels;
+    prof.batch_kernel_ms = batch_ms;
     for (int32_t q = 0; q < g->G; ++q) {
         prof.full_evals += (int64_t)hs[(size_t)q].full_evals;
         prof.active_vertices += (int64_t)hs[(size_t)q].full_nodes;
@@ -904,6 +942,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_red_max);
     dfree(g->d_red_cnt);
     dfree(g->d_running);
+    dfree(g->d_queue);
     dfree(g->d_trace);
     dfree(g->d_beliefs);
     if (g->h_running)
@@ -914,6 +953,10 @@ void bp_destroy_graph(bp_graph *g)
         cudaEventDestroy(g->ev0);
     if (g->ev1)
         cudaEventDestroy(g->ev1);
+    if (g->ev_pt0)
+        cudaEventDestroy(g->ev_pt0);
+    if (g->ev_pt1)
+        cudaEventDestroy(g->ev_pt1);
     for (auto ev : g->prof_events)
         cudaEventDestroy(ev);
     delete g;

@@ -90,6 +90,7 @@ struct DevRun {
     int32_t *n_running;           // [1]
     uint32_t *trace;              // [trace_capacity * trace_words]
     double *beliefs;              // [n*k]
+    int32_t *queue;               // [1] next graph for the persistent batch kernel
 };
 
 // Message buffer b (0 or 1). A select instead of msg[b]: indexing the kernel

@@ -12,6 +12,7 @@
 // u = log m(1) - log m(0), k-state messages as k normalised logs.
 #include "bp_internal.cuh"
 #include "bp_launch.h"
+#include "bp_update.cuh"
 
 #include <math.h>
 
@@ -24,9 +25,10 @@ constexpr int BLOCK = 256;
 // --------------------------------------------------------------------------
 // Binary Ising messages, one thread per vertex: the thread gathers the
 // incoming log-odds of its vertex through rev[], forms the cavity of each
-// out-edge by subtraction and writes every out-message of the vertex.
+// out-edge by subtraction and writes every out-message of the vertex
+// (eval_vertex_bin). Full evaluations only (LBP and the frontier modes).
 template <typename S, int MODE>
-__global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunParams rp, int level_L)
+__global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunParams rp)
 {
     using A = typename Store<S>::A;
     using RT = typename ResidT<S>::T;
@@ -38,66 +40,17 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
     bool valid = false;
     int gg = g0;
     A maxa = 0;
-    const A eps_a = eps_in(rp, (A)0);
     unsigned int cnt = 0;
     if (i < g.n) {
         gg = g.gid[i];
-        const int status = dr.gs[gg].status;
-        bool act = (status == ST_RUNNING);
-        if (MODE == MODE_SPLASH)
-            act = act && (dr.level[i] == level_L);
-        if (act) {
+        if (dr.gs[gg].status == ST_RUNNING) {
             valid = true;
-            const int cur_idx = dr.gs[gg].cur;
-            const S *cur = (const S *)msg_buf(dr, cur_idx);
-            S *out = (S *)msg_buf(dr, cur_idx ^ 1);
-            const int beg = g.row_ptr[i], end = g.row_ptr[i + 1];
-            const int deg = end - beg;
-            A h;
-            const A *q;
-            if constexpr (sizeof(A) == 8) {
-                h = g.udiff64[i];
-                q = (const A *)g.q64;
-            } else {
-                h = g.udiff32[i];
-                q = (const A *)g.q32;
-            }
-            constexpr int CACHE = 8;
-            A uin[CACHE];
-#pragma unroll
-            for (int c = 0; c < CACHE; ++c) {
-                if (c < deg) {
-                    uin[c] = Store<S>::ld(cur + g.rev[beg + c], g.qscale);
-                    h += uin[c];
-                }
-            }
-            for (int e = beg + CACHE; e < end; ++e)
-                h += Store<S>::ld(cur + g.rev[e], g.qscale);
-            RT *R = (RT *)dr.resid;
-            auto one = [&](int e, A u_in) {
-                A unew = ising_logodds(q[e], h - u_in);
-                if (MODE == MODE_SPLASH) {
-                    Store<S>::st(out + e, unew, g.qscale);
-                    return;
-                }
-                A uq = Store<S>::quant(unew, g.qscale);
-                A r = fabs(m_sigmoid(uq) - m_sigmoid(Store<S>::ld(cur + e, g.qscale)));
-                Store<S>::st(out + e, unew, g.qscale);
-                if (MODE == MODE_CAND)
-                    R[e] = (RT)r;
-                maxa = r > maxa ? r : maxa;
-                cnt += (r >= eps_a) ? 1u : 0u;
-            };
-#pragma unroll
-            for (int c = 0; c < CACHE; ++c)
-                if (c < deg)
-                    one(beg + c, uin[c]);
-            for (int e = beg + CACHE; e < end; ++e)
-                one(e, Store<S>::ld(cur + g.rev[e], g.qscale));
+            const int c = dr.gs[gg].cur;
+            eval_vertex_bin<S, MODE == MODE_CAND>(g, (const S *)msg_buf(dr, c), (S *)msg_buf(dr, c ^ 1),
+                                                  (RT *)dr.resid, i, eps_in(rp, (A)0), maxa, cnt);
         }
     }
-    if (MODE != MODE_SPLASH)
-        reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
+    reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
 }
 
 // --------------------------------------------------------------------------
@@ -638,14 +591,9 @@ __global__ void __launch_bounds__(BLOCK) k_bfs_level(DevGraph g, DevRun dr, int 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n)
         return;
-    if (dr.gs[g.gid[i]].status != ST_RUNNING || dr.level[i] >= 0)
+    if (dr.gs[g.gid[i]].status != ST_RUNNING)
         return;
-    for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
-        if (dr.level[g.col[e]] == d - 1) {
-            dr.level[i] = (int8_t)d;
-            return;
-        }
-    }
+    bfs_vertex(g, dr, i, d);
 }
 
 // Residual Splash sub-step commit: out-messages of level-L vertices.
@@ -671,6 +619,35 @@ __global__ void __launch_bounds__(BLOCK) k_splash_commit(DevGraph g, DevRun dr, 
             for (int t = beg * epm; t < end * epm; ++t)
                 dst[t] = src[t];
             c = (unsigned int)(end - beg);
+        }
+    }
+    add_commit_counts(dr, uniform, g0, valid, gg, c, true);
+}
+
+// Residual Splash, binary messages: commit of one sweep level fused with the
+// evaluation of the next. Vertices at level Lc copy their out-messages from
+// the candidate buffer (1) to the state buffer (0); vertices at level Le
+// compute new out-messages into buffer 1, reading an incoming message from
+// buffer 1 when its source is at level Lc (written by the previous sub-step,
+// committed by this one) and from buffer 0 otherwise. Consecutive sweep levels
+// differ, so the copies and the new candidates touch disjoint messages.
+// Lc = -1: evaluation only (first sub-step); Le = -1: commit only (last).
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_splash_step(DevGraph g, DevRun dr, int Lc, int Le)
+{
+    const int first = blockIdx.x * blockDim.x;
+    const int last = min(g.n - 1, first + (int)blockDim.x - 1);
+    const int g0 = g.gid[first];
+    const bool uniform = (g0 == g.gid[last]);
+    const int i = first + threadIdx.x;
+    bool valid = false;
+    int gg = g0;
+    unsigned int c = 0;
+    if (i < g.n) {
+        gg = g.gid[i];
+        if (dr.gs[gg].status == ST_RUNNING) {
+            c = splash_vertex_bin<S>(g, dr, i, dr.level[i], Lc, Le);
+            valid = c > 0;
         }
     }
     add_commit_counts(dr, uniform, g0, valid, gg, c, true);
@@ -711,8 +688,11 @@ __global__ void k_init_state(DevRun dr, int G)
             dr.gs[t] = st;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         *dr.n_running = G;
+        if (dr.queue)
+            *dr.queue = 0;
+    }
 }
 
 // Marks every still-running graph as stopped (wall-clock budget).
@@ -819,20 +799,19 @@ static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams
                             cudaStream_t s)
 {
     int nb = blocks_for(g.n, BLOCK);
+    (void)level_L;   // binary splash sweeps use k_splash_step
     // mapping: thread per vertex (variant 1) or 256-vertex tiles with edge quads (variant 2)
     const bool tiled = rp.variant == 2;
     if (mode == MODE_LBP) {
         if (tiled)
             k_eval_bin_tiled<S, MODE_LBP><<<blocks_for(g.n, TILE_V), TILE_V, 0, s>>>(g, dr, rp);
         else
-            k_eval_bin<S, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
-    } else if (mode == MODE_CAND) {
+            k_eval_bin<S, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+    } else {
         if (tiled)
             k_eval_bin_tiled<S, MODE_CAND><<<blocks_for(g.n, TILE_V), TILE_V, 0, s>>>(g, dr, rp);
         else
-            k_eval_bin<S, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
-    } else {
-        k_eval_bin<S, MODE_SPLASH><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L);
+            k_eval_bin<S, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp);
     }
 }
 
@@ -894,6 +873,14 @@ void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int le
         return;
     int nb = blocks_for(g.n, BLOCK);
     BPG_DISPATCH4(dtype, (k_splash_commit<S><<<nb, BLOCK, 0, s>>>(g, dr, level_L)));
+}
+
+void launch_splash_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    int nb = blocks_for(g.n, BLOCK);
+    BPG_DISPATCH4(dtype, (k_splash_step<S><<<nb, BLOCK, 0, s>>>(g, dr, Lc, Le)));
 }
 
 void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s)

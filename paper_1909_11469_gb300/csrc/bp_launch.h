@@ -22,10 +22,18 @@ int select_smem_limit();
 void launch_select_rbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
 void launch_select_rs(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
 void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s);
+// Residual Splash (binary messages): commit level Lc and evaluate level Le
+// in one kernel (Lc or Le may be -1).
+void launch_splash_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s);
 void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int level_L, cudaStream_t s);
 void launch_stop_running(const DevGraph &g, const DevRun &dr, cudaStream_t s);
 void launch_beliefs(int dtype, const DevGraph &g, const DevRun &dr, int kp, cudaStream_t s);
 void launch_messages(int dtype, const DevGraph &g, const DevRun &dr, int kp, double *out, cudaStream_t s);
+
+// Persistent batch kernel (binary Ising): every round of every graph in one
+// launch, one thread-block cluster per graph at a time.
+cudaError_t launch_persistent(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp,
+                              long long budget_ns, cudaStream_t s);
 
 // Sets the calling thread's message returned by bp_last_error().
 void set_last_error(const std::string &msg);

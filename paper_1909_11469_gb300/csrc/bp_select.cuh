@@ -1,0 +1,217 @@
+// Cluster-wide exact top-k selection (device functions shared by the
+// per-round selection kernels and the persistent batch kernel).
+//
+// Every CTA of a cluster owns a contiguous slice of a graph's keys (the
+// residual's IEEE bits: non-negative floats order as unsigned integers). An
+// MSB radix select narrows the k-th largest key one byte per pass: each CTA
+// builds a 256-bin histogram of its slice, the CTAs sum the cluster's
+// histograms through distributed shared memory, and every CTA takes the same
+// digit decision. An ordered pass takes every key above the threshold and the
+// lowest-id ties, ranked across the cluster when ties straddle the threshold.
+#pragma once
+
+#include "bp_internal.cuh"
+
+#include <cooperative_groups.h>
+
+namespace bpg {
+
+namespace cg = cooperative_groups;
+
+constexpr int SEL_THREADS = 1024;
+// Keys of a CTA's slice are staged in dynamic shared memory when they fit.
+constexpr int SEL_SMEM_BYTES = 200 * 1024;
+
+__device__ __forceinline__ uint32_t key_bits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ unsigned long long key_bits(double v)
+{
+    return (unsigned long long)__double_as_longlong(v);
+}
+
+// Shared state of the cluster-wide selection (one instance per CTA).
+template <typename KeyT> struct SelShared {
+    unsigned int hist[256];
+    unsigned int total[256];
+    KeyT prefix;
+    int krem;
+    int bucket;
+    unsigned int warp_cnt[32];
+    int eq_before;    // keys equal to thr in lower-ranked CTAs of the cluster
+    int taken;        // running rank among ties inside this CTA
+    int my_eq;        // keys equal to thr in this CTA's slice
+};
+
+// Cluster-wide threshold: thr = k-th largest key over the union of the CTAs'
+// slices (1 <= k <= total count), take_eq = keys equal to thr inside the top
+// k, eq_total = keys equal to thr. Every thread of every CTA of the cluster
+// must call it.
+template <typename KeyT, typename KeyFn>
+__device__ void cluster_select_threshold(cg::cluster_group &cl, SelShared<KeyT> &sh, int n_local, int k,
+                                         KeyFn key, KeyT &thr, int &take_eq, int &eq_total)
+{
+    const unsigned C = cl.num_blocks();
+    KeyT prefix = 0, mask = 0;
+    int krem = k;
+    for (int pass = 0; pass < (int)sizeof(KeyT); ++pass) {
+        const int shift = ((int)sizeof(KeyT) - 1 - pass) * 8;
+        for (int t = threadIdx.x; t < 256; t += blockDim.x)
+            sh.hist[t] = 0u;
+        __syncthreads();
+        // one shared atomic per distinct digit per warp (residuals cluster in a
+        // few exponent bins, so per-thread atomics would serialise)
+        for (int base = 0; base < n_local; base += blockDim.x) {
+            const int idx = base + threadIdx.x;
+            unsigned d = 0xffffffffu;
+            if (idx < n_local) {
+                const KeyT kv = key(idx);
+                if ((kv & mask) == prefix)
+                    d = (unsigned)((kv >> shift) & (KeyT)255);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (d != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(&sh.hist[d], (unsigned)__popc(peers));
+        }
+        cl.sync();   // every CTA's histogram is complete
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+            unsigned s = 0;
+            for (unsigned r = 0; r < C; ++r)
+                s += cl.map_shared_rank(&sh.hist[0], r)[t];
+            sh.total[t] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // lane L owns digits 255-8L down to 248-8L (descending order)
+            const int lane = threadIdx.x;
+            unsigned loc[8];
+            unsigned sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                loc[q] = sh.total[255 - 8 * lane - q];
+                sum += loc[q];
+            }
+            unsigned incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            const unsigned excl = incl - sum;
+            if (excl < (unsigned)krem && (unsigned)krem <= incl) {
+                unsigned acc = excl;
+                int d = 255 - 8 * lane - 7;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (acc + loc[q] >= (unsigned)krem) {
+                        d = 255 - 8 * lane - q;
+                        break;
+                    }
+                    acc += loc[q];
+                }
+                sh.prefix = prefix | ((KeyT)d << shift);
+                sh.krem = krem - (int)acc;
+                sh.bucket = (int)sh.total[d];
+            }
+        }
+        cl.sync();   // nobody clears its histogram while another CTA still reads it
+        prefix = sh.prefix;
+        krem = sh.krem;
+        mask |= ((KeyT)255 << shift);
+    }
+    thr = prefix;
+    take_eq = krem;
+    eq_total = sh.bucket;
+}
+
+// Ordered pass over this CTA's slice: on_item(idx, take) for every local idx,
+// take = key above thr, or equal to thr and among the first take_eq such keys
+// of the cluster in global index order (CTA rank order, then local order).
+template <typename KeyT, typename KeyFn, typename ItemFn>
+__device__ void cluster_select_apply(cg::cluster_group &cl, SelShared<KeyT> &sh, int n_local, KeyT thr,
+                                     int take_eq, int eq_total, KeyFn key, ItemFn on_item)
+{
+    if (take_eq == eq_total) {
+        // every key equal to thr is in the top k: no ranking of ties needed
+        for (int idx = threadIdx.x; idx < n_local; idx += blockDim.x)
+            on_item(idx, key(idx) >= thr);
+        return;
+    }
+    // ties straddle the threshold: rank them across the cluster
+    if (threadIdx.x == 0)
+        sh.my_eq = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int idx = threadIdx.x; idx < n_local; idx += blockDim.x)
+        mine += key(idx) == thr;
+    if (mine)
+        atomicAdd(&sh.my_eq, mine);
+    cl.sync();
+    if (threadIdx.x == 0) {
+        int before = 0;
+        for (unsigned r = 0; r < cl.block_rank(); ++r)
+            before += *cl.map_shared_rank(&sh.my_eq, r);
+        sh.eq_before = before;
+        sh.taken = 0;
+    }
+    cl.sync();   // keep my_eq readable until every CTA has summed it
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < n_local; base += blockDim.x) {
+        const int idx = base + threadIdx.x;
+        const bool in = idx < n_local;
+        const KeyT kv = in ? key(idx) : (KeyT)0;
+        const bool gt = in && kv > thr;
+        const bool eq = in && kv == thr;
+        const unsigned b = __ballot_sync(0xffffffffu, eq);
+        if (lane == 0)
+            sh.warp_cnt[warp] = __popc(b);
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w)
+            before += (int)sh.warp_cnt[w];
+        const int rank = sh.eq_before + sh.taken + before + __popc(b & ((1u << lane) - 1u));
+        if (in)
+            on_item(idx, gt || (eq && rank < take_eq));
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < nw; ++w)
+                tot += (int)sh.warp_cnt[w];
+            sh.taken += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// Copies n keys into shared memory with eight independent loads in flight per
+// thread.
+template <typename KeyT, typename LoadFn>
+__device__ void stage_keys(int n, KeyT *s_keys, LoadFn load)
+{
+    constexpr int U = 8;
+    for (int base = threadIdx.x; base < n; base += U * blockDim.x) {
+        KeyT v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < n)
+                v[u] = load(idx);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < n)
+                s_keys[idx] = v[u];
+        }
+    }
+    __syncthreads();
+}
+
+// Slice [lo, hi) of count items owned by CTA rank r of C.
+__device__ __forceinline__ void slice_of(int count, unsigned r, unsigned C, int &lo, int &hi)
+{
+    const int per = (count + (int)C - 1) / (int)C;
+    lo = min(count, (int)r * per);
+    hi = min(count, lo + per);
+}
+
+}  // namespace bpg

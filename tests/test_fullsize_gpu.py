@@ -44,8 +44,9 @@ def _stream_opts():
     return {"cuda_stream": torch.cuda.current_stream().cuda_stream}
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.1), ("rs", 0.1)])
-def test_bench_batch_sampled_graphs(sched, par):
+def test_bench_batch_sampled_graphs(sched, par, variant):
     """50 seeds of the 100x100, beta ~ U[-2.5, 2.5] grid as one batch (the bench
     workload); graphs 0, 17 and 49 followed by the oracle for 12 rounds (3 for
     Residual Splash, whose rounds sweep 2h + 1 = 5 levels each)."""
@@ -53,7 +54,7 @@ def test_bench_batch_sampled_graphs(sched, par):
     T = 3 if sched == "rs" else 12
     with bp.Graph(batch) as g:
         st = g.run(sched, par, eps=1e-4, max_rounds=T, msg_dtype="f32", record_trace=1,
-                   trace_capacity=T, seed=0, **_stream_opts())
+                   trace_capacity=T, seed=0, kernel_variant=variant, **_stream_opts())
         bel = g.beliefs()
         tr = g.trace(sched)
         gst = g.graph_stats()
@@ -90,14 +91,16 @@ def test_ising1000_full_grid(sched, dtype, tol):
     assert np.abs(bel - ref["beliefs"]).max() < tol
 
 
-def test_er_batch_4096_sampled():
+@pytest.mark.parametrize("variant", [0, 1])
+def test_er_batch_4096_sampled(variant):
     """4096 Erdos-Renyi graphs (n log-uniform in [50, 5000], mean degree 4,
     beta ~ U[-3, 3]): every graph converges or stops on its own; sampled graphs
     match oracle runs of the same length."""
     batch = synth.er_batch(4096, seed=0)
     T = 40
     with bp.Graph(batch) as g:
-        g.run("rnbp", 0.5, eps=1e-4, max_rounds=T, msg_dtype="f64", seed=2, **_stream_opts())
+        g.run("rnbp", 0.5, eps=1e-4, max_rounds=T, msg_dtype="f64", seed=2, kernel_variant=variant,
+              **_stream_opts())
         bel = g.beliefs()
         gst = g.graph_stats()
     rng = np.random.default_rng(0)

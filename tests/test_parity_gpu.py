@@ -62,13 +62,14 @@ def follow(prob, sched, res, eps, storage="f64"):
 
 
 # ------------------------------------------------------------ FP64 exact replay
+@pytest.mark.parametrize("variant", [1, 3])
 @pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5)])
-def test_ising10_fp64_exact_replay(sched, par):
+def test_ising10_fp64_exact_replay(sched, par, variant):
     """10x10 Ising, beta ~ U[-2, 2], seeds 0..9, eps 1e-4, max 1000 rounds."""
     for seed in range(10):
         prob = synth.ising_grid(10, 2.0, seed=seed)
         ref = oracle.run(prob, sched, parallelism=par, eps=1e-4, max_rounds=1000, seed=seed)
-        res = gpu_run(prob, sched, par, 1e-4, 1000, "f64", seed=seed)
+        res = gpu_run(prob, sched, par, 1e-4, 1000, "f64", seed=seed, kernel_variant=variant)
         assert res["stats"]["converged"] == ref["converged"], seed
         assert res["stats"]["rounds"] == ref["rounds"], seed
         if ref["converged"]:
@@ -76,14 +77,20 @@ def test_ising10_fp64_exact_replay(sched, par):
             assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F64, seed
 
 
+# kernel_variant 1: per-round kernels; 3: persistent batch kernel (one cluster per graph)
+VARIANTS = [1, 3]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5), ("rnbp", 0.1), ("rbp", 0.05),
                                        ("rbp", 1e-3), ("rs", 0.02), ("rs", 0.2)])
-def test_fp64_exact_replay_trace(sched, par):
+def test_fp64_exact_replay_trace(sched, par, variant):
     """Same frontier every round, same state after 60 rounds (ragged 13x11 grid)."""
     prob = synth.ising_grid(13, 2.0, seed=4, cols=11)
     T = 60
     ref = oracle.run(prob, sched, parallelism=par, eps=1e-7, max_rounds=T, seed=5, trace_cap=T)
-    res = gpu_run(prob, sched, par, 1e-7, T, "f64", trace=T if sched != "lbp" else 0, seed=5)
+    res = gpu_run(prob, sched, par, 1e-7, T, "f64", trace=T if sched != "lbp" else 0, seed=5,
+                  kernel_variant=variant)
     assert res["stats"]["rounds"] == ref["rounds"]
     if sched != "lbp":
         assert np.array_equal(res["trace"], ref["trace"][:ref["rounds"]])
@@ -137,16 +144,17 @@ TRACE_CASES = [
 ]
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("dtype,oracle_storage,beta_max,T,tol", TRACE_CASES)
 @pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5), ("rnbp", 0.1),
                                        ("rbp", 0.01), ("rs", 0.01)])
-def test_trace_follow_ising(dtype, oracle_storage, beta_max, T, tol, sched, par):
+def test_trace_follow_ising(dtype, oracle_storage, beta_max, T, tol, sched, par, variant):
     """37x29 grid (ragged over 256-vertex blocks). A Residual Splash round sweeps
     2h + 1 = 5 levels, so its short horizon is 5 times fewer rounds."""
     prob = synth.ising_grid(37, beta_max, seed=7, cols=29)
     if T < 100 and sched == "rs":
         T = T // 5
-    res = gpu_run(prob, sched, par, 1e-4, T, dtype, trace=T, seed=3)
+    res = gpu_run(prob, sched, par, 1e-4, T, dtype, trace=T, seed=3, kernel_variant=variant)
     if T > 100 and dtype != "bf16":
         assert res["stats"]["converged"]
     ref = follow(prob, sched, res, 1e-4, oracle_storage)
@@ -211,8 +219,9 @@ def test_potts_trace_follow(dtype, tol, sched, par):
 
 
 # ------------------------------------------------------------ batches
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.05), ("rs", 0.05)])
-def test_batch_equals_independent_runs(sched, par):
+def test_batch_equals_independent_runs(sched, par, variant):
     """A batch of uneven graphs: every graph converges or stops on its own and
     matches the oracle run of that graph alone (graph id = its batch index)."""
     members = [synth.ising_grid(9, 1.0, seed=1), synth.ising_chain(300, 2.0, seed=2),
@@ -220,7 +229,7 @@ def test_batch_equals_independent_runs(sched, par):
                synth.ising_grid(3, 0.0, seed=5)]
     members += [synth.er_batch(1, seed=s, n_min=30, n_max=200).graph(0) for s in range(5)]
     batch = synth.concat_batch(members)
-    res = gpu_run(batch, sched, par, 1e-5, 500, "f64", seed=9)
+    res = gpu_run(batch, sched, par, 1e-5, 500, "f64", seed=9, kernel_variant=variant)
     gstats = res["graph_stats"]
     for gi, m in enumerate(members):
         ref = oracle.run(m, sched, parallelism=par, eps=1e-5, max_rounds=500, seed=9, graph_id=gi)
@@ -299,10 +308,12 @@ def test_errors_on_device():
         bp.bp_destroy_graph(h)
 
 
-def test_time_budget_stops_cleanly():
+@pytest.mark.parametrize("variant", [1, 3])
+def test_time_budget_stops_cleanly(variant):
     prob = synth.ising_grid(60, 3.0, seed=1)
     with bp.Graph(prob) as g:
-        st = g.run("rbp", 1e-4, eps=1e-12, max_rounds=10_000_000, time_budget_ms=50.0)
+        st = g.run("rbp", 1e-4, eps=1e-12, max_rounds=10_000_000, time_budget_ms=50.0,
+                   kernel_variant=variant)
         assert st["status"] == bp.BP_ERR_TIMEOUT and not st["converged"]
         b = g.beliefs()
         assert np.all(np.isfinite(b)) and np.allclose(b.sum(1), 1.0)
