@@ -43,6 +43,9 @@ WORKLOADS = {
     "ising1000x1000_b3": dict(
         kind="grid_batch", side=1000, beta_max=3.0, lam_max=1.0, n_seeds=1, eps=1e-4, dtype="f32",
         schedules=[("lbp", 1.0), ("rnbp", 0.5)]),
+    # Potts 256x256, k = 32, unary ~ N(0, 1), one shared table I + N(0, 0.3) noise, RnBP 0.5
+    "potts256_k32": dict(
+        kind="potts", side=256, k=32, eps=1e-4, dtype="f32", schedules=[("rnbp", 0.5)]),
     # 4096 Erdos-Renyi graphs, n log-uniform in [50, 5000], mean degree 4, beta ~ U[-3, 3]
     "er4096_b3": dict(
         kind="er_batch", n_graphs=4096, beta_max=3.0, lam_max=1.0, eps=1e-4, dtype="f32",
@@ -58,9 +61,19 @@ MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
 BYTES_PER_VERTEX = 12
 
 
-def bytes_per_msg(sched: str, dtype: str) -> int:
+def bytes_per_msg(sched: str, dtype: str, k: int = 2) -> int:
+    """Per evaluated message: rev, incoming message, old message, new message
+    (k values each for k-state messages, one log-odds for binary ones), the
+    Ising exp(-2 beta) (binary only), + the residual in the frontier modes."""
     s = MSG_BYTES[dtype]
-    return 8 + 3 * s + (0 if sched == "lbp" else (8 if dtype == "f64" else 4))
+    if k == 2:
+        return 8 + 3 * s + (0 if sched == "lbp" else (8 if dtype == "f64" else 4))
+    return 4 + 3 * k * s + (0 if sched == "lbp" else 4)
+
+
+def bytes_per_vertex(k: int = 2) -> int:
+    """Per processed vertex: row_ptr, graph id, unary (one log-odds, or k logs)."""
+    return 12 if k == 2 else 8 + 4 * k
 
 
 ROUNDS_SCALE = 1.0
@@ -75,7 +88,7 @@ def batch_kernel_bytes(sched: str, dtype: str, st: dict, pr: dict) -> float:
     the source level, the incoming message and exp(-2 beta) and writes the
     candidate (13 + 2 s B), then commits it (2 s B)."""
     s = MSG_BYTES[dtype]
-    b = bytes_per_msg(sched, dtype) * pr["full_evals"] + BYTES_PER_VERTEX * pr["active_vertices"]
+    b = bytes_per_msg(sched, dtype) * pr["full_evals"] + bytes_per_vertex() * pr["active_vertices"]
     if sched in ("rnbp", "rbp"):
         b += 4 * pr["full_evals"] + 2 * s * st["committed_updates"]
     elif sched == "rs":
@@ -83,18 +96,18 @@ def batch_kernel_bytes(sched: str, dtype: str, st: dict, pr: dict) -> float:
     return b
 
 
-def eval_roofline(step, dtype: str, peak: float, peak_src: str):
+def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kernel: str = ""):
     """Roofline of the per-round message-update kernel from a profiled step."""
     alg_bytes, eval_ms, eval_launches = 0.0, 0.0, 0
     phase = {"eval_ms": 0.0, "decide_ms": 0.0, "frontier_ms": 0.0}
     for sched, p, st, pr, gst in step:
-        alg_bytes += bytes_per_msg(sched, dtype) * pr["full_evals"] + BYTES_PER_VERTEX * pr["active_vertices"]
+        alg_bytes += bytes_per_msg(sched, dtype, k) * pr["full_evals"] + bytes_per_vertex(k) * pr["active_vertices"]
         eval_ms += pr["eval_ms"]
         eval_launches += pr["eval_launches"]
         for k in phase:
             phase[k] += pr[k]
     achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
-    return ({"bound": "hbm", "kernel": f"k_eval_bin ({dtype} messages; Eq. 2 + Eq. 4 + reduction)",
+    return ({"bound": "hbm", "kernel": kernel or f"k_eval_bin ({dtype} messages; Eq. 2 + Eq. 4 + reduction)",
              "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_source": peak_src,
              "frac": (achieved / peak) if achieved else None, "traffic": None,
              "launches": eval_launches, "bytes_per_launch": alg_bytes / max(eval_launches, 1),
@@ -116,6 +129,8 @@ def make_batch(wl, rank: int):
     if wl["kind"] == "er_batch":
         return synth.er_batch(wl["n_graphs"], seed=rank, beta_max=wl["beta_max"],
                               lam_max=wl["lam_max"])
+    if wl["kind"] == "potts":
+        return synth.potts_grid(wl["side"], wl["k"], seed=rank)
     seeds = range(rank * wl["n_seeds"], (rank + 1) * wl["n_seeds"])
     if wl["n_seeds"] == 1:
         return synth.ising_grid(wl["side"], wl["beta_max"], rank, wl["lam_max"])
@@ -179,6 +194,8 @@ def oracle_sample(wl, budget_rounds: int, seed: int = 0):
     from paper_1909_11469_gb300 import synth
     if wl["kind"] == "er_batch":
         prob = synth.er_batch(1, seed=seed, beta_max=wl["beta_max"], lam_max=wl["lam_max"])
+    elif wl["kind"] == "potts":
+        prob = synth.potts_grid(wl["side"], wl["k"], seed=seed)
     else:
         prob = synth.ising_grid(wl["side"], wl["beta_max"], seed, wl["lam_max"])
     committed, t = 0, 0.0
@@ -241,6 +258,9 @@ def main():
                          "(profiler passes only)")
     ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2],
                     help="binary update mapping (0 = library's choice)")
+    ap.add_argument("--potts-path", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="shared-table update: 0 automatic, 1 CUDA cores, 2 tensor cores BF16, "
+                         "3 tensor cores split")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "q16", "f64"],
                     help="message storage (default: the workload's)")
     args = ap.parse_args()
@@ -278,7 +298,8 @@ def main():
 
     def opts(**kw):
         return bp.bp_default_options(msg_dtype=wl["dtype"], cuda_stream=stream.cuda_stream,
-                                     graph_id_base=rank * G, kernel_variant=args.kernel_variant, **kw)
+                                     graph_id_base=rank * G, kernel_variant=args.kernel_variant,
+                                     potts_path=args.potts_path, **kw)
 
     def one_step(profile: int):
         out = []
@@ -357,7 +378,12 @@ def main():
         args.kernel_variant = saved
         update_roofline, phase = eval_roofline(upd_step, wl["dtype"], peak, peak_src)
     elif prof_step:
-        roofline, phase = eval_roofline(prof_step, wl["dtype"], peak, peak_src)
+        kname = ""
+        if prob.k > 2:
+            kname = {1: "k_eval_gen (CUDA cores)", 2: "k_potts_tc (tcgen05, BF16 products)",
+                     3: "k_potts_tc (tcgen05, split BF16 products)"}.get(
+                        args.potts_path or (3 if prob.k >= 16 else 1), "")
+        roofline, phase = eval_roofline(prof_step, wl["dtype"], peak, peak_src, prob.k, kname)
     per_sched = {}
     for step in results:
         for sched, p, st, pr, gst in step:
@@ -411,7 +437,8 @@ def main():
             "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
             "config": {"workload": args.workload, "graphs_per_gpu": G,
                        "rounds_scale": args.rounds_scale, "direct_launch": bool(args.direct_launch),
-                       "vertices": int(prob.n), "directed_messages": int(prob.m),
+                       "vertices": int(prob.n), "directed_messages": int(prob.m), "states": int(prob.k),
+                       "potts_path": args.potts_path,
                        "eps": wl["eps"], "schedules": [f"{s}:{p}" for s, p in wl["schedules"]],
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"dp{world}" if world > 1 else "single"},

@@ -111,6 +111,12 @@ typedef struct {
                                  kernel: one thread-block cluster per graph runs all of
                                  its rounds in a single launch */
     int32_t profile;          /* 1: time every round's phases with CUDA events (default 0) */
+    int32_t potts_path;       /* shared-table (BP_PAIR_SHARED) update, FP32/BF16 storage,
+                                 tiles of <= 128 edges: 0 = automatic (3 for k >= 16,
+                                 else the per-vertex k-state kernel), 1 = tiles on the
+                                 CUDA cores, 2 = tiles on the tensor cores with BF16
+                                 products, 3 = tensor cores with the BF16 residual
+                                 products added (close to FP32) */
 } bp_options;
 
 /* Phase timings and launch counts of the last bp_run. The timings are filled

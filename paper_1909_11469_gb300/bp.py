@@ -58,7 +58,8 @@ class bp_options(ctypes.Structure):
                 ("record_trace", ctypes.c_int32), ("trace_capacity", ctypes.c_int32),
                 ("rounds_per_launch", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("time_budget_ms", ctypes.c_double), ("graph_id_base", ctypes.c_uint32),
-                ("kernel_variant", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("kernel_variant", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("potts_path", ctypes.c_int32)]
 
 
 class bp_profile(ctypes.Structure):

@@ -101,6 +101,11 @@ struct bp_graph {
     int32_t *d_running = nullptr;
     int32_t *d_queue = nullptr;
     int32_t max_graph_vertices = 0;
+    // tensor-core tiles of consecutive vertices (<= 128 out-edges, <= 32 vertices)
+    int32_t *d_tc_tiles = nullptr;
+    int32_t n_tc_tiles = 0;
+    bool tc_tiles_ok = false;
+    int32_t *d_err = nullptr;
     uint32_t *d_trace = nullptr;
     size_t trace_alloc_words = 0;
     double *d_beliefs = nullptr;
@@ -271,6 +276,7 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     // Everything above is host-side validation; device work starts here.
     cudaGetDevice(&g->dev);
     prepare_select_kernels();
+    prepare_potts_tc();
     g->n = n;
     g->k = k;
     g->M = M;
@@ -309,6 +315,35 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
         (rc = dalloc(&g->d_level, (size_t)std::max(n, 1))) ||
         (rc = dalloc(&g->d_beliefs, (size_t)n * (size_t)k)))
         return rc;
+    {
+        // tensor-core tiles: greedy runs of vertices, at most 128 edges and 32 vertices
+        std::vector<int32_t> tv;
+        tv.push_back(0);
+        bool ok = true;
+        int32_t cur_v = 0;
+        int64_t cur_e = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            const int64_t d = row_ptr[i + 1] - row_ptr[i];
+            if (d > 128)
+                ok = false;
+            if (cur_v > 0 && (cur_v + 1 > 32 || cur_e + d > 128)) {
+                tv.push_back(i);
+                cur_v = 0;
+                cur_e = 0;
+            }
+            ++cur_v;
+            cur_e += d;
+        }
+        if (n > 0)
+            tv.push_back(n);
+        g->tc_tiles_ok = ok;
+        g->n_tc_tiles = (int32_t)tv.size() - 1;
+        if ((rc = dalloc(&g->d_tc_tiles, tv.size())))
+            return rc;
+        BP_CK(cudaMemcpy(g->d_tc_tiles, tv.data(), sizeof(int32_t) * tv.size(), cudaMemcpyHostToDevice));
+        if ((rc = dalloc(&g->d_err, 1)))
+            return rc;
+    }
     BP_CK(cudaMallocHost((void **)&g->h_running, sizeof(int32_t)));
     BP_CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     BP_CK(cudaEventCreate(&g->ev0));
@@ -348,7 +383,11 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
     int64_t kernels = 0;
     if (ev)
         cudaEventRecord(ev[0], s);
-    launch_eval(dtype, dg, dr, rp, rp.schedule == SCHED_LBP ? MODE_LBP : MODE_CAND, 0, g->kp, s);
+    const int emode = rp.schedule == SCHED_LBP ? MODE_LBP : MODE_CAND;
+    if (rp.tc_path)
+        launch_potts_tc(dtype, dg, dr, rp, emode, g->d_tc_tiles, g->n_tc_tiles, rp.tc_path, g->d_err, s);
+    else
+        launch_eval(dtype, dg, dr, rp, emode, 0, g->kp, s);
     kernels += any;
     if (ev)
         cudaEventRecord(ev[1], s);
@@ -478,6 +517,7 @@ void bp_default_options(bp_options *opt)
     opt->graph_id_base = 0;
     opt->kernel_variant = 0;
     opt->profile = 0;
+    opt->potts_path = 0;
 }
 
 int bp_create_graph(int32_t n_vars, int32_t n_states, int64_t n_dir_edges, const int64_t *row_ptr,
@@ -630,6 +670,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_UNSUPPORTED, "Q16 storage needs the binary Ising layout");
     if (!(opt.high_p >= 0.0) || !std::isfinite(opt.high_p) || !std::isfinite(opt.ratio_threshold))
         return fail(BP_ERR_INVALID_ARG, "bad high_p or ratio_threshold");
+    if (opt.potts_path < 0 || opt.potts_path > 3)
+        return fail(BP_ERR_INVALID_ARG, "potts_path must be 0..3");
     if (opt.kernel_variant < 0 || opt.kernel_variant > 3)
         return fail(BP_ERR_INVALID_ARG, "kernel_variant must be 0, 1, 2 or 3");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
@@ -660,6 +702,18 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     rp.trace_words = (int32_t)((trace_count + 31) / 32);
     rp.variant = opt.kernel_variant == 2 ? 2 : 1;
     rp.eps_f = float_at_least(eps);
+    // shared-table update in vertex tiles: 0 = per-vertex k-state kernel,
+    // 1 = tiles on CUDA cores, 2 = tiles on tensor cores, 3 = tensor cores split
+    rp.tc_path = 0;
+    if (g->pair_kind == BP_PAIR_SHARED && g->tc_tiles_ok && (dtype == BP_F32 || dtype == BP_BF16)) {
+        if (opt.potts_path >= 1)
+            rp.tc_path = opt.potts_path;
+        else if (g->k >= 16)
+            rp.tc_path = 3;
+    }
+    if (opt.potts_path >= 1 && rp.tc_path == 0)
+        return fail(BP_ERR_UNSUPPORTED, "the tiled shared-table update needs a shared table, FP32/BF16 "
+                                        "storage and vertices with at most 128 out-edges");
     if (rp.record_trace) {
         size_t words = (size_t)rp.trace_capacity * (size_t)rp.trace_words;
         if (words > g->trace_alloc_words) {
@@ -680,6 +734,7 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     BP_CK(cudaEventRecord(g->ev0, s));
     launch_init(dtype, dg, dr, s);
     kernels += ((size_t)g->M * g->k > 0) + 1;
+    BP_CK(cudaMemsetAsync(g->d_err, 0, sizeof(int32_t), s));
     if (rp.record_trace)
         BP_CK(cudaMemsetAsync(g->d_trace, 0, sizeof(uint32_t) * (size_t)rp.trace_capacity * rp.trace_words, s));
     BP_CK(cudaGetLastError());
@@ -768,6 +823,12 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     BP_CK(cudaStreamSynchronize(s));
     float ms = 0.f;
     BP_CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    {
+        int32_t h_err = 0;
+        BP_CK(cudaMemcpy(&h_err, g->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (h_err)
+            return fail(BP_ERR_CUDA, "a tensor-core completion wait expired; results are invalid");
+    }
     if (persistent) {
         BP_CK(cudaEventElapsedTime(&batch_ms, g->ev_pt0, g->ev_pt1));
         for (const GState &st : hs)
@@ -943,6 +1004,8 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_red_cnt);
     dfree(g->d_running);
     dfree(g->d_queue);
+    dfree(g->d_tc_tiles);
+    dfree(g->d_err);
     dfree(g->d_trace);
     dfree(g->d_beliefs);
     if (g->h_running)

@@ -72,6 +72,8 @@ struct RunParams {
     int32_t trace_words;      // words per recorded round
     int32_t variant;          // binary update mapping: 1 thread per vertex, 2 tiled edge quads
     float eps_f;              // smallest float >= eps: (double)r >= eps  <=>  r >= eps_f for float r
+    int32_t tc_path;          // shared-table update: 0 per-vertex, 1 tiles/CUDA cores, 2 tiles/tensor
+                              // cores, 3 tiles/tensor cores with residual products
 };
 
 // eps in the residual type, chosen so that the comparison equals the FP64 test.

@@ -35,6 +35,14 @@ void launch_messages(int dtype, const DevGraph &g, const DevRun &dr, int kp, dou
 cudaError_t launch_persistent(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp,
                               long long budget_ns, cudaStream_t s);
 
+// Shared-table (Potts) update in tiles of consecutive vertices with at most
+// 128 out-edges and 32 vertices (tile_v, n_tiles + 1 entries); path 1 = CUDA
+// cores, 2 = tensor cores with BF16 products, 3 = tensor cores with the BF16
+// residual products added. FP32 or BF16 storage.
+void prepare_potts_tc();
+void launch_potts_tc(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode,
+                     const int *tile_v, int n_tiles, int path, int *err_flag, cudaStream_t s);
+
 // Sets the calling thread's message returned by bp_last_error().
 void set_last_error(const std::string &msg);
 

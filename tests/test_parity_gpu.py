@@ -319,3 +319,53 @@ def test_time_budget_stops_cleanly(variant):
         assert np.all(np.isfinite(b)) and np.allclose(b.sum(1), 1.0)
         st2 = g.run("lbp", 1.0, eps=1e-4, max_rounds=5)
         assert st2["status"] == 0 and st2["rounds"] == 5
+
+
+# ------------------------------------------------------------ Potts update paths
+@pytest.mark.parametrize("path,dtype,tol", [(1, "f32", TOL_F32), (3, "f32", TOL_F32),
+                                            (2, "f32", TOL_BF16), (3, "bf16", TOL_BF16),
+                                            (2, "bf16", 1.6e-2)])
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5)])
+def test_potts_update_paths(path, dtype, tol, sched, par):
+    """Shared k = 32 table on a 20x20 grid: CUDA cores (1), tensor cores BF16 (2)
+    and tensor cores with the BF16 residual products (3), against the oracle
+    following the GPU frontiers (BF16 storage: the BF16-emulating oracle).
+    Tensor-core BF16 products keep 8 significant bits per factor, so path 2 is
+    held to the BF16 tolerance; with BF16 storage as well its product rounding is
+    not emulated by the oracle and it gets the BF16 storage flip bound (1.6e-2)."""
+    prob = synth.potts_grid(20, 32, seed=5)
+    res = gpu_run(prob, sched, par, 1e-4, 25, dtype, trace=25, seed=4, potts_path=path)
+    ref = follow(prob, sched, res, 1e-4, "bf16" if dtype == "bf16" else "f64")
+    err = np.abs(res["beliefs"] - ref["beliefs"]).max()
+    print(f"potts path {path} {dtype} {sched}: {err:.3e}")
+    assert err < tol, err
+
+
+@pytest.mark.gpu
+def test_potts_tensor_core_ragged_tiles():
+    """k = 20 (states padded to 32) on an irregular graph whose tiles hold
+    uneven vertex and edge counts."""
+    row_ptr, col, rev = synth.csr_from_undirected(*_random_graph(300, 700, seed=2))
+    rng = np.random.default_rng(3)
+    k = 20
+    theta = np.eye(k) + np.triu(rng.normal(0, 0.3, (k, k)))
+    theta = np.triu(theta) + np.triu(theta, 1).T
+    prob = synth.Problem(300, k, row_ptr, col, rev, rng.standard_normal(300 * k).astype(np.float32),
+                         synth.PAIR_SHARED, theta.astype(np.float32).ravel(), np.array([0, 300], np.int64))
+    res = gpu_run(prob, "lbp", 1.0, 1e-4, 20, "f32", potts_path=3)
+    ref = oracle.run(prob, "lbp", eps=1e-4, trace_in=all_ones_trace(prob.m, res["stats"]["rounds"]),
+                     trace_rounds=res["stats"]["rounds"])
+    assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F32
+
+
+def _random_graph(n, m, seed):
+    rng = np.random.default_rng(seed)
+    seen = set()
+    ei, ej = [], []
+    while len(seen) < m:
+        a, b = (int(x) for x in rng.integers(0, n, 2))
+        if a != b and (min(a, b), max(a, b)) not in seen:
+            seen.add((min(a, b), max(a, b)))
+            ei.append(a)
+            ej.append(b)
+    return n, np.array(ei), np.array(ej)
