@@ -47,9 +47,11 @@ WORKLOADS = {
     "potts256_k32": dict(
         kind="potts", side=256, k=32, eps=1e-4, dtype="f32", schedules=[("rnbp", 0.5)]),
     # 4096 Erdos-Renyi graphs, n log-uniform in [50, 5000], mean degree 4, beta ~ U[-3, 3]
+    # (mapping autotuned per size class; RnBP LowP tuned per graph-size class
+    # among 0.1 .. 0.9 in setup; per-graph launches timed on a sample of graphs)
     "er4096_b3": dict(
         kind="er_batch", n_graphs=4096, beta_max=3.0, lam_max=1.0, eps=1e-4, dtype="f32",
-        schedules=[("rnbp", 0.5), ("lbp", 1.0)]),
+        schedules=[("rnbp", 0.5), ("lbp", 1.0)], autotune=True),
 }
 DEFAULT_WORKLOAD = "ising100x100_b2.5_50seeds"
 L2_FLUSH_BYTES = 512 << 20          # > 126 MB of L2
@@ -104,14 +106,62 @@ def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kern
         alg_bytes += bytes_per_msg(sched, dtype, k) * pr["full_evals"] + bytes_per_vertex(k) * pr["active_vertices"]
         eval_ms += pr["eval_ms"]
         eval_launches += pr["eval_launches"]
-        for k in phase:
-            phase[k] += pr[k]
+        for key in phase:
+            phase[key] += pr[key]
     achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
     return ({"bound": "hbm", "kernel": kernel or f"k_eval_bin ({dtype} messages; Eq. 2 + Eq. 4 + reduction)",
              "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_source": peak_src,
              "frac": (achieved / peak) if achieved else None, "traffic": None,
              "launches": eval_launches, "bytes_per_launch": alg_bytes / max(eval_launches, 1),
              "avg_launch_us": 1e3 * eval_ms / max(eval_launches, 1)}, phase)
+
+
+def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str):
+    """Roofline of the Residual Splash sweep kernel (k_splash_list_step) from a
+    profiled step. The sweeps run over per-level vertex lists: per evaluated
+    message rev, col, the source's level, the incoming message, exp(-2 beta) and
+    the written candidate (13 + 2 s B), per evaluated vertex its list entry,
+    row_ptr and unary log-odds (16 B, spread over its d-bar out-messages); per
+    committed message a read and a write of s bytes, per committed vertex its
+    list entry and row_ptr (12 B). Every evaluated message is committed once."""
+    s = MSG_BYTES[dtype]
+    dbar = m / max(n, 1)
+    b, ms, launches = 0.0, 0.0, 0
+    for sched, p, st, pr, gst in step:
+        if sched != "rs" or pr["sweep_launches"] == 0:
+            continue
+        upd = st["committed_updates"]
+        b += upd * (13 + 2 * s + 16 / dbar) + upd * (2 * s + 12 / dbar)
+        ms += pr["sweep_ms"]
+        launches += pr["sweep_launches"]
+    if ms <= 0:
+        return None
+    a = b / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": f"k_splash_list_step ({dtype} messages; Residual Splash sweep over "
+            "level lists: commit of one level fused with the evaluation of the next)", "achieved": a,
+            "peak": peak, "unit": "GB/s", "peak_source": peak_src, "frac": a / peak, "traffic": None,
+            "launches": launches, "bytes_per_launch": b / launches, "avg_launch_us": 1e3 * ms / launches}
+
+
+def select_roofline(step, dtype: str, peak: float, peak_src: str):
+    """Roofline of the selection kernels (RBP / RS top-k, RnBP commit) from a
+    profiled step: every residual read once per round (4 B) plus a read and a
+    write of each committed message."""
+    s = MSG_BYTES[dtype]
+    b, ms, launches = 0.0, 0.0, 0
+    for sched, p, st, pr, gst in step:
+        if sched == "lbp":
+            continue
+        b += 4 * pr["full_evals"] + (2 * s * st["committed_updates"] if sched != "rs" else 0)
+        ms += pr["select_ms"]
+        launches += pr["eval_launches"]
+    if ms <= 0:
+        return None
+    a = b / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": "k_select_rbp / k_select_rs / k_commit_rnbp (frontier selection)",
+            "achieved": a, "peak": peak, "unit": "GB/s", "peak_source": peak_src, "frac": a / peak,
+            "traffic": None, "launches": launches, "bytes_per_launch": b / max(launches, 1),
+            "avg_launch_us": 1e3 * ms / max(launches, 1)}
 
 
 def round_cap(sched: str, p: float) -> int:
@@ -124,14 +174,14 @@ def round_cap(sched: str, p: float) -> int:
     return max(1, int(round(base * ROUNDS_SCALE)))
 
 
-def make_batch(wl, rank: int):
-    from paper_1909_11469_gb300 import synth
+def make_batch(wl, rank: int, world: int = 1):
+    from paper_1909_11469_gb300 import shard, synth
     if wl["kind"] == "er_batch":
         return synth.er_batch(wl["n_graphs"], seed=rank, beta_max=wl["beta_max"],
                               lam_max=wl["lam_max"])
     if wl["kind"] == "potts":
         return synth.potts_grid(wl["side"], wl["k"], seed=rank)
-    seeds = range(rank * wl["n_seeds"], (rank + 1) * wl["n_seeds"])
+    seeds = shard.shard_seeds(rank, world, wl["n_seeds"])
     if wl["n_seeds"] == 1:
         return synth.ising_grid(wl["side"], wl["beta_max"], rank, wl["lam_max"])
     return synth.ising_grid_batch(wl["side"], wl["beta_max"], seeds, wl["lam_max"])
@@ -256,13 +306,16 @@ def main():
     ap.add_argument("--direct-launch", action="store_true",
                     help="timed steps launch kernels directly instead of replaying CUDA graphs "
                          "(profiler passes only)")
-    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="binary update mapping (0 = library's choice)")
     ap.add_argument("--potts-path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="shared-table update: 0 automatic, 1 CUDA cores, 2 tensor cores BF16, "
                          "3 tensor cores split")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "q16", "f64"],
                     help="message storage (default: the workload's)")
+    ap.add_argument("--autotune", type=int, default=None, choices=[0, 1],
+                    help="tune the update mapping (and RnBP LowP per size class) in setup "
+                         "(default: the workload's setting)")
     args = ap.parse_args()
     global ROUNDS_SCALE
     ROUNDS_SCALE = args.rounds_scale
@@ -290,15 +343,18 @@ def main():
     __graft_entry__.build()
     from paper_1909_11469_gb300 import bp
 
-    prob = make_batch(wl, rank)
+    prob = make_batch(wl, rank, world)
     stream = torch.cuda.current_stream()
     g = bp.Graph(prob)
     G = prob.n_graphs
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    from paper_1909_11469_gb300 import shard
+
     def opts(**kw):
         return bp.bp_default_options(msg_dtype=wl["dtype"], cuda_stream=stream.cuda_stream,
-                                     graph_id_base=rank * G, kernel_variant=args.kernel_variant,
+                                     graph_id_base=shard.graph_id_base(rank, G),
+                                     kernel_variant=args.kernel_variant,
                                      potts_path=args.potts_path, **kw)
 
     def one_step(profile: int):
@@ -307,6 +363,22 @@ def main():
             st = bp.bp_run(g.handle, sched, p, wl["eps"], round_cap(sched, p), opts(profile=profile))
             out.append((sched, p, st, bp.bp_get_profile(g.handle), bp.bp_get_graph_stats(g.handle)))
         return out
+
+    tuning = None
+    if (wl.get("autotune", False) if args.autotune is None else bool(args.autotune)) and prob.k == 2:
+        # setup, untimed: mapping per schedule (size class of this batch), then
+        # RnBP LowP per graph-size class
+        tuning = {"mapping": {}}
+        for sched, p in wl["schedules"]:
+            r = bp.bp_autotune(g.handle, sched, p, wl["eps"], opts(), 16)
+            tuning["mapping"][sched] = {"kernel_variant": r["kernel_variant"],
+                                        "ms_per_round": [round(x, 4) for x in r["ms_per_round"]]}
+        if any(sched == "rnbp" for sched, _ in wl["schedules"]):
+            cand = [0.1, 0.3, 0.5, 0.7, 0.9]
+            gp = bp.bp_autotune_parallelism(g.handle, "rnbp", cand, wl["eps"], 1000, opts())
+            sizes = np.diff(prob.graph_var_offsets)
+            cls = np.floor(np.log2(np.maximum(sizes, 1))).astype(int)
+            tuning["rnbp_low_p_by_log2_size"] = {int(c): float(gp[np.argmax(cls == c)]) for c in np.unique(cls)}
 
     for _ in range(max(args.warmup, 0)):
         one_step(0)
@@ -331,18 +403,12 @@ def main():
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-
     committed = sum(st["committed_updates"] for step in results for (_, _, st, _, _) in step)
     evals = sum(st["candidate_evals"] for step in results for (_, _, st, _, _) in step)
     launches = sum(pr["kernel_launches"] for step in results for (_, _, _, pr, _) in step)
     if world > 1:
-        t = torch.tensor([committed, evals, launches], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t)
-        committed, evals, launches = (int(x) for x in t.tolist())
+        total_ms, (committed, evals, launches) = shard.reduce_step_stats(
+            dist, "cuda", total_ms, [committed, evals, launches])
     value = committed / (total_ms / 1e3)
 
     # Roofline. One more step of the same workload with profiling: the
@@ -380,10 +446,17 @@ def main():
     elif prof_step:
         kname = ""
         if prob.k > 2:
-            kname = {1: "k_eval_gen (CUDA cores)", 2: "k_potts_tc (tcgen05, BF16 products)",
+            kname = {1: "k_potts_tc (CUDA cores)", 2: "k_potts_tc (tcgen05, BF16 products)",
                      3: "k_potts_tc (tcgen05, split BF16 products)"}.get(
-                        args.potts_path or (3 if prob.k >= 16 else 1), "")
-        roofline, phase = eval_roofline(prof_step, wl["dtype"], peak, peak_src, prob.k, kname)
+                        args.potts_path or (3 if prob.k >= 16 else 0), "k_eval_gen")
+        update_roofline, phase = eval_roofline(prof_step, wl["dtype"], peak, peak_src, prob.k, kname)
+        phase["select_ms"] = sum(pr["select_ms"] for _, _, _, pr, _ in prof_step)
+        phase["sweep_ms"] = sum(pr["sweep_ms"] for _, _, _, pr, _ in prof_step)
+        # the dominant kernel class of the step gets the roofline
+        cands = [(phase["eval_ms"], update_roofline),
+                 (phase["sweep_ms"], sweep_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src)),
+                 (phase["select_ms"], select_roofline(prof_step, wl["dtype"], peak, peak_src))]
+        roofline = max((c for c in cands if c[1] is not None), key=lambda c: c[0])[1]
     per_sched = {}
     for step in results:
         for sched, p, st, pr, gst in step:
@@ -397,6 +470,29 @@ def main():
     for d in per_sched.values():
         d["batch_ms"] = float(np.median(d.pop("ms")))
         d["committed_updates"] //= args.steps
+        d["graphs_per_s"] = G / (d["batch_ms"] / 1e3)
+
+    # batches: the same graphs launched one handle per graph, on a sample of
+    # 64 graphs spread over the batch (per-graph launches vs the batched run)
+    per_graph = None
+    if G >= 256 and rank == 0:
+        idx = np.linspace(0, G - 1, 64).astype(int)
+        tot_ms = {f"{sched}_p{p}": 0.0 for sched, p in wl["schedules"]}
+        for q in idx:
+            sub = prob.graph(int(q))
+            with bp.Graph(sub) as h:
+                for sched, p in wl["schedules"]:
+                    pq = p
+                    if sched == "rnbp" and tuning and "rnbp_low_p_by_log2_size" in tuning:
+                        nq = int(prob.graph_var_offsets[q + 1] - prob.graph_var_offsets[q])
+                        pq = tuning["rnbp_low_p_by_log2_size"][int(np.floor(np.log2(max(nq, 1))))]
+                    o = bp.bp_default_options(msg_dtype=wl["dtype"], cuda_stream=stream.cuda_stream,
+                                              graph_id_base=int(q))
+                    bp.bp_run(h.handle, sched, pq, wl["eps"], round_cap(sched, p), o)   # warm-up
+                    st = bp.bp_run(h.handle, sched, pq, wl["eps"], round_cap(sched, p), o)
+                    tot_ms[f"{sched}_p{p}"] += st["device_ms"]
+        per_graph = {k: {"graphs_per_s": len(idx) / (v / 1e3), "sample_graphs": len(idx)}
+                     for k, v in tot_ms.items()}
 
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
@@ -444,6 +540,7 @@ def main():
                        "parallelism": f"dp{world}" if world > 1 else "single"},
             "candidate_evals_per_s": evals / (total_ms / 1e3),
             "schedules": per_sched,
+            "per_graph_launches": per_graph, "tuning": tuning,
             "profiled_step_phase_ms": phase,
             "roofline": roofline, "update_kernel_roofline": update_roofline,
             "e2e": e2e, "cpu_baseline": cpu,

@@ -105,11 +105,16 @@ typedef struct {
     void *cuda_stream;        /* cudaStream_t to run on (NULL = the legacy default stream) */
     double time_budget_ms;    /* wall-clock budget of bp_run, 0 = none */
     uint32_t graph_id_base;   /* Philox graph id of graph 0 of the handle (default 0) */
-    int32_t kernel_variant;   /* binary Ising path: 0 = automatic (currently 1), 1 =
+    int32_t kernel_variant;   /* binary Ising update mapping (every mapping computes the
+                                 same bits): 0 = automatic (the choice bp_autotune
+                                 recorded for the handle's size class, else 4 when no
+                                 vertex has more than 4 edges and 1 otherwise), 1 =
                                  per-round kernels, one thread per vertex, 2 = per-round,
                                  256-vertex tiles with 4-edge quads, 3 = persistent batch
                                  kernel: one thread-block cluster per graph runs all of
-                                 its rounds in a single launch */
+                                 its rounds in a single launch, 4 = one thread per vertex
+                                 with the graph arrays of 4 edges prefetched in parallel
+                                 with the graph's status, 5 = the same with 8 edges */
     int32_t profile;          /* 1: time every round's phases with CUDA events (default 0) */
     int32_t potts_path;       /* shared-table (BP_PAIR_SHARED) update, FP32/BF16 storage,
                                  tiles of <= 128 edges: 0 = automatic (3 for k >= 16,
@@ -137,10 +142,23 @@ typedef struct {
     double frontier_ms;        /* summed duration of selection / splash / commit */
     double batch_kernel_ms;    /* duration of the persistent batch kernel (always recorded
                                   when that kernel ran; 0 otherwise) */
+    double select_ms;          /* part of frontier_ms: selection, RnBP commit, splash levels */
+    double sweep_ms;           /* part of frontier_ms: the Residual Splash sweeps */
+    int64_t sweep_launches;    /* fused sweep-step launches (binary RS), counted with sweep_ms */
 } bp_profile;
 
 /* Fills *opt with the defaults listed above. */
 void bp_default_options(bp_options *opt);
+
+/* Result of bp_autotune. */
+typedef struct {
+    int32_t kernel_variant;    /* the fastest mapping measured (1 to 5) */
+    int32_t size_class;        /* the key it was recorded under: schedule (bits 0-1), msg_dtype
+                                  (2-3), floor(log2(n_vars / n_graphs)) (4-8),
+                                  floor(log2(n_graphs)) (9-13), largest vertex degree
+                                  <= 4 / <= 8 / more (14-15) */
+    double ms_per_round[6];    /* measured device ms per round, index = mapping; 0 = not tried */
+} bp_tune_result;
 
 /*
  * Creates a handle for one graph. n_states = k (uniform over vertices,
@@ -192,6 +210,14 @@ int bp_get_beliefs(const bp_graph *g, double *out);
  * [n_dir_edges * k] float64 (row e = message on directed edge e). */
 int bp_get_messages(const bp_graph *g, double *out);
 
+/* Copies the residuals (Eq. 4: max-norm of the probability-domain change) of
+ * the evaluation that ended the last bp_run, out[n_dir_edges] float64: for a
+ * run stopped by max_rounds = t these are the residuals the frontier of round
+ * t + 1 would be selected from. RnBP, RBP and RS runs (LBP keeps none:
+ * BP_ERR_UNSUPPORTED); in a batch, a graph that stopped earlier keeps its own
+ * final evaluation's values. */
+int bp_get_residuals(const bp_graph *g, double *out);
+
 /* Copies per-graph statistics of the last bp_run into out[n_graphs]. */
 int bp_get_graph_stats(const bp_graph *g, bp_run_stats *out);
 
@@ -236,6 +262,54 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
                        const int32_t *rev, const float *unary_log, const float *beta, double eps,
                        int32_t max_rounds, double *beliefs, int32_t *rounds_out, int32_t *converged_out,
                        void *cuda_stream);
+
+/*
+ * bp_autotune - picks the binary Ising update mapping (bp_options.kernel_variant)
+ * for the handle's size class by measurement. The paper has no counterpart
+ * (it runs one kernel design); the batch configuration of arbitrary graph
+ * sizes calls for a tuned choice per size class.
+ *
+ * For each mapping (1, 2, 4, 5, and 3 when the handle holds more than one
+ * graph) it runs bp_run(schedule, parallelism, eps, trial_rounds, opt) twice
+ * (the first run captures the rounds; the second is timed by its device_ms)
+ * and records the mapping with the least device time per round in a
+ * process-wide table under the size class (see bp_tune_result). Later runs
+ * with kernel_variant = 0 on any handle of that size class, schedule and
+ * msg_dtype use it. Every mapping gives the same results, so tuning changes
+ * speed only. The trial runs leave no result (bp_get_beliefs fails with
+ * BP_ERR_NO_RESULT until the next bp_run). Binary Ising handles only
+ * (BP_ERR_UNSUPPORTED otherwise); trial_rounds >= 1; errors of bp_run pass
+ * through. The table is guarded by a mutex; the handle itself is not
+ * thread-safe.
+ */
+int bp_autotune(bp_graph *g, int32_t schedule, double parallelism, double eps, const bp_options *opt,
+                int32_t trial_rounds, bp_tune_result *out);
+
+/*
+ * bp_set_graph_parallelism - per-graph parallelism for the graphs of a batch:
+ * p[q] (host array of n_graphs values, each > 0 and finite) replaces bp_run's
+ * parallelism argument for graph q: its RnBP LowP (Section IV-A), or its RBP /
+ * RS frontier fraction (Section III-D). p = NULL returns to the run's single
+ * value. The values are copied to the device and stay until changed. The
+ * paper runs one p per experiment; a batch of graphs of different sizes can
+ * use a p per size class (bp_autotune_parallelism).
+ */
+int bp_set_graph_parallelism(bp_graph *g, const double *p);
+
+/*
+ * bp_autotune_parallelism - picks the parallelism of every size class of the
+ * batch's graphs (class = floor(log2(vertices of the graph))) among
+ * candidates[0 .. n_candidates) (each > 0, at most 64 candidates) for RnBP,
+ * RBP or RS. For each candidate it runs bp_run(schedule, candidate, eps,
+ * max_rounds, opt) on the whole batch and scores each class by the rounds its
+ * graphs took to converge, a graph that did not converge counting
+ * 2 * max_rounds; the lowest score wins (ties: the earlier candidate). The
+ * choice is installed with bp_set_graph_parallelism and, when graph_p_out is
+ * not NULL, copied to graph_p_out[n_graphs] (host). The trial runs leave no
+ * result. Errors of bp_run pass through.
+ */
+int bp_autotune_parallelism(bp_graph *g, int32_t schedule, const double *candidates, int32_t n_candidates,
+                            double eps, int32_t max_rounds, const bp_options *opt, double *graph_p_out);
 
 /* Copies the phase profile of the last bp_run (see bp_profile). */
 int bp_get_profile(const bp_graph *g, bp_profile *out);

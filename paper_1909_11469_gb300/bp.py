@@ -66,10 +66,21 @@ class bp_profile(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("eval_launches", ctypes.c_int64),
                 ("full_evals", ctypes.c_int64), ("active_vertices", ctypes.c_int64),
                 ("eval_ms", ctypes.c_double), ("decide_ms", ctypes.c_double),
-                ("frontier_ms", ctypes.c_double), ("batch_kernel_ms", ctypes.c_double)]
+                ("frontier_ms", ctypes.c_double), ("batch_kernel_ms", ctypes.c_double),
+                ("select_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double),
+                ("sweep_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class bp_tune_result(ctypes.Structure):
+    _fields_ = [("kernel_variant", ctypes.c_int32), ("size_class", ctypes.c_int32),
+                ("ms_per_round", ctypes.c_double * 6)]
+
+    def as_dict(self):
+        return {"kernel_variant": self.kernel_variant, "size_class": self.size_class,
+                "ms_per_round": list(self.ms_per_round)}
 
 
 _P = ctypes.c_void_p
@@ -82,8 +93,14 @@ _SIGNATURES = {
     "bp_get_beliefs": (ctypes.c_int, [_P, _P]),
     "bp_get_messages": (ctypes.c_int, [_P, _P]),
     "bp_get_graph_stats": (ctypes.c_int, [_P, _P]),
+    "bp_get_residuals": (ctypes.c_int, [_P, _P]),
     "bp_get_trace": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "bp_get_profile": (ctypes.c_int, [_P, _P]),
+    "bp_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P, ctypes.c_int32,
+                                   _P]),
+    "bp_set_graph_parallelism": (ctypes.c_int, [_P, _P]),
+    "bp_autotune_parallelism": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_double,
+                                               ctypes.c_int32, _P, _P]),
     "bp_lbp_run_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
                                           ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P]),
     "bp_graph_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -242,10 +259,44 @@ def bp_get_trace(handle, count: int) -> np.ndarray:
     return out.reshape(rounds.value, words)
 
 
+def bp_get_residuals(handle) -> np.ndarray:
+    m = _info(handle)[2]
+    out = np.empty(m, dtype=np.float64)
+    _check(lib().bp_get_residuals(handle, _ptr(out)), "bp_get_residuals")
+    return out
+
+
 def bp_get_profile(handle) -> dict:
     p = bp_profile()
     _check(lib().bp_get_profile(handle, ctypes.byref(p)), "bp_get_profile")
     return p.as_dict()
+
+
+def bp_autotune(handle, schedule, parallelism, eps, options: bp_options | None = None,
+                trial_rounds: int = 16) -> dict:
+    sched = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    r = bp_tune_result()
+    _check(lib().bp_autotune(handle, sched, float(parallelism), float(eps),
+                             ctypes.byref(options) if options is not None else None, int(trial_rounds),
+                             ctypes.byref(r)), "bp_autotune")
+    return r.as_dict()
+
+
+def bp_set_graph_parallelism(handle, p) -> None:
+    arr = None if p is None else np.ascontiguousarray(p, dtype=np.float64)
+    _check(lib().bp_set_graph_parallelism(handle, _ptr(arr)), "bp_set_graph_parallelism")
+
+
+def bp_autotune_parallelism(handle, schedule, candidates, eps, max_rounds, options: bp_options | None = None):
+    """Returns the chosen parallelism of every graph (float64 [n_graphs])."""
+    sched = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    cand = np.ascontiguousarray(candidates, dtype=np.float64)
+    G = _info(handle)[3]
+    out = np.empty(G, dtype=np.float64)
+    _check(lib().bp_autotune_parallelism(handle, sched, _ptr(cand), int(len(cand)), float(eps), int(max_rounds),
+                                         ctypes.byref(options) if options is not None else None, _ptr(out)),
+           "bp_autotune_parallelism")
+    return out
 
 
 def bp_lbp_run_noalloc(n_vars, n_dir_edges, row_ptr, col, rev, unary_log, beta, eps, max_rounds,
@@ -297,6 +348,19 @@ class Graph:
 
     def profile(self):
         return bp_get_profile(self.handle)
+
+    def residuals(self):
+        return bp_get_residuals(self.handle)
+
+    def autotune(self, schedule="lbp", parallelism=1.0, eps=1e-4, trial_rounds=16, **opts):
+        return bp_autotune(self.handle, schedule, parallelism, eps, bp_default_options(**opts), trial_rounds)
+
+    def set_graph_parallelism(self, p):
+        bp_set_graph_parallelism(self.handle, p)
+
+    def autotune_parallelism(self, schedule, candidates, eps=1e-4, max_rounds=1000, **opts):
+        return bp_autotune_parallelism(self.handle, schedule, candidates, eps, max_rounds,
+                                       bp_default_options(**opts))
 
     def trace(self, schedule):
         sched = SCHEDULES[schedule] if isinstance(schedule, str) else schedule

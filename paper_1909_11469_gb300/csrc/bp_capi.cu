@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -68,6 +70,21 @@ struct CachedGraph {
 
 void destroy_cached(CachedGraph &c) { cudaGraphExecDestroy(c.exec); }
 
+// Process-wide table of tuned binary-update mappings (bp_autotune), keyed by
+// size class.
+std::mutex g_tune_mu;
+std::map<uint32_t, int32_t> g_tune_table;
+
+int log2_floor(int64_t v)
+{
+    int b = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++b;
+    }
+    return b;
+}
+
 }  // namespace
 
 void bpg::set_last_error(const std::string &msg) { g_last_error = msg; }
@@ -95,6 +112,10 @@ struct bp_graph {
     void *d_msg[2] = {nullptr, nullptr};
     void *d_resid = nullptr, *d_vres = nullptr;
     int8_t *d_level = nullptr;
+    int32_t *d_lvl_list = nullptr, *d_lvl_cnt = nullptr;   // Residual Splash level lists (lazy)
+    double *d_graph_p = nullptr;   // per-graph parallelism (bp_set_graph_parallelism)
+    bool graph_p_set = false;
+    int32_t max_deg = 0;           // largest vertex degree (size class, mapping heuristic)
     GState *d_gs = nullptr;
     unsigned long long *d_red_max = nullptr;
     unsigned int *d_red_cnt = nullptr;
@@ -146,6 +167,33 @@ void free_run_buffers(bp_graph *g)
 // Binary Ising messages are stored as one log-odds value, others as k logs.
 int epm_of(const bp_graph *g) { return (g->k == 2 && g->pair_kind == BP_PAIR_ISING_BETA) ? 1 : g->k; }
 
+// Size class of a handle for a schedule and storage format: mean vertices
+// per graph and graph count (log2 buckets), largest degree (<= 4, <= 8, more).
+uint32_t size_class(const bp_graph *g, int schedule, int dtype)
+{
+    const int64_t per = std::max<int64_t>(1, (int64_t)g->n / std::max(g->G, 1));
+    const uint32_t nb = (uint32_t)log2_floor(per), gb = (uint32_t)log2_floor(g->G);
+    const uint32_t db = g->max_deg <= 4 ? 0u : (g->max_deg <= 8 ? 1u : 2u);
+    return (uint32_t)schedule | ((uint32_t)dtype << 2) | (nb << 4) | (gb << 9) | (db << 14);
+}
+
+// Binary update mapping of a run: the requested one, else the tuned one of the
+// handle's size class, else thread per vertex with prefetched gathers for
+// graphs of degree <= 4 (every vertex's edges held in registers) and the plain
+// thread-per-vertex form otherwise.
+int32_t resolve_variant(const bp_graph *g, int schedule, int dtype, int32_t requested)
+{
+    if (requested != 0)
+        return requested;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_table.find(size_class(g, schedule, dtype));
+        if (it != g_tune_table.end())
+            return it->second;
+    }
+    return g->max_deg <= 4 ? 4 : 1;
+}
+
 DevGraph dev_graph(const bp_graph *g)
 {
     DevGraph d;
@@ -189,6 +237,9 @@ DevRun dev_run(const bp_graph *g)
     r.trace = g->d_trace;
     r.beliefs = g->d_beliefs;
     r.queue = g->d_queue;
+    r.lvl_list = g->d_lvl_list;
+    r.lvl_cnt = g->d_lvl_cnt;
+    r.graph_p = g->graph_p_set ? g->d_graph_p : nullptr;
     return r;
 }
 
@@ -295,6 +346,8 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     std::vector<int32_t> rp32((size_t)n + 1);
     for (int32_t i = 0; i <= n; ++i)
         rp32[(size_t)i] = (int32_t)row_ptr[i];
+    for (int32_t i = 0; i < n; ++i)
+        g->max_deg = std::max<int32_t>(g->max_deg, (int32_t)(row_ptr[i + 1] - row_ptr[i]));
     int rc;
     if ((rc = dalloc(&g->d_row_ptr, (size_t)n + 1)) || (rc = dalloc(&g->d_col, (size_t)M)) ||
         (rc = dalloc(&g->d_rev, (size_t)M)) || (rc = dalloc(&g->d_gid, (size_t)std::max(n, 1))) ||
@@ -374,8 +427,9 @@ int create_common(int32_t n_graphs, const int64_t *gvo, int32_t n, int32_t k, in
 }
 
 // Records one round (evaluation, decision, frontier work) on stream s and
-// returns the number of kernels it launched. ev (nullable) receives 4 events:
-// round start, after evaluation, after decision, round end.
+// returns the number of kernels it launched. ev (nullable) receives 5 events:
+// round start, after evaluation, after decision, after selection (and splash
+// levels), round end (after the splash sweep).
 int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &dr, const RunParams &rp,
                      cudaStream_t s, cudaEvent_t *ev)
 {
@@ -410,10 +464,27 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
         launch_select_rs(dtype, dg, dr, rp, s);
         kernels += 1;
         const int h = rp.splash_depth;
+        auto level_of = [h](int step) { return step <= h ? h - step : step - h; };
+        if (dg.epm == 1 && dr.lvl_list && h <= LVL_MAX) {
+            // sweeps over per-level vertex lists built by the last BFS level
+            for (int d = 1; d < h; ++d)
+                launch_bfs_level(dg, dr, d, s);
+            launch_bfs_level_lists(dg, dr, h, h, s);
+            kernels += any ? (h > 0 ? h : 1) : 0;
+            if (ev)
+                cudaEventRecord(ev[3], s);
+            launch_splash_list_step(dtype, dg, dr, -1, level_of(0), s);
+            for (int step = 0; step < 2 * h; ++step)
+                launch_splash_list_step(dtype, dg, dr, level_of(step), level_of(step + 1), s);
+            launch_splash_list_step(dtype, dg, dr, level_of(2 * h), -1, s);
+            kernels += any ? 2 * h + 2 : 0;
+            break;
+        }
         for (int d = 1; d <= h; ++d)
             launch_bfs_level(dg, dr, d, s);
         kernels += any ? h : 0;
-        auto level_of = [h](int step) { return step <= h ? h - step : step - h; };
+        if (ev)
+            cudaEventRecord(ev[3], s);
         if (dg.epm == 1) {
             // binary messages: each sub-step's commit fused with the next evaluation
             launch_splash_step(dtype, dg, dr, -1, level_of(0), s);
@@ -431,8 +502,11 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
         }
     }
     }
-    if (ev)
-        cudaEventRecord(ev[3], s);
+    if (ev) {
+        if (rp.schedule != SCHED_RS)
+            cudaEventRecord(ev[3], s);
+        cudaEventRecord(ev[4], s);
+    }
     return kernels;
 }
 
@@ -672,8 +746,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "bad high_p or ratio_threshold");
     if (opt.potts_path < 0 || opt.potts_path > 3)
         return fail(BP_ERR_INVALID_ARG, "potts_path must be 0..3");
-    if (opt.kernel_variant < 0 || opt.kernel_variant > 3)
-        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be 0, 1, 2 or 3");
+    if (opt.kernel_variant < 0 || opt.kernel_variant > 5)
+        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 5]");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
         return fail(BP_ERR_INVALID_ARG, "splash_depth must be in [0, 16]");
     if (opt.record_trace && opt.trace_capacity < 0)
@@ -683,6 +757,13 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     int rc = ensure_msg_buffers(g, dtype);
     if (rc != BP_OK)
         return rc;
+    if (schedule == BP_RS && epm_of(g) == 1 && opt.splash_depth <= LVL_MAX && !g->d_lvl_list) {
+        // level lists of the Residual Splash sweeps, kept until the handle is destroyed
+        if ((rc = dalloc(&g->d_lvl_list, (size_t)(LVL_MAX + 1) * (size_t)std::max(g->n, 1))) != BP_OK ||
+            (rc = dalloc(&g->d_lvl_cnt, (size_t)(LVL_MAX + 1))) != BP_OK)
+            return rc;
+        BP_CK(cudaMemset(g->d_lvl_cnt, 0, sizeof(int32_t) * (LVL_MAX + 1)));
+    }
 
     RunParams rp;
     memset(&rp, 0, sizeof(rp));
@@ -700,7 +781,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     rp.trace_capacity = rp.record_trace ? opt.trace_capacity : 0;
     const int64_t trace_count = schedule == BP_RS ? g->n : g->M;
     rp.trace_words = (int32_t)((trace_count + 31) / 32);
-    rp.variant = opt.kernel_variant == 2 ? 2 : 1;
+    const int32_t variant = epm_of(g) == 1 ? resolve_variant(g, schedule, dtype, opt.kernel_variant) : 1;
+    rp.variant = variant == 3 ? 1 : variant;
     rp.eps_f = float_at_least(eps);
     // shared-table update in vertex tiles: 0 = per-vertex k-state kernel,
     // 1 = tiles on CUDA cores, 2 = tiles on tensor cores, 3 = tensor cores split
@@ -743,10 +825,10 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     // launch) is taken on request; the automatic choice replays captured rounds,
     // which measured faster on every workload here (the per-round kernels keep
     // 64 warps per SM over the whole batch, a cluster only 32 per SM).
-    const bool persistent = epm_of(g) == 1 && opt.kernel_variant == 3;
+    const bool persistent = epm_of(g) == 1 && variant == 3;
     float batch_ms = 0.f;
     bool stopped = false;
-    std::vector<float> t_eval, t_decide, t_front;   // per global round (profile)
+    std::vector<float> t_eval, t_decide, t_front, t_sweep;   // per global round (profile)
     if (persistent) {
         const long long budget_ns = opt.time_budget_ms > 0.0 ? (long long)(opt.time_budget_ms * 1e6) : 0;
         BP_CK(cudaEventRecord(g->ev_pt0, s));
@@ -764,14 +846,14 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         for (;;) {
             if (opt.profile) {
                 // direct launches with events between the phases of every round
-                if (g->prof_events.size() < (size_t)chunk * 4) {
+                if (g->prof_events.size() < (size_t)chunk * 5) {
                     size_t old = g->prof_events.size();
-                    g->prof_events.resize((size_t)chunk * 4);
+                    g->prof_events.resize((size_t)chunk * 5);
                     for (size_t q = old; q < g->prof_events.size(); ++q)
                         BP_CK(cudaEventCreate(&g->prof_events[q]));
                 }
                 for (int r = 0; r < chunk; ++r)
-                    kernels += record_round(g, dtype, dg, dr, rp, s, &g->prof_events[(size_t)r * 4]);
+                    kernels += record_round(g, dtype, dg, dr, rp, s, &g->prof_events[(size_t)r * 5]);
                 BP_CK(cudaGetLastError());
             } else {
                 CachedGraph *cg = nullptr;
@@ -785,14 +867,16 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
             BP_CK(cudaStreamSynchronize(s));
             if (opt.profile) {
                 for (int r = 0; r < chunk; ++r) {
-                    float a = 0.f, b = 0.f, c = 0.f;
-                    cudaEvent_t *ev = &g->prof_events[(size_t)r * 4];
+                    float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
+                    cudaEvent_t *ev = &g->prof_events[(size_t)r * 5];
                     BP_CK(cudaEventElapsedTime(&a, ev[0], ev[1]));
                     BP_CK(cudaEventElapsedTime(&b, ev[1], ev[2]));
                     BP_CK(cudaEventElapsedTime(&c, ev[2], ev[3]));
+                    BP_CK(cudaEventElapsedTime(&d, ev[3], ev[4]));
                     t_eval.push_back(a);
                     t_decide.push_back(b);
                     t_front.push_back(c);
+                    t_sweep.push_back(d);
                 }
             }
             if (*g->h_running <= 0)
@@ -877,9 +961,14 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         for (size_t r = 0; r < live; ++r) {
             prof.eval_ms += t_eval[r];
             prof.decide_ms += t_decide[r];
-            prof.frontier_ms += t_front[r];
+            prof.select_ms += t_front[r];
+            prof.sweep_ms += t_sweep[r];
         }
+        prof.frontier_ms = prof.select_ms + prof.sweep_ms;
         prof.eval_launches = (int64_t)live;
+        // every committing round of an RS run sweeps 2h + 2 fused steps (binary)
+        if (schedule == BP_RS && epm_of(g) == 1)
+            prof.sweep_launches = (int64_t)(live > 0 ? live - 1 : 0) * (2 * opt.splash_depth + 2);
     }
     g->last_profile = prof;
     g->has_result = true;
@@ -927,6 +1016,29 @@ int bp_get_messages(const bp_graph *g, double *out)
     return BP_OK;
 }
 
+int bp_get_residuals(const bp_graph *g, double *out)
+{
+    if (!g || !out)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (!g->has_result)
+        return fail(BP_ERR_NO_RESULT, "no bp_run result");
+    if (g->res_schedule == BP_LBP)
+        return fail(BP_ERR_UNSUPPORTED, "LBP runs keep no residuals");
+    if (!g->M)
+        return BP_OK;
+    BP_CK(cudaSetDevice(g->dev));
+    const size_t M = (size_t)g->M;
+    if (g->res_dtype == DT_F64) {
+        BP_CK(cudaMemcpy(out, g->d_resid, sizeof(double) * M, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> tmp(M);
+        BP_CK(cudaMemcpy(tmp.data(), g->d_resid, sizeof(float) * M, cudaMemcpyDeviceToHost));
+        for (size_t e = 0; e < M; ++e)
+            out[e] = (double)tmp[e];
+    }
+    return BP_OK;
+}
+
 int bp_get_graph_stats(const bp_graph *g, bp_run_stats *out)
 {
     if (!g || !out)
@@ -951,6 +1063,137 @@ int bp_get_trace(const bp_graph *g, uint32_t *out, int64_t capacity_words, int32
         return fail(BP_ERR_INVALID_ARG, "trace buffer too small");
     BP_CK(cudaSetDevice(g->dev));
     BP_CK(cudaMemcpy(out, g->d_trace, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost));
+    return BP_OK;
+}
+
+int bp_set_graph_parallelism(bp_graph *g, const double *p)
+{
+    if (!g)
+        return fail(BP_ERR_INVALID_ARG, "NULL handle");
+    if (!p) {
+        if (g->graph_p_set)
+            clear_cache(g);   // captured rounds hold the per-graph array
+        g->graph_p_set = false;
+        return BP_OK;
+    }
+    for (int32_t q = 0; q < g->G; ++q)
+        if (!(p[q] > 0.0) || !std::isfinite(p[q]))
+            return fail(BP_ERR_INVALID_ARG, "parallelism of graph " + std::to_string(q) +
+                                                " must be positive and finite");
+    BP_CK(cudaSetDevice(g->dev));
+    int rc;
+    if (!g->d_graph_p && (rc = dalloc(&g->d_graph_p, (size_t)g->G)) != BP_OK)
+        return rc;
+    BP_CK(cudaMemcpy(g->d_graph_p, p, sizeof(double) * (size_t)g->G, cudaMemcpyHostToDevice));
+    if (!g->graph_p_set)
+        clear_cache(g);
+    g->graph_p_set = true;
+    return BP_OK;
+}
+
+int bp_autotune(bp_graph *g, int32_t schedule, double parallelism, double eps, const bp_options *opt,
+                int32_t trial_rounds, bp_tune_result *out)
+{
+    if (!g || !out)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (trial_rounds < 1)
+        return fail(BP_ERR_INVALID_ARG, "trial_rounds must be >= 1");
+    if (!g->has_pot)
+        return fail(BP_ERR_NO_POTENTIALS, "bp_set_potentials has not been called");
+    if (epm_of(g) != 1)
+        return fail(BP_ERR_UNSUPPORTED, "mapping autotuning covers the binary Ising update");
+    bp_options o;
+    if (opt)
+        o = *opt;
+    else
+        bp_default_options(&o);
+    o.profile = 0;
+    o.time_budget_ms = 0.0;
+    o.record_trace = 0;
+    memset(out, 0, sizeof(*out));
+    static const int32_t cand[] = {1, 2, 4, 5, 3};
+    const int n_cand = g->G > 1 ? 5 : 4;   // the persistent kernel runs one cluster per graph
+    double best = std::numeric_limits<double>::infinity();
+    int32_t best_v = 1;
+    for (int c = 0; c < n_cand; ++c) {
+        o.kernel_variant = cand[c];
+        bp_run_stats st;
+        int rc = bp_run(g, schedule, parallelism, eps, trial_rounds, &o, &st);   // warm-up: captures rounds
+        if (rc != BP_OK)
+            return rc;
+        if ((rc = bp_run(g, schedule, parallelism, eps, trial_rounds, &o, &st)) != BP_OK)
+            return rc;
+        const double ms = st.device_ms / (double)std::max(st.rounds, 1);
+        out->ms_per_round[cand[c]] = ms;
+        if (ms < best) {
+            best = ms;
+            best_v = cand[c];
+        }
+    }
+    const uint32_t key = size_class(g, schedule, o.msg_dtype);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_table[key] = best_v;
+    }
+    out->kernel_variant = best_v;
+    out->size_class = (int32_t)key;
+    g->has_result = false;   // the trial runs leave no result to read
+    return BP_OK;
+}
+
+int bp_autotune_parallelism(bp_graph *g, int32_t schedule, const double *candidates, int32_t n_candidates,
+                            double eps, int32_t max_rounds, const bp_options *opt, double *graph_p_out)
+{
+    if (!g || !candidates)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (schedule != BP_RNBP && schedule != BP_RBP && schedule != BP_RS)
+        return fail(BP_ERR_INVALID_ARG, "parallelism is tuned for RnBP, RBP and RS");
+    if (n_candidates < 1 || n_candidates > 64)
+        return fail(BP_ERR_INVALID_ARG, "n_candidates must be in [1, 64]");
+    for (int32_t c = 0; c < n_candidates; ++c)
+        if (!(candidates[c] > 0.0) || !std::isfinite(candidates[c]))
+            return fail(BP_ERR_INVALID_ARG, "candidates must be positive and finite");
+    int rc;
+    if ((rc = bp_set_graph_parallelism(g, nullptr)) != BP_OK)
+        return rc;
+    // size class of every graph: floor(log2(vertices))
+    std::vector<int> cls((size_t)g->G);
+    int n_cls = 0;
+    for (int32_t q = 0; q < g->G; ++q) {
+        cls[(size_t)q] = log2_floor(std::max(1, g->h_gv_off[(size_t)q + 1] - g->h_gv_off[(size_t)q]));
+        n_cls = std::max(n_cls, cls[(size_t)q] + 1);
+    }
+    // score of a candidate on a class: rounds to convergence summed over the
+    // class's graphs, a graph that did not converge counting 2 * max_rounds
+    std::vector<double> score((size_t)n_cls * (size_t)n_candidates, 0.0);
+    std::vector<bp_run_stats> per((size_t)g->G);
+    for (int32_t c = 0; c < n_candidates; ++c) {
+        if ((rc = bp_run(g, schedule, candidates[c], eps, max_rounds, opt, nullptr)) != BP_OK)
+            return rc;
+        if ((rc = bp_get_graph_stats(g, per.data())) != BP_OK)
+            return rc;
+        for (int32_t q = 0; q < g->G; ++q) {
+            const bp_run_stats &st = per[(size_t)q];
+            score[(size_t)cls[(size_t)q] * n_candidates + c] +=
+                st.converged ? (double)st.rounds : 2.0 * (double)max_rounds;
+        }
+    }
+    std::vector<double> chosen((size_t)n_cls, candidates[0]);
+    for (int k = 0; k < n_cls; ++k) {
+        int best = 0;
+        for (int32_t c = 1; c < n_candidates; ++c)
+            if (score[(size_t)k * n_candidates + c] < score[(size_t)k * n_candidates + best])
+                best = c;
+        chosen[(size_t)k] = candidates[best];
+    }
+    std::vector<double> p((size_t)g->G);
+    for (int32_t q = 0; q < g->G; ++q)
+        p[(size_t)q] = chosen[(size_t)cls[(size_t)q]];
+    if ((rc = bp_set_graph_parallelism(g, p.data())) != BP_OK)
+        return rc;
+    if (graph_p_out)
+        memcpy(graph_p_out, p.data(), sizeof(double) * p.size());
+    g->has_result = false;
     return BP_OK;
 }
 
@@ -999,6 +1242,9 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_pair);
     dfree(g->d_psi_shared);
     dfree(g->d_level);
+    dfree(g->d_lvl_list);
+    dfree(g->d_lvl_cnt);
+    dfree(g->d_graph_p);
     dfree(g->d_gs);
     dfree(g->d_red_max);
     dfree(g->d_red_cnt);

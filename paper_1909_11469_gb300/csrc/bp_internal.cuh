@@ -93,7 +93,19 @@ struct DevRun {
     uint32_t *trace;              // [trace_capacity * trace_words]
     double *beliefs;              // [n*k]
     int32_t *queue;               // [1] next graph for the persistent batch kernel
+    int32_t *lvl_list;            // [(LVL_MAX+1) * n] Residual Splash vertices of each level
+    int32_t *lvl_cnt;             // [LVL_MAX+1] entries of each level list
+    const double *graph_p;        // [G] per-graph parallelism, or null: every graph uses rp.low_p
 };
+
+// Parallelism of graph gg: RnBP LowP, or the RBP / RS frontier fraction.
+__device__ __forceinline__ double graph_low_p(const DevRun &dr, const RunParams &rp, int gg)
+{
+    return dr.graph_p ? dr.graph_p[gg] : rp.low_p;
+}
+
+// Deepest splash whose sweeps run over per-level vertex lists (binary messages).
+constexpr int LVL_MAX = 3;
 
 // Message buffer b (0 or 1). A select instead of msg[b]: indexing the kernel
 // parameter array with a runtime value would copy the whole struct to local memory.
@@ -127,7 +139,9 @@ template <> struct Store<__nv_bfloat16> {
         return __bfloat162float(__float2bfloat16_rn(v));
     }
 };
-// Q16: binary log-odds as a signed 16-bit multiple of sc, |q| <= 32767.
+// Q16: binary log-odds as a signed 16-bit multiple of sc, |q| <= 32767. The
+// products q * sc are rounded explicitly (__fmul_rn), so no kernel fuses them
+// into a neighbouring addition and every kernel decodes the same value.
 template <> struct Store<int16_t> {
     using A = float;
     static __device__ __forceinline__ float code(float v, float sc)
@@ -135,10 +149,10 @@ template <> struct Store<int16_t> {
         float q = rintf(__fdividef(v, sc));
         return fminf(fmaxf(q, -32767.0f), 32767.0f);
     }
-    static __device__ __forceinline__ float ld(const int16_t *p, float sc) { return (float)*p * sc; }
-    static __device__ __forceinline__ float val(int16_t x, float sc) { return (float)x * sc; }
+    static __device__ __forceinline__ float ld(const int16_t *p, float sc) { return __fmul_rn((float)*p, sc); }
+    static __device__ __forceinline__ float val(int16_t x, float sc) { return __fmul_rn((float)x, sc); }
     static __device__ __forceinline__ void st(int16_t *p, float v, float sc) { *p = (int16_t)code(v, sc); }
-    static __device__ __forceinline__ float quant(float v, float sc) { return code(v, sc) * sc; }
+    static __device__ __forceinline__ float quant(float v, float sc) { return __fmul_rn(code(v, sc), sc); }
 };
 
 // Residual element type: double for FP64 messages, float otherwise.
@@ -160,17 +174,19 @@ __device__ __forceinline__ double m_sigmoid(double u) { return 1.0 / (1.0 + exp(
 // With cavity log-odds h of x_i and q = exp(-2 beta):
 //   u = sign(h) * log((1 + q F) / (q + F)),  F = exp(-|h|),
 // which is log[(e^{-b} + e^{b+h}) / (e^{b} + e^{h-b})] rearranged so that no
-// term overflows (the sum over x_i of Eq. 2 for the 2x2 Ising table).
+// term overflows (the sum over x_i of Eq. 2 for the 2x2 Ising table). The
+// product q F is rounded explicitly (fmaf / __dmul_rn), so every kernel that
+// inlines this computes the same bits whatever the compiler contracts around it.
 __device__ __forceinline__ float ising_logodds(float q, float h)
 {
     float F = __expf(-fabsf(h));
-    float u = __logf(__fdividef(1.0f + q * F, q + F));
+    float u = __logf(__fdividef(fmaf(q, F, 1.0f), q + F));
     return h >= 0.0f ? u : -u;
 }
 __device__ __forceinline__ double ising_logodds(double q, double h)
 {
     double F = exp(-fabs(h));
-    double u = log1p(q * F) - log(q + F);
+    double u = log1p(__dmul_rn(q, F)) - log(q + F);
     return h >= 0.0 ? u : -u;
 }
 

@@ -53,6 +53,31 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
     reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
 }
 
+// The same mapping with the prefetching vertex routine (eval_vertex_bin_pf):
+// graph arrays and the graph's status load in parallel. MINB = resident
+// blocks per SM the register budget is fitted to.
+template <typename S, int MODE, int CACHE, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_eval_bin_pf(DevGraph g, DevRun dr, RunParams rp)
+{
+    using A = typename Store<S>::A;
+    using RT = typename ResidT<S>::T;
+    const int first = blockIdx.x * blockDim.x;
+    const int last = min(g.n - 1, first + (int)blockDim.x - 1);
+    const int g0 = g.gid[first];
+    const bool uniform = (g0 == g.gid[last]);
+    const int i = first + threadIdx.x;
+    bool valid = false;
+    int gg = g0;
+    A maxa = 0;
+    unsigned int cnt = 0;
+    if (i < g.n) {
+        gg = g.gid[i];
+        valid = eval_vertex_bin_pf<S, MODE == MODE_CAND, CACHE>(g, dr, (RT *)dr.resid, i, gg,
+                                                                 eps_in(rp, (A)0), maxa, cnt);
+    }
+    reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
+}
+
 // --------------------------------------------------------------------------
 // k-state messages (k <= KP <= 32): a group of KP lanes per vertex, lane x
 // holds state x. S_i(x) = theta_i(x) + sum_in l(x); per out-edge the cavity is
@@ -186,6 +211,8 @@ __global__ void k_decide(DevGraph g, DevRun dr, RunParams rp)
 {
     const int gg = blockIdx.x;
     const int lane = threadIdx.x;
+    if (gg == 0 && lane <= LVL_MAX && dr.lvl_cnt)
+        dr.lvl_cnt[lane] = 0;   // Residual Splash level lists of this round start empty
     GState *stp = dr.gs + gg;
     if (stp->status != ST_RUNNING)
         return;
@@ -220,13 +247,13 @@ __global__ void k_decide(DevGraph g, DevRun dr, RunParams rp)
             if (st.rounds == 1)
                 p = rp.high_p;
             else
-                p = ((double)c / (double)st.n_prev > rp.ratio_threshold) ? rp.low_p : rp.high_p;
+                p = ((double)c / (double)st.n_prev > rp.ratio_threshold) ? graph_low_p(dr, rp, gg) : rp.high_p;
             st.always = (p >= 1.0) ? 1 : 0;
             st.thr = (p <= 0.0 || p >= 1.0) ? 0u : (uint32_t)(uint64_t)(p * 4294967296.0);
         } else {
             const int64_t base = (rp.schedule == SCHED_RS && rp.rs_roots_mode == 1) ? ng : Mg;
             const int64_t hi = (rp.schedule == SCHED_RS) ? ng : Mg;
-            double v = ceil(rp.low_p * (double)base);
+            double v = ceil(graph_low_p(dr, rp, gg) * (double)base);
             int64_t kk = (v > (double)hi) ? hi : (int64_t)v;
             kk = kk < 1 ? 1 : kk;
             kk = kk > hi ? hi : kk;
@@ -653,6 +680,83 @@ __global__ void __launch_bounds__(BLOCK) k_splash_step(DevGraph g, DevRun dr, in
     add_commit_counts(dr, uniform, g0, valid, gg, c, true);
 }
 
+// Residual Splash, last BFS level (pull, level d; d = 0: no BFS step, the
+// splash has depth 0) fused with the per-level vertex lists of the sweeps:
+// every vertex of a running graph with a level L <= h is appended to list L
+// (warp-aggregated, ascending within a warp). The per-graph counts of the
+// round's splash (a level-0 vertex is evaluated and committed once, a deeper
+// one twice: the sweep visits levels h..1 on the way down and up) are added
+// here, so the sweep kernels count nothing.
+__global__ void __launch_bounds__(BLOCK) k_bfs_level_lists(DevGraph g, DevRun dr, int d, int h)
+{
+    const int first = blockIdx.x * blockDim.x;
+    const int last = min(g.n - 1, first + (int)blockDim.x - 1);
+    const int g0 = g.gid[first];
+    const bool uniform = (g0 == g.gid[last]);
+    const int i = first + threadIdx.x;
+    int gg = g0;
+    int lv = -1;
+    unsigned int c = 0;
+    if (i < g.n) {
+        gg = g.gid[i];
+        if (dr.gs[gg].status == ST_RUNNING) {
+            if (d > 0)
+                bfs_vertex(g, dr, i, d);
+            lv = dr.level[i];
+            if (lv > h)
+                lv = -1;
+            if (lv >= 0)
+                c = (unsigned int)(g.row_ptr[i + 1] - g.row_ptr[i]) * (lv == 0 ? 1u : 2u);
+        }
+    }
+    // block-aggregated appends: per level, a warp ballot ranks the lanes, the
+    // block's warps take consecutive ranges of one global reservation
+    __shared__ int s_wcnt[LVL_MAX + 1][BLOCK / 32];
+    __shared__ int s_base[LVL_MAX + 1];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int L = 0; L <= h; ++L) {
+        const unsigned mask = __ballot_sync(0xffffffffu, lv == L);
+        if (lane == 0)
+            s_wcnt[L][warp] = __popc(mask);
+    }
+    __syncthreads();
+    if (threadIdx.x <= (unsigned)h) {
+        int tot = 0;
+        for (int w = 0; w < BLOCK / 32; ++w)
+            tot += s_wcnt[threadIdx.x][w];
+        s_base[threadIdx.x] = tot ? atomicAdd(&dr.lvl_cnt[threadIdx.x], tot) : 0;
+    }
+    __syncthreads();
+    for (int L = 0; L <= h; ++L) {
+        const unsigned mask = __ballot_sync(0xffffffffu, lv == L);
+        if (lv == L) {
+            int before = s_base[L];
+            for (unsigned w = 0; w < warp; ++w)
+                before += s_wcnt[L][w];
+            dr.lvl_list[(size_t)L * g.n + before + __popc(mask & ((1u << lane) - 1u))] = i;
+        }
+    }
+    add_commit_counts(dr, uniform, g0, lv >= 0, gg, c, true);
+}
+
+// Residual Splash over the level lists, binary messages: commit of level Lc
+// fused with the evaluation of level Le (the same sub-step pairing as
+// k_splash_step), one thread per listed vertex, grid-stride.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_splash_list_step(DevGraph g, DevRun dr, int Lc, int Le)
+{
+    const int nc = Lc >= 0 ? dr.lvl_cnt[Lc] : 0;
+    const int ne = Le >= 0 ? dr.lvl_cnt[Le] : 0;
+    const int *lc = dr.lvl_list + (size_t)(Lc >= 0 ? Lc : 0) * g.n;
+    const int *le = dr.lvl_list + (size_t)(Le >= 0 ? Le : 0) * g.n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc + ne; t += gridDim.x * blockDim.x) {
+        if (t < nc)
+            splash_commit_vertex<S>(g, dr, lc[t]);
+        else
+            splash_eval_vertex<S>(g, dr, le[t - nc], Lc);
+    }
+}
+
 // --------------------------------------------------------------------------
 // Set-up of a run.
 template <typename S>
@@ -799,9 +903,21 @@ static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams
                             cudaStream_t s)
 {
     int nb = blocks_for(g.n, BLOCK);
-    (void)level_L;   // binary splash sweeps use k_splash_step
-    // mapping: thread per vertex (variant 1) or 256-vertex tiles with edge quads (variant 2)
+    (void)level_L;   // binary splash sweeps use k_splash_step / k_splash_list_step
+    // mapping: thread per vertex (variant 1), 256-vertex tiles with edge quads
+    // (variant 2), thread per vertex with prefetched graph arrays of 4 (variant
+    // 4, 40 registers: 6 blocks per SM) or 8 edges (variant 5, 4 blocks per SM)
     const bool tiled = rp.variant == 2;
+    if (rp.variant >= 4) {
+        if (mode == MODE_LBP) {
+            if (rp.variant == 4) k_eval_bin_pf<S, MODE_LBP, 4, 6><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+            else k_eval_bin_pf<S, MODE_LBP, 8, 4><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+        } else {
+            if (rp.variant == 4) k_eval_bin_pf<S, MODE_CAND, 4, 6><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+            else k_eval_bin_pf<S, MODE_CAND, 8, 4><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+        }
+        return;
+    }
     if (mode == MODE_LBP) {
         if (tiled)
             k_eval_bin_tiled<S, MODE_LBP><<<blocks_for(g.n, TILE_V), TILE_V, 0, s>>>(g, dr, rp);
@@ -865,6 +981,21 @@ void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s
     if (g.n == 0)
         return;
     k_bfs_level<<<blocks_for(g.n, BLOCK), BLOCK, 0, s>>>(g, dr, d);
+}
+
+void launch_bfs_level_lists(const DevGraph &g, const DevRun &dr, int d, int h, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    k_bfs_level_lists<<<blocks_for(g.n, BLOCK), BLOCK, 0, s>>>(g, dr, d, h);
+}
+
+void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    const int nb = std::min(blocks_for(g.n, BLOCK), 152 * 8);
+    BPG_DISPATCH4(dtype, (k_splash_list_step<S><<<nb, BLOCK, 0, s>>>(g, dr, Lc, Le)));
 }
 
 void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int level_L, cudaStream_t s)

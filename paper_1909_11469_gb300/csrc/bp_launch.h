@@ -25,6 +25,12 @@ void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s
 // Residual Splash (binary messages): commit level Lc and evaluate level Le
 // in one kernel (Lc or Le may be -1).
 void launch_splash_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s);
+// Residual Splash over per-level vertex lists (binary messages, depth <=
+// LVL_MAX): the last BFS level (d = h; d = 0 for depth 0) builds the lists and
+// the round's per-graph counts; the list steps pair commits and evaluations
+// as launch_splash_step does.
+void launch_bfs_level_lists(const DevGraph &g, const DevRun &dr, int d, int h, cudaStream_t s);
+void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s);
 void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int level_L, cudaStream_t s);
 void launch_stop_running(const DevGraph &g, const DevRun &dr, cudaStream_t s);
 void launch_beliefs(int dtype, const DevGraph &g, const DevRun &dr, int kp, cudaStream_t s);

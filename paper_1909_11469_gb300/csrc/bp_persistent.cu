@@ -25,6 +25,7 @@
 namespace bpg {
 
 constexpr int PT_THREADS = 1024;
+static_assert(PT_THREADS == SEL_THREADS, "the cluster select scans assume SEL_THREADS threads per CTA");
 
 struct PtShared {
     double part_max;                 // this CTA's largest residual of the evaluation
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_persistent(DevGraph g, DevRun dr
                 if (rounds == 1)
                     p = rp.high_p;
                 else
-                    p = ((double)ntot / (double)n_prev > rp.ratio_threshold) ? rp.low_p : rp.high_p;
+                    p = ((double)ntot / (double)n_prev > rp.ratio_threshold) ? graph_low_p(dr, rp, gg) : rp.high_p;
                 GState sel;
                 sel.always = (p >= 1.0) ? 1 : 0;
                 sel.thr = (p <= 0.0 || p >= 1.0) ? 0u : (uint32_t)(uint64_t)(p * 4294967296.0);
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_persistent(DevGraph g, DevRun dr
                 }
                 n_prev = ntot;
             } else if (SCHED == SCHED_RBP) {
-                double v = ceil(rp.low_p * (double)Mg);
+                double v = ceil(graph_low_p(dr, rp, gg) * (double)Mg);
                 long long kk = (v > (double)Mg) ? Mg : (long long)v;
                 kk = kk < 1 ? 1 : (kk > Mg ? Mg : kk);
                 rbp_committed += (unsigned long long)kk;
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_persistent(DevGraph g, DevRun dr
                 });
             } else {   // SCHED_RS
                 const int64_t base = (rp.rs_roots_mode == 1) ? nv : Mg;
-                double v = ceil(rp.low_p * (double)base);
+                double v = ceil(graph_low_p(dr, rp, gg) * (double)base);
                 long long kk = (v > (double)nv) ? nv : (long long)v;
                 kk = kk < 1 ? 1 : (kk > nv ? nv : kk);
                 const int nl = vhi - vlo;

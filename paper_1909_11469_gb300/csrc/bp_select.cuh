@@ -3,11 +3,15 @@
 //
 // Every CTA of a cluster owns a contiguous slice of a graph's keys (the
 // residual's IEEE bits: non-negative floats order as unsigned integers). An
-// MSB radix select narrows the k-th largest key one byte per pass: each CTA
-// builds a 256-bin histogram of its slice, the CTAs sum the cluster's
-// histograms through distributed shared memory, and every CTA takes the same
-// digit decision. An ordered pass takes every key above the threshold and the
-// lowest-id ties, ranked across the cluster when ties straddle the threshold.
+// MSB radix select narrows the k-th largest key one digit per pass: each CTA
+// builds a histogram of its slice, the CTAs sum the cluster's histograms
+// through distributed shared memory, and every CTA takes the same digit
+// decision. 32-bit keys take three passes (11, 11 and 10 bits) with one
+// histogram array per pass, so a pass never clears an array a peer may still
+// read and one cluster barrier per pass suffices; the keys that survive the
+// second pass are compacted, so the third pass touches only them. 64-bit keys
+// take eight 8-bit passes. An ordered pass takes every key above the threshold
+// and the lowest-id ties, ranked across the cluster when ties straddle it.
 #pragma once
 
 #include "bp_internal.cuh"
@@ -20,7 +24,9 @@ namespace cg = cooperative_groups;
 
 constexpr int SEL_THREADS = 1024;
 // Keys of a CTA's slice are staged in dynamic shared memory when they fit.
-constexpr int SEL_SMEM_BYTES = 200 * 1024;
+constexpr int SEL_SMEM_BYTES = 176 * 1024;
+// Candidates of the third pass of the 32-bit select held per CTA.
+constexpr int SEL_CAND = 4096;
 
 __device__ __forceinline__ uint32_t key_bits(float v) { return __float_as_uint(v); }
 __device__ __forceinline__ unsigned long long key_bits(double v)
@@ -28,7 +34,7 @@ __device__ __forceinline__ unsigned long long key_bits(double v)
     return (unsigned long long)__double_as_longlong(v);
 }
 
-// Shared state of the cluster-wide selection (one instance per CTA).
+// Shared state of the cluster-wide selection (one instance per CTA); 64-bit keys.
 template <typename KeyT> struct SelShared {
     unsigned int hist[256];
     unsigned int total[256];
@@ -41,6 +47,166 @@ template <typename KeyT> struct SelShared {
     int my_eq;        // keys equal to thr in this CTA's slice
 };
 
+// 32-bit keys: one histogram per pass and the compacted candidates.
+template <> struct SelShared<uint32_t> {
+    unsigned int hist1[2048];   // key bits 31..21
+    unsigned int hist2[2048];   // key bits 20..10 (keys whose bits 31..21 match)
+    unsigned int hist3[1024];   // key bits 9..0 (keys whose bits 31..10 match)
+    uint32_t cand[SEL_CAND];    // this CTA's keys that match bits 31..21 (when they fit)
+    int n_cand;
+    uint32_t prefix;
+    int krem;
+    int bucket;
+    unsigned int warp_cnt[32];
+    unsigned int warp_scan[32];
+    int eq_before;
+    int taken;
+    int my_eq;
+};
+
+// Adds one key digit per lane to a shared histogram (d = 0xffffffff: none):
+// one shared atomic per distinct digit per warp (residuals cluster in a few
+// exponent bins, so per-lane atomics would serialise). Whole warps only.
+__device__ __forceinline__ void hist_add(unsigned int *hist, unsigned d)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (d != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1)
+        atomicAdd(&hist[d], (unsigned)__popc(peers));
+}
+
+// Sums the cluster's copies of a NB-bin histogram (after a cluster barrier)
+// and finds the digit that holds the krem-th largest key: thread t owns the
+// NB / SEL_THREADS bins starting at the t-th from the top (blocks of
+// SEL_THREADS threads), a block-wide scan of
+// the owned sums locates the digit. Every CTA computes the same result, into
+// sh.prefix (digit), sh.krem (rank inside the digit) and sh.bucket (its
+// cluster-wide count).
+template <int NB>
+__device__ __forceinline__ void cluster_digit(cg::cluster_group &cl, SelShared<uint32_t> &sh, unsigned int *hist,
+                                              int krem)
+{
+    const unsigned C = cl.num_blocks();
+    constexpr int per = NB / SEL_THREADS;   // bins per thread; blocks of SEL_THREADS threads
+    unsigned v[per];
+    unsigned mine = 0;
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        const int d = NB - 1 - ((int)threadIdx.x * per + q);
+        unsigned s = 0;
+        for (unsigned r = 0; r < C; ++r)
+            s += cl.map_shared_rank(hist, r)[d];
+        v[q] = s;
+        mine += s;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        sh.warp_cnt[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        unsigned w = lane < nw ? sh.warp_cnt[lane] : 0u;
+        unsigned wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o)
+                wi += y;
+        }
+        sh.warp_scan[lane] = wi - w;   // exclusive
+    }
+    __syncthreads();
+    incl += sh.warp_scan[warp];
+    unsigned acc = incl - mine;
+    if (acc < (unsigned)krem && (unsigned)krem <= incl) {
+        // the digit is among this thread's bins, walked from the top
+#pragma unroll
+        for (int q = 0; q < per; ++q) {
+            if (acc + v[q] >= (unsigned)krem) {
+                sh.prefix = (uint32_t)(NB - 1 - ((int)threadIdx.x * per + q));
+                sh.krem = krem - (int)acc;
+                sh.bucket = (int)v[q];
+                break;
+            }
+            acc += v[q];
+        }
+    }
+    __syncthreads();
+}
+
+// 32-bit cluster-wide threshold (see cluster_select_threshold).
+template <typename KeyFn>
+__device__ void cluster_select_threshold32(cg::cluster_group &cl, SelShared<uint32_t> &sh, int n_local, int k,
+                                           KeyFn key, uint32_t &thr, int &take_eq, int &eq_total)
+{
+    for (int t = threadIdx.x; t < 2048; t += blockDim.x) {
+        sh.hist1[t] = 0u;
+        sh.hist2[t] = 0u;
+    }
+    for (int t = threadIdx.x; t < 1024; t += blockDim.x)
+        sh.hist3[t] = 0u;
+    if (threadIdx.x == 0)
+        sh.n_cand = 0;
+    __syncthreads();
+    // pass 1: bits 31..21
+    for (int base = 0; base < n_local; base += blockDim.x) {
+        const int idx = base + threadIdx.x;
+        hist_add(sh.hist1, idx < n_local ? key(idx) >> 21 : 0xffffffffu);
+    }
+    cl.sync();   // every CTA's first histogram is complete
+    cluster_digit<2048>(cl, sh, sh.hist1, k);
+    const uint32_t d1 = sh.prefix;
+    int krem = sh.krem;
+    // pass 2: bits 20..10 of the keys in digit d1; they are also compacted
+    // when this CTA's share fits
+    const bool compact = sh.hist1[d1] <= (unsigned)SEL_CAND;
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < n_local; base += blockDim.x) {
+        const int idx = base + threadIdx.x;
+        const uint32_t kv = idx < n_local ? key(idx) : 0u;
+        const bool in = idx < n_local && (kv >> 21) == d1;
+        hist_add(sh.hist2, in ? (kv >> 10) & 2047u : 0xffffffffu);
+        if (compact) {
+            const unsigned b = __ballot_sync(0xffffffffu, in);
+            int pos = 0;
+            if (lane == 0 && b)
+                pos = atomicAdd(&sh.n_cand, __popc(b));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (in)
+                sh.cand[pos + __popc(b & ((1u << lane) - 1u))] = kv;
+        }
+    }
+    cl.sync();
+    cluster_digit<2048>(cl, sh, sh.hist2, krem);
+    const uint32_t pre2 = (d1 << 11) | sh.prefix;
+    krem = sh.krem;
+    // pass 3: bits 9..0 of the keys that match bits 31..10
+    const int nc = compact ? sh.n_cand : n_local;
+    for (int base = 0; base < nc; base += blockDim.x) {
+        const int idx = base + threadIdx.x;
+        unsigned d = 0xffffffffu;
+        if (idx < nc) {
+            const uint32_t kv = compact ? sh.cand[idx] : key(idx);
+            if ((kv >> 10) == pre2)
+                d = kv & 1023u;
+        }
+        hist_add(sh.hist3, d);
+    }
+    cl.sync();
+    cluster_digit<1024>(cl, sh, sh.hist3, krem);
+    // no CTA may leave (or reuse its histograms) while a peer still reads them
+    cl.sync();
+    thr = (pre2 << 10) | sh.prefix;
+    take_eq = sh.krem;
+    eq_total = sh.bucket;
+}
+
 // Cluster-wide threshold: thr = k-th largest key over the union of the CTAs'
 // slices (1 <= k <= total count), take_eq = keys equal to thr inside the top
 // k, eq_total = keys equal to thr. Every thread of every CTA of the cluster
@@ -49,6 +215,10 @@ template <typename KeyT, typename KeyFn>
 __device__ void cluster_select_threshold(cg::cluster_group &cl, SelShared<KeyT> &sh, int n_local, int k,
                                          KeyFn key, KeyT &thr, int &take_eq, int &eq_total)
 {
+    if constexpr (sizeof(KeyT) == 4) {
+        cluster_select_threshold32(cl, sh, n_local, k, key, thr, take_eq, eq_total);
+        return;
+    } else {
     const unsigned C = cl.num_blocks();
     KeyT prefix = 0, mask = 0;
     int krem = k;
@@ -121,6 +291,7 @@ __device__ void cluster_select_threshold(cg::cluster_group &cl, SelShared<KeyT> 
     thr = prefix;
     take_eq = krem;
     eq_total = sh.bucket;
+    }
 }
 
 // Ordered pass over this CTA's slice: on_item(idx, take) for every local idx,

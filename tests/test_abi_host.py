@@ -43,9 +43,11 @@ def test_struct_layout_matches_header(tmp_path):
 #include <stdio.h>
 #include "bp_gb300.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(bp_options), sizeof(bp_run_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bp_options), sizeof(bp_run_stats),
          offsetof(bp_options, cuda_stream), offsetof(bp_options, kernel_variant),
-         offsetof(bp_run_stats, device_ms), offsetof(bp_run_stats, status));
+         offsetof(bp_run_stats, device_ms), offsetof(bp_run_stats, status),
+         sizeof(bp_profile), offsetof(bp_profile, sweep_launches),
+         sizeof(bp_tune_result), offsetof(bp_tune_result, ms_per_round));
   return 0;
 }
 """)
@@ -54,7 +56,9 @@ int main(void) {
     vals = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     assert vals == [ctypes.sizeof(bp.bp_options), ctypes.sizeof(bp.bp_run_stats),
                     bp.bp_options.cuda_stream.offset, bp.bp_options.kernel_variant.offset,
-                    bp.bp_run_stats.device_ms.offset, bp.bp_run_stats.status.offset]
+                    bp.bp_run_stats.device_ms.offset, bp.bp_run_stats.status.offset,
+                    ctypes.sizeof(bp.bp_profile), bp.bp_profile.sweep_launches.offset,
+                    ctypes.sizeof(bp.bp_tune_result), bp.bp_tune_result.ms_per_round.offset]
 
 
 def test_status_strings(L):
@@ -100,3 +104,12 @@ def test_invalid_graphs_rejected_on_host(L):
         np.array([0, 4, p.n]), 2, rp, col, rev))
     _expect(bp.BP_ERR_BAD_GRAPH, lambda: bp.bp_create_batch(
         np.array([0, 5, 4, p.n]), 2, rp, col, rev))
+
+
+def test_tuning_entry_points_reject_bad_arguments(L):
+    out = bp.bp_tune_result()
+    assert L.bp_autotune(None, 0, 1.0, 1e-4, None, 4, ctypes.byref(out)) == bp.BP_ERR_INVALID_ARG
+    assert L.bp_set_graph_parallelism(None, None) == bp.BP_ERR_INVALID_ARG
+    cand = np.array([0.5])
+    assert L.bp_autotune_parallelism(None, bp.BP_RNBP, cand.ctypes.data, 1, 1e-4, 10, None,
+                                     None) == bp.BP_ERR_INVALID_ARG

@@ -1,0 +1,104 @@
+"""The size-class autotuner and per-graph parallelism of batches.
+
+* bp_autotune measures every binary update mapping and records the fastest
+  under the handle's size class; kernel_variant = 0 then uses it (the
+  mappings compute the same bits, so only the speed changes).
+* bp_set_graph_parallelism gives each graph of a batch its own p: with FP64
+  messages each graph replays the oracle run of that graph alone at its p
+  exactly (same frontiers, rounds, commits; beliefs to 1e-9 on graphs whose
+  run contracts, beta <= 0.6).
+* bp_autotune_parallelism picks per size class the candidate whose graphs
+  converge in the fewest rounds; the test recomputes the scores from plain
+  runs and checks the choice."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_11469_gb300 import bp, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_autotune_records_choice():
+    prob = synth.ising_grid_batch(40, 2.5, range(8))
+    with bp.Graph(prob) as g:
+        r = g.autotune("rnbp", 0.5, eps=1e-4, trial_rounds=8)
+        assert r["kernel_variant"] in (1, 2, 3, 4, 5)
+        tried = [v for v in (1, 2, 3, 4, 5) if r["ms_per_round"][v] > 0]
+        assert tried == [1, 2, 3, 4, 5]
+        best = min(tried, key=lambda v: r["ms_per_round"][v])
+        assert r["kernel_variant"] == best
+        sc = r["size_class"]
+        assert sc & 3 == bp.BP_RNBP and (sc >> 2) & 3 == bp.BP_F32
+        assert (sc >> 4) & 31 == int(np.floor(np.log2(1600))) and (sc >> 9) & 31 == 3
+        assert (sc >> 14) & 3 == 0   # grid: degree <= 4
+        with pytest.raises(bp.BPError):
+            g.beliefs()   # trial runs leave no result
+        st_auto = g.run("rnbp", 0.5, eps=1e-4, max_rounds=40, seed=1)
+        b_auto = g.beliefs()
+        st_fix = g.run("rnbp", 0.5, eps=1e-4, max_rounds=40, seed=1, kernel_variant=r["kernel_variant"])
+        assert st_auto["rounds"] == st_fix["rounds"]
+        assert np.array_equal(b_auto, g.beliefs())
+
+
+@pytest.mark.parametrize("sched", ["rnbp", "rbp", "rs"])
+def test_graph_parallelism_replays_each_graph(sched):
+    prob = synth.er_batch(6, 11, n_max=400, beta_max=0.6)
+    ps = np.array([0.15, 0.3, 0.5, 0.7, 0.9, 0.4])
+    cap = 3000
+    with bp.Graph(prob) as g:
+        g.set_graph_parallelism(ps)
+        g.run(sched, 0.99, eps=1e-6, max_rounds=cap, msg_dtype="f64", seed=4)
+        gst = g.graph_stats()
+        bel = g.beliefs()
+    for q in range(prob.n_graphs):
+        ref = oracle.run(prob.graph(q), sched, parallelism=ps[q], eps=1e-6, max_rounds=cap, seed=4, graph_id=q)
+        assert (gst[q]["converged"], gst[q]["rounds"], gst[q]["committed_updates"]) == \
+            (int(ref["converged"]), ref["rounds"], ref["committed_updates"]), q
+        assert ref["converged"], q
+        v0, v1 = prob.graph_var_offsets[q], prob.graph_var_offsets[q + 1]
+        assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < 1e-9, q
+    # the per-graph values matter: graphs with different p take different round counts
+    assert len({x["rounds"] for x in gst}) > 1
+
+
+def test_uniform_graph_parallelism_equals_run_value():
+    prob = synth.ising_grid_batch(30, 2.0, range(4))
+    with bp.Graph(prob) as g:
+        st0 = g.run("rnbp", 0.5, eps=1e-4, max_rounds=100, seed=2)
+        b0 = g.beliefs()
+        g.set_graph_parallelism(np.full(4, 0.5))
+        st1 = g.run("rnbp", 0.9, eps=1e-4, max_rounds=100, seed=2)
+        b1 = g.beliefs()
+        g.set_graph_parallelism(None)
+        st2 = g.run("rnbp", 0.5, eps=1e-4, max_rounds=100, seed=2)
+        assert (st0["rounds"], st0["committed_updates"]) == (st1["rounds"], st1["committed_updates"])
+        assert (st0["rounds"], st0["committed_updates"]) == (st2["rounds"], st2["committed_updates"])
+        assert np.array_equal(b0, b1)
+
+
+def test_autotune_parallelism_choice():
+    prob = synth.er_batch(48, 5, n_max=2000)
+    cand = [0.3, 0.6, 0.9]
+    cap = 400
+    sizes = np.diff(prob.graph_var_offsets)
+    cls = np.floor(np.log2(np.maximum(sizes, 1))).astype(int)
+    with bp.Graph(prob) as g:
+        chosen = g.autotune_parallelism("rnbp", cand, eps=1e-4, max_rounds=cap, seed=0)
+        scores = {}
+        g.set_graph_parallelism(None)
+        for c in cand:
+            g.run("rnbp", c, eps=1e-4, max_rounds=cap, seed=0)
+            for q, x in enumerate(g.graph_stats()):
+                s = x["rounds"] if x["converged"] else 2 * cap
+                scores[(cls[q], c)] = scores.get((cls[q], c), 0) + s
+    for q in range(prob.n_graphs):
+        best = min(cand, key=lambda c: (scores[(cls[q], c)], cand.index(c)))
+        assert chosen[q] == best, (q, cls[q], chosen[q], best)
+    print("chosen p per size class:", {int(k): float(chosen[np.argmax(cls == k)]) for k in np.unique(cls)})

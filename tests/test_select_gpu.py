@@ -1,0 +1,87 @@
+"""The frontier selection is an exact top-k of the residuals the device
+computed (Section III-D; ties to the smaller id). For storage formats whose
+residuals are FP32 the GPU's residuals cannot be recomputed bit for bit on the
+host, so the test reads them back: a run stopped by max_rounds = t - 1 leaves
+the residuals of the evaluation that round t selects from (bp_get_residuals),
+and the same run with max_rounds = t records round t's frontier. The frontier
+must be the top k of those residuals by (residual desc, id asc): RBP over
+messages, RS over vertex residuals (max over incoming messages). Cases cover
+the compacted and the uncompacted third pass of the 32-bit select (a graph
+with constant potentials has few distinct residuals, so whole slices share a
+digit) and ties that straddle the threshold."""
+import numpy as np
+import pytest
+
+from paper_1909_11469_gb300 import bp, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _constant(side, lam, beta):
+    p = synth.ising_grid(side, 1.0, 0)
+    p.unary_log = np.tile(np.array([-lam, lam], dtype=np.float32), p.n)
+    p.pair_log = np.full(p.m, beta, dtype=np.float32)
+    return p
+
+
+def _problems():
+    return {
+        "grid_batch": synth.ising_grid_batch(100, 2.5, range(4)),
+        "constant": _constant(300, 0.3, 0.8),
+        "er": synth.er_batch(24, 9, n_max=3000),
+    }
+
+
+def _topk(keys, k):
+    order = np.lexsort((np.arange(len(keys)), -keys))
+    sel = np.zeros(len(keys), dtype=bool)
+    sel[order[:k]] = True
+    return sel
+
+
+def _bits(trace_row, count):
+    w = np.asarray(trace_row, dtype=np.uint32)
+    bits = (w[:, None] >> np.arange(32, dtype=np.uint32)) & 1
+    return bits.ravel()[:count].astype(bool)
+
+
+@pytest.mark.parametrize("name", ["grid_batch", "constant", "er"])
+@pytest.mark.parametrize("dtype", ["f32", "q16", "f64"])
+@pytest.mark.parametrize("sched,par", [("rbp", 0.1), ("rbp", 0.001), ("rs", 0.1), ("rs", 0.01)])
+def test_frontier_is_exact_topk(name, dtype, sched, par):
+    prob = _problems()[name]
+    gv = prob.graph_var_offsets
+    ge = prob.row_ptr[gv]
+    for t in (1, 3):
+        with bp.Graph(prob) as g:
+            g.run(sched, par, eps=1e-12, max_rounds=t - 1, msg_dtype=dtype, seed=1)
+            R = g.residuals()
+            st = g.run(sched, par, eps=1e-12, max_rounds=t, msg_dtype=dtype, seed=1, record_trace=1,
+                       trace_capacity=t)
+            tr = g.trace(sched)
+        assert st["rounds"] == t
+        count = prob.n if sched == "rs" else prob.m
+        got = _bits(tr[t - 1], count)
+        if sched == "rs":
+            deg = np.diff(prob.row_ptr)
+            vres_all = np.zeros(prob.n)
+            nz = deg > 0
+            vres_all[nz] = np.maximum.reduceat(R[prob.rev], prob.row_ptr[:-1][nz])
+        for q in range(prob.n_graphs):
+            v0, v1, e0, e1 = gv[q], gv[q + 1], ge[q], ge[q + 1]
+            Mg, nv = e1 - e0, v1 - v0
+            if sched == "rbp":
+                k = int(min(max(np.ceil(par * Mg), 1), Mg))
+                want = _topk(R[e0:e1], k)
+                assert np.array_equal(got[e0:e1], want), (name, dtype, sched, par, t, q)
+            else:
+                vres = vres_all[v0:v1]
+                k = int(min(max(np.ceil(par * Mg), 1), nv))
+                want = _topk(vres, k)
+                assert np.array_equal(got[v0:v1], want), (name, dtype, sched, par, t, q)
