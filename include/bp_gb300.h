@@ -122,6 +122,10 @@ typedef struct {
                                  CUDA cores, 2 = tiles on the tensor cores with BF16
                                  products, 3 = tensor cores with the BF16 residual
                                  products added (close to FP32) */
+    int32_t select_path;      /* RBP / RS top-k selection (same frontier either way):
+                                 0 = automatic (by an occupancy-based time estimate), 1 =
+                                 one thread-block cluster per graph, 2 = grid-wide
+                                 kernels (for a few large graphs) */
 } bp_options;
 
 /* Phase timings and launch counts of the last bp_run. The timings are filled
@@ -145,6 +149,8 @@ typedef struct {
     double select_ms;          /* part of frontier_ms: selection, RnBP commit, splash levels */
     double sweep_ms;           /* part of frontier_ms: the Residual Splash sweeps */
     int64_t sweep_launches;    /* fused sweep-step launches (binary RS), counted with sweep_ms */
+    int32_t select_ctas[2];    /* RBP, RS selection of the run: CTAs per graph of the cluster
+                                  kernels (0 when the grid-wide kernels ran; always filled) */
 } bp_profile;
 
 /* Fills *opt with the defaults listed above. */

@@ -122,6 +122,14 @@ struct bp_graph {
     int32_t *d_running = nullptr;
     int32_t *d_queue = nullptr;
     int32_t max_graph_vertices = 0;
+    int32_t max_graph_edges = 0;
+    int32_t sel_plan[4][6];          // per message dtype: RBP CTAs, bytes, grid flag; RS the same
+    bool sel_planned[4] = {false, false, false, false};
+    // grid-wide selection buffers (allocated when a plan picks the grid kernels)
+    GSelState *d_gsel = nullptr;
+    unsigned int *d_gsel_hist = nullptr;
+    int32_t *d_gsel_tie = nullptr, *d_chunk_off = nullptr;
+    int32_t n_chunks_rbp = 0, n_chunks_rs = 0;
     // tensor-core tiles of consecutive vertices (<= 128 out-edges, <= 32 vertices)
     int32_t *d_tc_tiles = nullptr;
     int32_t n_tc_tiles = 0;
@@ -205,6 +213,11 @@ DevGraph dev_graph(const bp_graph *g)
     d.qscale = g->qscale;
     d.vec_ok = 1;   // every device array of a handle comes from cudaMalloc (256-byte aligned)
     d.sel_smem_bytes = g->sel_smem_bytes;
+    d.max_ge = g->max_graph_edges;
+    d.max_gv = g->max_graph_vertices;
+    d.sel_c[0] = d.sel_c[1] = 1;
+    d.sel_dyn[0] = d.sel_dyn[1] = 0;
+    d.sel_grid[0] = d.sel_grid[1] = 0;
     d.row_ptr = g->d_row_ptr;
     d.col = g->d_col;
     d.rev = g->d_rev;
@@ -240,7 +253,27 @@ DevRun dev_run(const bp_graph *g)
     r.lvl_list = g->d_lvl_list;
     r.lvl_cnt = g->d_lvl_cnt;
     r.graph_p = g->graph_p_set ? g->d_graph_p : nullptr;
+    r.gsel = g->d_gsel;
+    r.gsel_hist = g->d_gsel_hist;
+    r.gsel_tie = g->d_gsel_tie;
+    r.chunk_off = g->d_chunk_off;
+    r.n_chunks_rbp = g->n_chunks_rbp;
+    r.n_chunks_rs = g->n_chunks_rs;
     return r;
+}
+
+// Selection shape of a run: the cluster plan of the handle for this storage
+// format and the grid-wide flags the run chose (bit 0 RBP, bit 1 RS).
+void apply_select_plan(const bp_graph *g, int dtype, int sel_grid_bits, DevGraph &dg)
+{
+    if (g->sel_planned[dtype]) {
+        dg.sel_c[0] = g->sel_plan[dtype][0];
+        dg.sel_dyn[0] = g->sel_plan[dtype][1];
+        dg.sel_c[1] = g->sel_plan[dtype][3];
+        dg.sel_dyn[1] = g->sel_plan[dtype][4];
+    }
+    dg.sel_grid[0] = sel_grid_bits & 1;
+    dg.sel_grid[1] = (sel_grid_bits >> 1) & 1;
 }
 
 size_t dtype_size(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }   // BF16, Q16: 2
@@ -337,8 +370,10 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     g->h_gv_off = gv;
     g->h_ge_off = ge;
     int64_t max_keys = 1;
-    for (int32_t q = 0; q < n_graphs; ++q)
+    for (int32_t q = 0; q < n_graphs; ++q) {
         g->max_graph_vertices = std::max(g->max_graph_vertices, gv[(size_t)q + 1] - gv[(size_t)q]);
+        g->max_graph_edges = std::max(g->max_graph_edges, ge[(size_t)q + 1] - ge[(size_t)q]);
+    }
     for (int32_t q = 0; q < n_graphs; ++q)
         max_keys = std::max<int64_t>(max_keys, std::max<int64_t>(ge[(size_t)q + 1] - ge[(size_t)q],
                                                                  gv[(size_t)q + 1] - gv[(size_t)q]));
@@ -458,19 +493,23 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
         break;
     case SCHED_RBP:
         launch_select_rbp(dtype, dg, dr, rp, s);
-        kernels += 1;
+        kernels += (dg.sel_grid[0] && dr.gsel) ? grid_select_launches(dtype, false) : 1;
         break;
     default: {   // SCHED_RS
         launch_select_rs(dtype, dg, dr, rp, s);
-        kernels += 1;
+        kernels += (dg.sel_grid[1] && dr.gsel) ? grid_select_launches(dtype, true) : 1;
         const int h = rp.splash_depth;
         auto level_of = [h](int step) { return step <= h ? h - step : step - h; };
+        // the cluster selection forms the BFS levels (and the level lists) itself
+        const bool in_select = !(dg.sel_grid[1] && dr.gsel);
         if (dg.epm == 1 && dr.lvl_list && h <= LVL_MAX) {
-            // sweeps over per-level vertex lists built by the last BFS level
-            for (int d = 1; d < h; ++d)
-                launch_bfs_level(dg, dr, d, s);
-            launch_bfs_level_lists(dg, dr, h, h, s);
-            kernels += any ? (h > 0 ? h : 1) : 0;
+            // sweeps over per-level vertex lists
+            if (!in_select) {
+                for (int d = 1; d < h; ++d)
+                    launch_bfs_level(dg, dr, d, s);
+                launch_bfs_level_lists(dg, dr, h, h, s);
+                kernels += any ? (h > 0 ? h : 1) : 0;
+            }
             if (ev)
                 cudaEventRecord(ev[3], s);
             launch_splash_list_step(dtype, dg, dr, -1, level_of(0), s);
@@ -480,9 +519,11 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
             kernels += any ? 2 * h + 2 : 0;
             break;
         }
-        for (int d = 1; d <= h; ++d)
-            launch_bfs_level(dg, dr, d, s);
-        kernels += any ? h : 0;
+        if (!in_select) {
+            for (int d = 1; d <= h; ++d)
+                launch_bfs_level(dg, dr, d, s);
+            kernels += any ? h : 0;
+        }
         if (ev)
             cudaEventRecord(ev[3], s);
         if (dg.epm == 1) {
@@ -533,6 +574,7 @@ int get_graph_exec(bp_graph *g, int dtype, const RunParams &rp, int rounds, Cach
     c.epm = epm_of(g);
     c.kernels = 0;
     DevGraph dg = dev_graph(g);
+    apply_select_plan(g, dtype, rp.sel_grid, dg);
     DevRun dr = dev_run(g);
     BP_CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int r = 0; r < rounds; ++r)
@@ -592,6 +634,7 @@ void bp_default_options(bp_options *opt)
     opt->kernel_variant = 0;
     opt->profile = 0;
     opt->potts_path = 0;
+    opt->select_path = 0;
 }
 
 int bp_create_graph(int32_t n_vars, int32_t n_states, int64_t n_dir_edges, const int64_t *row_ptr,
@@ -746,6 +789,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "bad high_p or ratio_threshold");
     if (opt.potts_path < 0 || opt.potts_path > 3)
         return fail(BP_ERR_INVALID_ARG, "potts_path must be 0..3");
+    if (opt.select_path < 0 || opt.select_path > 2)
+        return fail(BP_ERR_INVALID_ARG, "select_path must be 0..2");
     if (opt.kernel_variant < 0 || opt.kernel_variant > 5)
         return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 5]");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
@@ -808,7 +853,43 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     }
 
     cudaStream_t s = (cudaStream_t)opt.cuda_stream;
+    if ((schedule == BP_RBP || schedule == BP_RS) &&
+        (!g->sel_planned[dtype] || (opt.select_path == 2 && !g->d_gsel))) {
+        int32_t c[2], dyn[2], grid[2];
+        plan_select(dtype, g->G, g->max_graph_edges, g->max_graph_vertices, c, dyn, grid);
+        if ((grid[0] || grid[1] || opt.select_path == 2) && !g->d_gsel) {
+            // buffers of the grid-wide selection, kept until the handle is destroyed
+            std::vector<int32_t> co(2 * ((size_t)g->G + 1));
+            g->n_chunks_rbp = grid_select_chunks(g->h_ge_off.data(), g->G, co.data());
+            g->n_chunks_rs = grid_select_chunks(g->h_gv_off.data(), g->G, co.data() + g->G + 1);
+            const size_t bins = (size_t)g->G * grid_select_bins();
+            if ((rc = dalloc(&g->d_gsel, (size_t)g->G)) != BP_OK ||
+                (rc = dalloc(&g->d_gsel_hist, bins)) != BP_OK ||
+                (rc = dalloc(&g->d_gsel_tie, (size_t)std::max(g->n_chunks_rbp, g->n_chunks_rs))) != BP_OK ||
+                (rc = dalloc(&g->d_chunk_off, co.size())) != BP_OK)
+                return rc;
+            BP_CK(cudaMemset(g->d_gsel_hist, 0, sizeof(unsigned int) * bins));
+            BP_CK(cudaMemcpy(g->d_chunk_off, co.data(), sizeof(int32_t) * co.size(), cudaMemcpyHostToDevice));
+            clear_cache(g);   // captured rounds hold the run buffers
+        }
+        g->sel_plan[dtype][0] = c[0];
+        g->sel_plan[dtype][1] = dyn[0];
+        g->sel_plan[dtype][2] = grid[0];
+        g->sel_plan[dtype][3] = c[1];
+        g->sel_plan[dtype][4] = dyn[1];
+        g->sel_plan[dtype][5] = grid[1];
+        g->sel_planned[dtype] = true;
+    }
     DevGraph dg = dev_graph(g);
+    {
+        int bits = g->sel_planned[dtype] ? (g->sel_plan[dtype][2] | (g->sel_plan[dtype][5] << 1)) : 0;
+        if (opt.select_path != 0)
+            bits = opt.select_path == 2 ? 3 : 0;
+        if (!g->d_gsel)
+            bits = 0;
+        apply_select_plan(g, dtype, bits, dg);
+        rp.sel_grid = bits;
+    }
     DevRun dr = dev_run(g);
     g->has_result = false;
     auto t_start = std::chrono::steady_clock::now();
@@ -970,6 +1051,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         if (schedule == BP_RS && epm_of(g) == 1)
             prof.sweep_launches = (int64_t)(live > 0 ? live - 1 : 0) * (2 * opt.splash_depth + 2);
     }
+    for (int w = 0; w < 2; ++w)
+        prof.select_ctas[w] = (dg.sel_grid[w] && dr.gsel) ? 0 : dg.sel_c[w];
     g->last_profile = prof;
     g->has_result = true;
     g->res_dtype = dtype;
@@ -1245,6 +1328,10 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_lvl_list);
     dfree(g->d_lvl_cnt);
     dfree(g->d_graph_p);
+    dfree(g->d_gsel);
+    dfree(g->d_gsel_hist);
+    dfree(g->d_gsel_tie);
+    dfree(g->d_chunk_off);
     dfree(g->d_gs);
     dfree(g->d_red_max);
     dfree(g->d_red_cnt);

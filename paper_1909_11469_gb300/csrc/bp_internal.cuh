@@ -37,7 +37,12 @@ struct DevGraph {
     int32_t epm;              // stored elements per message: 1 (binary log-odds) or k
     float qscale;             // Q16 storage: log-odds per integer step
     int32_t vec_ok;           // 1: rev, q and message buffers are 16-byte aligned
-    int32_t sel_smem_bytes;   // dynamic shared memory of the selection kernels
+    int32_t sel_smem_bytes;   // dynamic shared memory of the selection kernels (set per launch)
+    int32_t max_ge;           // largest directed-edge count of a graph
+    int32_t max_gv;           // largest vertex count of a graph
+    int32_t sel_c[2];         // selection clusters: CTAs per graph (RBP, RS), planned per run
+    int32_t sel_dyn[2];       // selection clusters: staged-key bytes per CTA (RBP, RS)
+    int32_t sel_grid[2];      // 1: select with the grid-wide kernels instead (RBP, RS)
     const int32_t *row_ptr;   // [n+1]
     const int32_t *col;       // [M]
     const int32_t *rev;       // [M]
@@ -74,11 +79,22 @@ struct RunParams {
     float eps_f;              // smallest float >= eps: (double)r >= eps  <=>  r >= eps_f for float r
     int32_t tc_path;          // shared-table update: 0 per-vertex, 1 tiles/CUDA cores, 2 tiles/tensor
                               // cores, 3 tiles/tensor cores with residual products
+    int32_t sel_grid;         // grid-wide selection: bit 0 RBP, bit 1 RS (keys the captured rounds)
 };
 
 // eps in the residual type, chosen so that the comparison equals the FP64 test.
 __device__ __forceinline__ float eps_in(const RunParams &rp, float) { return rp.eps_f; }
 __device__ __forceinline__ double eps_in(const RunParams &rp, double) { return rp.eps; }
+
+// Grid-wide selection state of one graph (large graphs, bp_select_grid.cu):
+// the key prefix fixed so far (the threshold after the last pass), the rank
+// of the k-th key inside the current digit (after the last pass: the number of
+// threshold ties to take) and the count of keys in that digit.
+struct GSelState {
+    unsigned long long prefix;
+    int32_t krem;
+    int32_t eq_total;
+};
 
 // Mutable per-run device buffers.
 struct DevRun {
@@ -96,6 +112,12 @@ struct DevRun {
     int32_t *lvl_list;            // [(LVL_MAX+1) * n] Residual Splash vertices of each level
     int32_t *lvl_cnt;             // [LVL_MAX+1] entries of each level list
     const double *graph_p;        // [G] per-graph parallelism, or null: every graph uses rp.low_p
+    // grid-wide selection (large graphs; null when unused)
+    GSelState *gsel;              // [G]
+    unsigned int *gsel_hist;      // [G * 2048]
+    int32_t *gsel_tie;            // [chunks] threshold ties per chunk, then their exclusive scan
+    const int32_t *chunk_off;     // [2 (G + 1)] chunk offsets per graph: RBP (edges), then RS (vertices)
+    int32_t n_chunks_rbp, n_chunks_rs;
 };
 
 // Parallelism of graph gg: RnBP LowP, or the RBP / RS frontier fraction.

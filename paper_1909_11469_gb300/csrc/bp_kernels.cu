@@ -743,7 +743,7 @@ __global__ void __launch_bounds__(BLOCK) k_bfs_level_lists(DevGraph g, DevRun dr
 // fused with the evaluation of level Le (the same sub-step pairing as
 // k_splash_step), one thread per listed vertex, grid-stride.
 template <typename S>
-__global__ void __launch_bounds__(BLOCK) k_splash_list_step(DevGraph g, DevRun dr, int Lc, int Le)
+__global__ void __launch_bounds__(BLOCK, 6) k_splash_list_step(DevGraph g, DevRun dr, int Lc, int Le)
 {
     const int nc = Lc >= 0 ? dr.lvl_cnt[Lc] : 0;
     const int ne = Le >= 0 ? dr.lvl_cnt[Le] : 0;
@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(BLOCK) k_splash_list_step(DevGraph g, DevRun d
         if (t < nc)
             splash_commit_vertex<S>(g, dr, lc[t]);
         else
-            splash_eval_vertex<S>(g, dr, le[t - nc], Lc);
+            splash_eval_vertex<S, 4>(g, dr, le[t - nc], Lc);
     }
 }
 
@@ -994,7 +994,7 @@ void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int
 {
     if (g.n == 0)
         return;
-    const int nb = std::min(blocks_for(g.n, BLOCK), 152 * 8);
+    const int nb = std::min(blocks_for(g.n, BLOCK), 152 * 6);   // one wave at 6 blocks per SM
     BPG_DISPATCH4(dtype, (k_splash_list_step<S><<<nb, BLOCK, 0, s>>>(g, dr, Lc, Le)));
 }
 

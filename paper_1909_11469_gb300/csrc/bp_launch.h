@@ -19,8 +19,20 @@ void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const Ru
 // One-time attribute set-up of the selection kernels (dynamic shared memory).
 void prepare_select_kernels();
 int select_smem_limit();
+// Cluster shape of the RBP and RS selection launches for this graph set and
+// storage format (host occupancy queries; call outside stream capture).
+// grid_out[w] = 1 where the grid-wide kernels are estimated faster (a few large graphs).
+void plan_select(int dtype, int G, int max_ge, int max_gv, int32_t c_out[2], int32_t dyn_out[2],
+                 int32_t grid_out[2]);
 void launch_select_rbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
 void launch_select_rs(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
+// Grid-wide selection for a few large graphs (bp_select_grid.cu): kernels per
+// call, chunk offsets of a graph set (returns the chunk count), histogram bins.
+void launch_select_rbp_grid(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
+void launch_select_rs_grid(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
+int grid_select_launches(int dtype, bool rs);
+int grid_select_chunks(const int32_t *off, int G, int32_t *chunk_off);
+int grid_select_bins();
 void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s);
 // Residual Splash (binary messages): commit level Lc and evaluate level Le
 // in one kernel (Lc or Le may be -1).

@@ -15,6 +15,9 @@
 #include "bp_internal.cuh"
 #include "bp_launch.h"
 #include "bp_select.cuh"
+#include "bp_update.cuh"
+
+#include <algorithm>
 
 namespace bpg {
 
@@ -65,9 +68,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_rbp(DevGraph g, DevRun d
 
 // RS: vertex residual = max residual of the messages into the vertex; select
 // the top k_sel vertices as splash roots (level 0), every other vertex gets
-// level -1. Each CTA owns a slice of the graph's vertices.
+// level -1, then the BFS levels 1..h and (binary messages) the per-level
+// vertex lists of the sweeps. Each CTA owns a slice of the graph's vertices.
 template <typename S>
-__global__ void __launch_bounds__(SEL_THREADS) k_select_rs(DevGraph g, DevRun dr, RunParams rp)
+__global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun dr, RunParams rp)
 {
     using RT = typename ResidT<S>::T;
     using KeyT = decltype(key_bits((RT)0));
@@ -140,12 +144,81 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_rs(DevGraph g, DevRun dr
         if (take && tr)
             atomicOr(&dr.trace[(size_t)(st.rounds - 1) * rp.trace_words + (v >> 5)], 1u << (v & 31));
     });
+    // The cluster owns the whole graph, so the splash levels 1..h (multi-source
+    // BFS, pull form) are formed here too, a cluster barrier between levels.
+    // Each vertex's level is written only by the thread that owns it.
+    const int h = rp.splash_depth;
+    for (int d = 1; d <= h; ++d) {
+        cl.sync();   // level d - 1 of every slice is visible
+        for (int idx = threadIdx.x; idx < nl; idx += blockDim.x)
+            bfs_vertex(g, dr, v0 + lo + idx, d);
+    }
+    if (dr.lvl_list && h <= LVL_MAX && g.epm == 1) {
+        // per-level vertex lists of the sweeps (one reservation per level per
+        // CTA) and the round's sweep counts: a level-0 vertex is evaluated and
+        // committed once, a deeper one twice
+        __shared__ int s_cnt[LVL_MAX + 1];
+        __shared__ int s_base[LVL_MAX + 1];
+        __shared__ unsigned long long s_commit;
+        if (threadIdx.x <= (unsigned)LVL_MAX)
+            s_cnt[threadIdx.x] = 0;
+        if (threadIdx.x == 0)
+            s_commit = 0ull;
+        __syncthreads();
+        const unsigned lane = threadIdx.x & 31;
+        // counts per level (one shared atomic per warp and level)
+        for (int base = 0; base < nl; base += blockDim.x) {
+            const int idx = base + threadIdx.x;
+            const int lv = idx < nl ? (int)dr.level[v0 + lo + idx] : -1;
+            for (int L = 0; L <= h; ++L) {
+                const unsigned m = __ballot_sync(0xffffffffu, lv == L);
+                if (lane == 0 && m)
+                    atomicAdd(&s_cnt[L], __popc(m));
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x <= (unsigned)h) {
+            s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&dr.lvl_cnt[threadIdx.x], s_cnt[threadIdx.x]) : 0;
+            s_cnt[threadIdx.x] = 0;
+        }
+        __syncthreads();
+        unsigned long long c = 0;
+        for (int base = 0; base < nl; base += blockDim.x) {
+            const int idx = base + threadIdx.x;
+            const int v = v0 + lo + idx;
+            const int lv = idx < nl ? (int)dr.level[v] : -1;
+            for (int L = 0; L <= h; ++L) {
+                const unsigned m = __ballot_sync(0xffffffffu, lv == L);
+                int wpos = 0;
+                if (lane == 0 && m)
+                    wpos = atomicAdd(&s_cnt[L], __popc(m));
+                wpos = __shfl_sync(0xffffffffu, wpos, 0);
+                if (lv == L) {
+                    dr.lvl_list[(size_t)L * g.n + s_base[L] + wpos + __popc(m & ((1u << lane) - 1u))] = v;
+                    c += (unsigned long long)(g.row_ptr[v + 1] - g.row_ptr[v]) * (L == 0 ? 1u : 2u);
+                }
+            }
+        }
+        c += __shfl_xor_sync(0xffffffffu, c, 16);
+        c += __shfl_xor_sync(0xffffffffu, c, 8);
+        c += __shfl_xor_sync(0xffffffffu, c, 4);
+        c += __shfl_xor_sync(0xffffffffu, c, 2);
+        c += __shfl_xor_sync(0xffffffffu, c, 1);
+        if (lane == 0 && c)
+            atomicAdd(&s_commit, c);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_commit) {
+            atomicAdd(&dr.gs[gg].committed, s_commit);
+            atomicAdd(&dr.gs[gg].evals, s_commit);
+        }
+    }
     cl.sync();   // no CTA leaves while a peer may still address its shared memory
 }
 
 template <typename K> static void set_smem_attr(K kernel)
 {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_SMEM_BYTES);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
 }
 
 void prepare_select_kernels()
@@ -160,22 +233,88 @@ void prepare_select_kernels()
 
 int select_smem_limit() { return SEL_SMEM_BYTES; }
 
-// CTAs per graph: enough clusters to cover the SMs, at most 8 (portable size).
-static unsigned cluster_size(int G)
+// Cluster shape of one selection kernel over G graphs of at most max_keys
+// keys: every cluster owns one graph and every CTA a slice of it, staged in
+// shared memory. For each cluster size c = 1..8 the occupancy query gives how
+// many clusters fit on the GPU at once (clusters are placed inside one GPC, so
+// this is below 152 / c); the shape with the least estimated time wins, where
+// a wave of clusters costs a fixed ~12 us (passes, barriers) plus ~1 us per
+// 1000 keys of a slice.
+template <typename K>
+static double plan_one(K kernel, int G, int max_keys, int key_bytes, int32_t &c_out, int32_t &dyn_out)
 {
-    int c = 152 / (G > 0 ? G : 1);
-    c = c < 1 ? 1 : (c > 8 ? 8 : c);
-    return (unsigned)c;
+    double best = 1e300;
+    c_out = 1;
+    dyn_out = 0;
+    for (int c = 1; c <= 8; ++c) {
+        const long long per = ((long long)max_keys + c - 1) / c;
+        long long bytes = (per * key_bytes + 15) / 16 * 16;
+        if (bytes > SEL_SMEM_BYTES)
+            bytes = SEL_SMEM_BYTES;   // larger slices read their keys from global memory
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(c * std::max(1, std::min(G, 64))), 1, 1);
+        cfg.blockDim = dim3(SEL_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = (size_t)bytes;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, kernel, &cfg) != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const double waves = (double)((G + ncl - 1) / ncl);
+        const double cost = waves * (12.0 + (double)per / 1000.0);
+        if (cost < best) {
+            best = cost;
+            c_out = c;
+            dyn_out = (int32_t)bytes;
+        }
+    }
+    return best;
+}
+
+// Estimated time of the grid-wide selection: ~6 us per kernel (measured: 50
+// graphs of 39,600 keys took ~70 us in 10 kernels) plus every key of every
+// graph at ~150,000 keys per us over the whole GPU.
+static double grid_cost(int dtype, bool rs, int G, int max_keys)
+{
+    return 6.0 * grid_select_launches(dtype, rs) + (double)G * (double)max_keys / 150000.0;
+}
+
+void plan_select(int dtype, int G, int max_ge, int max_gv, int32_t c_out[2], int32_t dyn_out[2],
+                 int32_t grid_out[2])
+{
+    double t_rbp, t_rs;
+    switch (dtype) {
+    case DT_F64: t_rbp = plan_one(k_select_rbp<double>, G, max_ge, 8, c_out[0], dyn_out[0]); break;
+    case DT_F32: t_rbp = plan_one(k_select_rbp<float>, G, max_ge, 4, c_out[0], dyn_out[0]); break;
+    case DT_BF16: t_rbp = plan_one(k_select_rbp<__nv_bfloat16>, G, max_ge, 4, c_out[0], dyn_out[0]); break;
+    default: t_rbp = plan_one(k_select_rbp<int16_t>, G, max_ge, 4, c_out[0], dyn_out[0]); break;
+    }
+    if (dtype == DT_F64)
+        t_rs = plan_one(k_select_rs<double>, G, max_gv, 8, c_out[1], dyn_out[1]);
+    else
+        t_rs = plan_one(k_select_rs<float>, G, max_gv, 4, c_out[1], dyn_out[1]);
+    grid_out[0] = grid_cost(dtype, false, G, max_ge) < t_rbp ? 1 : 0;
+    grid_out[1] = grid_cost(dtype, true, G, max_gv) < t_rs ? 1 : 0;
 }
 
 template <typename K>
-static void launch_clustered(K kernel, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
+static void launch_clustered(K kernel, int which, const DevGraph &g, const DevRun &dr, const RunParams &rp,
+                             cudaStream_t s)
 {
-    const unsigned C = cluster_size(g.G);
+    const unsigned C = (unsigned)std::max(1, g.sel_c[which]);
+    DevGraph gl = g;
+    gl.sel_smem_bytes = g.sel_dyn[which];   // the kernels stage a slice only when it fits this size
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)g.G * C, 1, 1);
     cfg.blockDim = dim3(SEL_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)g.sel_smem_bytes;
+    cfg.dynamicSmemBytes = (size_t)gl.sel_smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -184,26 +323,34 @@ static void launch_clustered(K kernel, const DevGraph &g, const DevRun &dr, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, g, dr, rp);
+    cudaLaunchKernelEx(&cfg, kernel, gl, dr, rp);
 }
 
 void launch_select_rbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
 {
+    if (g.sel_grid[0] && dr.gsel) {
+        launch_select_rbp_grid(dtype, g, dr, rp, s);
+        return;
+    }
     switch (dtype) {
-    case DT_F64: launch_clustered(k_select_rbp<double>, g, dr, rp, s); break;
-    case DT_F32: launch_clustered(k_select_rbp<float>, g, dr, rp, s); break;
-    case DT_BF16: launch_clustered(k_select_rbp<__nv_bfloat16>, g, dr, rp, s); break;
-    default: launch_clustered(k_select_rbp<int16_t>, g, dr, rp, s); break;
+    case DT_F64: launch_clustered(k_select_rbp<double>, 0, g, dr, rp, s); break;
+    case DT_F32: launch_clustered(k_select_rbp<float>, 0, g, dr, rp, s); break;
+    case DT_BF16: launch_clustered(k_select_rbp<__nv_bfloat16>, 0, g, dr, rp, s); break;
+    default: launch_clustered(k_select_rbp<int16_t>, 0, g, dr, rp, s); break;
     }
 }
 
 void launch_select_rs(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
 {
+    if (g.sel_grid[1] && dr.gsel) {
+        launch_select_rs_grid(dtype, g, dr, rp, s);
+        return;
+    }
     // selection reads residuals only: FP64 runs keep double residuals, the others float
     if (dtype == DT_F64)
-        launch_clustered(k_select_rs<double>, g, dr, rp, s);
+        launch_clustered(k_select_rs<double>, 1, g, dr, rp, s);
     else
-        launch_clustered(k_select_rs<float>, g, dr, rp, s);
+        launch_clustered(k_select_rs<float>, 1, g, dr, rp, s);
 }
 
 }  // namespace bpg

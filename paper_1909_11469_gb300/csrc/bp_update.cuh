@@ -146,7 +146,7 @@ __device__ __forceinline__ unsigned int splash_commit_vertex(const DevGraph &g, 
 // Residual Splash evaluation of vertex i: new out-messages into buffer 1, an
 // incoming message read from buffer 1 when its source is at level Lc (written
 // by the previous sub-step, committed by this one), else from buffer 0.
-template <typename S>
+template <typename S, int CACHE = 8>
 __device__ __forceinline__ void splash_eval_vertex(const DevGraph &g, const DevRun &dr, int i, int Lc)
 {
     using A = typename Store<S>::A;
@@ -162,7 +162,6 @@ __device__ __forceinline__ void splash_eval_vertex(const DevGraph &g, const DevR
         h = g.udiff32[i];
         q = (const A *)g.q32;
     }
-    constexpr int CACHE = 8;
     A uin[CACHE];
     auto incoming = [&](int e) -> A {
         const int f = g.rev[e];
@@ -170,13 +169,32 @@ __device__ __forceinline__ void splash_eval_vertex(const DevGraph &g, const DevR
         return Store<S>::ld((fresh ? (const S *)b1 : b0) + f, g.qscale);
     };
     const int deg = end - beg;
+    // the first CACHE incoming messages: both buffers are read next to the
+    // source's level, so the value does not wait for the level
+    int rf[CACHE], rc[CACHE];
 #pragma unroll
     for (int k = 0; k < CACHE; ++k) {
         if (k < deg) {
-            uin[k] = incoming(beg + k);
-            h += uin[k];
+            rf[k] = g.rev[beg + k];
+            rc[k] = g.col[beg + k];
         }
     }
+#pragma unroll
+    for (int k = 0; k < CACHE; ++k) {
+        if (k < deg) {
+            const A u0 = Store<S>::ld(b0 + rf[k], g.qscale);
+            if (Lc >= 0) {
+                const A u1 = Store<S>::ld((const S *)b1 + rf[k], g.qscale);
+                uin[k] = dr.level[rc[k]] == Lc ? u1 : u0;
+            } else {
+                uin[k] = u0;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CACHE; ++k)
+        if (k < deg)
+            h += uin[k];
     for (int e = beg + CACHE; e < end; ++e)
         h += incoming(e);
 #pragma unroll

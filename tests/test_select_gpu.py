@@ -5,10 +5,12 @@ host, so the test reads them back: a run stopped by max_rounds = t - 1 leaves
 the residuals of the evaluation that round t selects from (bp_get_residuals),
 and the same run with max_rounds = t records round t's frontier. The frontier
 must be the top k of those residuals by (residual desc, id asc): RBP over
-messages, RS over vertex residuals (max over incoming messages). Cases cover
-the compacted and the uncompacted third pass of the 32-bit select (a graph
-with constant potentials has few distinct residuals, so whole slices share a
-digit) and ties that straddle the threshold."""
+messages, RS over vertex residuals (max over incoming messages). Both
+selection paths are checked (one cluster per graph; grid-wide kernels). Cases
+cover the compacted and the uncompacted third pass of the 32-bit cluster
+select (a graph with constant potentials has few distinct residuals, so whole
+slices share a digit), ties that straddle the threshold, and a 1000x1000
+graph (4M messages)."""
 import numpy as np
 import pytest
 
@@ -51,19 +53,15 @@ def _bits(trace_row, count):
     return bits.ravel()[:count].astype(bool)
 
 
-@pytest.mark.parametrize("name", ["grid_batch", "constant", "er"])
-@pytest.mark.parametrize("dtype", ["f32", "q16", "f64"])
-@pytest.mark.parametrize("sched,par", [("rbp", 0.1), ("rbp", 0.001), ("rs", 0.1), ("rs", 0.01)])
-def test_frontier_is_exact_topk(name, dtype, sched, par):
-    prob = _problems()[name]
+def _check(prob, dtype, sched, par, path, ts=(1, 3)):
     gv = prob.graph_var_offsets
     ge = prob.row_ptr[gv]
-    for t in (1, 3):
+    for t in ts:
         with bp.Graph(prob) as g:
-            g.run(sched, par, eps=1e-12, max_rounds=t - 1, msg_dtype=dtype, seed=1)
+            g.run(sched, par, eps=1e-12, max_rounds=t - 1, msg_dtype=dtype, seed=1, select_path=path)
             R = g.residuals()
             st = g.run(sched, par, eps=1e-12, max_rounds=t, msg_dtype=dtype, seed=1, record_trace=1,
-                       trace_capacity=t)
+                       trace_capacity=t, select_path=path)
             tr = g.trace(sched)
         assert st["rounds"] == t
         count = prob.n if sched == "rs" else prob.m
@@ -79,9 +77,23 @@ def test_frontier_is_exact_topk(name, dtype, sched, par):
             if sched == "rbp":
                 k = int(min(max(np.ceil(par * Mg), 1), Mg))
                 want = _topk(R[e0:e1], k)
-                assert np.array_equal(got[e0:e1], want), (name, dtype, sched, par, t, q)
+                assert np.array_equal(got[e0:e1], want), (dtype, sched, par, path, t, q)
             else:
                 vres = vres_all[v0:v1]
                 k = int(min(max(np.ceil(par * Mg), 1), nv))
                 want = _topk(vres, k)
-                assert np.array_equal(got[v0:v1], want), (name, dtype, sched, par, t, q)
+                assert np.array_equal(got[v0:v1], want), (dtype, sched, par, path, t, q)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("name", ["grid_batch", "constant", "er"])
+@pytest.mark.parametrize("dtype", ["f32", "q16", "f64"])
+@pytest.mark.parametrize("sched,par", [("rbp", 0.1), ("rbp", 0.001), ("rs", 0.1), ("rs", 0.01)])
+def test_frontier_is_exact_topk(name, dtype, sched, par, path):
+    _check(_problems()[name], dtype, sched, par, path)
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("sched,par", [("rbp", 0.1), ("rs", 0.1)])
+def test_frontier_is_exact_topk_4m_messages(sched, par, path):
+    _check(synth.ising_grid(1000, 3.0, 0), "f32", sched, par, path, ts=(1, 2))
