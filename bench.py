@@ -36,13 +36,15 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     # the configuration the metric is quoted on: 100x100, beta ~ U[-2.5, 2.5], 50 seeds
+    # (update mapping and selection path tuned per schedule in setup)
     "ising100x100_b2.5_50seeds": dict(
         kind="grid_batch", side=100, beta_max=2.5, lam_max=1.0, n_seeds=50, eps=1e-4, dtype="f32",
-        schedules=[("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.1), ("rs", 0.1)]),
+        schedules=[("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.1), ("rs", 0.1)], autotune="mapping"),
     # 1000x1000, beta ~ U[-3, 3]: one graph of 4M messages, LBP and RnBP
+    # (the same schedules are also run once with BF16 and Q16 storage: dtype_compare)
     "ising1000x1000_b3": dict(
         kind="grid_batch", side=1000, beta_max=3.0, lam_max=1.0, n_seeds=1, eps=1e-4, dtype="f32",
-        schedules=[("lbp", 1.0), ("rnbp", 0.5)]),
+        schedules=[("lbp", 1.0), ("rnbp", 0.5)], dtype_compare=["f32", "bf16", "q16"]),
     # Potts 256x256, k = 32, unary ~ N(0, 1), one shared table I + N(0, 0.3) noise, RnBP 0.5
     "potts256_k32": dict(
         kind="potts", side=256, k=32, eps=1e-4, dtype="f32", schedules=[("rnbp", 0.5)]),
@@ -51,7 +53,7 @@ WORKLOADS = {
     # among 0.1 .. 0.9 in setup; per-graph launches timed on a sample of graphs)
     "er4096_b3": dict(
         kind="er_batch", n_graphs=4096, beta_max=3.0, lam_max=1.0, eps=1e-4, dtype="f32",
-        schedules=[("rnbp", 0.5), ("lbp", 1.0)], autotune=True),
+        schedules=[("rnbp", 0.5), ("lbp", 1.0)], autotune="mapping+p"),
 }
 DEFAULT_WORKLOAD = "ising100x100_b2.5_50seeds"
 L2_FLUSH_BYTES = 512 << 20          # > 126 MB of L2
@@ -109,7 +111,11 @@ def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kern
         for key in phase:
             phase[key] += pr[key]
     achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
-    return ({"bound": "hbm", "kernel": kernel or f"k_eval_bin ({dtype} messages; Eq. 2 + Eq. 4 + reduction)",
+    mappings = sorted({pr.get("kernel_variant", 1) for _, _, _, pr, _ in step})
+    names = {1: "k_eval_bin", 2: "k_eval_bin_tiled", 3: "k_eval_bin", 4: "k_eval_bin_pf<4 edges>",
+             5: "k_eval_bin_pf<8 edges>"}
+    kname = " / ".join(dict.fromkeys(names.get(v, "k_eval_bin") for v in mappings))
+    return ({"bound": "hbm", "kernel": kernel or f"{kname} ({dtype} messages; Eq. 2 + Eq. 4 + reduction)",
              "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_source": peak_src,
              "frac": (achieved / peak) if achieved else None, "traffic": None,
              "launches": eval_launches, "bytes_per_launch": alg_bytes / max(eval_launches, 1),
@@ -143,22 +149,33 @@ def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str)
             "launches": launches, "bytes_per_launch": b / launches, "avg_launch_us": 1e3 * ms / launches}
 
 
-def select_roofline(step, dtype: str, peak: float, peak_src: str):
-    """Roofline of the selection kernels (RBP / RS top-k, RnBP commit) from a
-    profiled step: every residual read once per round (4 B) plus a read and a
-    write of each committed message."""
+def select_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str):
+    """Roofline of the frontier kernels (RBP / RS top-k, RnBP commit) from a
+    profiled step: RBP and RnBP read every residual once per round (4 B) and
+    read and write each committed message (2 s B); RS gathers the residuals of
+    every vertex's incoming messages (rev 4 + residual 4 B per message) and,
+    when its sweeps run inside the selection kernel, moves the splash bytes of
+    sweep_roofline as well."""
     s = MSG_BYTES[dtype]
+    dbar = m / max(n, 1)
     b, ms, launches = 0.0, 0.0, 0
     for sched, p, st, pr, gst in step:
         if sched == "lbp":
             continue
-        b += 4 * pr["full_evals"] + (2 * s * st["committed_updates"] if sched != "rs" else 0)
+        if sched == "rs":
+            b += 8 * pr["full_evals"]
+            if pr["sweep_ms"] == 0:
+                upd = st["committed_updates"]
+                b += upd * (13 + 2 * s + 16 / dbar) + upd * (2 * s + 12 / dbar)
+        else:
+            b += 4 * pr["full_evals"] + 2 * s * st["committed_updates"]
         ms += pr["select_ms"]
         launches += pr["eval_launches"]
     if ms <= 0:
         return None
     a = b / (ms / 1e3) / 1e9
-    return {"bound": "hbm", "kernel": "k_select_rbp / k_select_rs / k_commit_rnbp (frontier selection)",
+    return {"bound": "hbm", "kernel": "k_select_rbp / k_select_rs / k_commit_rnbp (frontier: top-k selection; "
+            "RS: BFS levels and splash sweeps in the same cluster kernel)",
             "achieved": a, "peak": peak, "unit": "GB/s", "peak_source": peak_src, "frac": a / peak,
             "traffic": None, "launches": launches, "bytes_per_launch": b / max(launches, 1),
             "avg_launch_us": 1e3 * ms / max(launches, 1)}
@@ -306,16 +323,16 @@ def main():
     ap.add_argument("--direct-launch", action="store_true",
                     help="timed steps launch kernels directly instead of replaying CUDA graphs "
                          "(profiler passes only)")
-    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
+    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="binary update mapping (0 = library's choice)")
     ap.add_argument("--potts-path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="shared-table update: 0 automatic, 1 CUDA cores, 2 tensor cores BF16, "
                          "3 tensor cores split")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "q16", "f64"],
                     help="message storage (default: the workload's)")
-    ap.add_argument("--autotune", type=int, default=None, choices=[0, 1],
-                    help="tune the update mapping (and RnBP LowP per size class) in setup "
-                         "(default: the workload's setting)")
+    ap.add_argument("--autotune", default=None, choices=["none", "mapping", "mapping+p"],
+                    help="tune the update mapping and selection path (and the RnBP LowP per graph-size "
+                         "class) in setup (default: the workload's setting)")
     args = ap.parse_args()
     global ROUNDS_SCALE
     ROUNDS_SCALE = args.rounds_scale
@@ -365,15 +382,21 @@ def main():
         return out
 
     tuning = None
-    if (wl.get("autotune", False) if args.autotune is None else bool(args.autotune)) and prob.k == 2:
-        # setup, untimed: mapping per schedule (size class of this batch), then
-        # RnBP LowP per graph-size class
+    tune = wl.get("autotune", "none") if args.autotune is None else args.autotune
+    if args.kernel_variant != 0:
+        tune = "none"
+    if tune != "none" and prob.k == 2:
+        # setup, untimed: mapping and selection path per schedule (size class of
+        # this batch), then (mapping+p) the RnBP LowP per graph-size class
         tuning = {"mapping": {}}
         for sched, p in wl["schedules"]:
             r = bp.bp_autotune(g.handle, sched, p, wl["eps"], opts(), 16)
             tuning["mapping"][sched] = {"kernel_variant": r["kernel_variant"],
                                         "ms_per_round": [round(x, 4) for x in r["ms_per_round"]]}
-        if any(sched == "rnbp" for sched, _ in wl["schedules"]):
+            if sched in ("rbp", "rs"):
+                tuning["mapping"][sched]["select_path"] = r["select_path"]
+                tuning["mapping"][sched]["ms_per_round_select"] = [round(x, 4) for x in r["ms_per_round_select"]]
+        if tune == "mapping+p" and any(sched == "rnbp" for sched, _ in wl["schedules"]):
             cand = [0.1, 0.3, 0.5, 0.7, 0.9]
             gp = bp.bp_autotune_parallelism(g.handle, "rnbp", cand, wl["eps"], 1000, opts())
             sizes = np.diff(prob.graph_var_offsets)
@@ -455,7 +478,7 @@ def main():
         # the dominant kernel class of the step gets the roofline
         cands = [(phase["eval_ms"], update_roofline),
                  (phase["sweep_ms"], sweep_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src)),
-                 (phase["select_ms"], select_roofline(prof_step, wl["dtype"], peak, peak_src))]
+                 (phase["select_ms"], select_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src))]
         roofline = max((c for c in cands if c[1] is not None), key=lambda c: c[0])[1]
     per_sched = {}
     for step in results:
@@ -471,6 +494,24 @@ def main():
         d["batch_ms"] = float(np.median(d.pop("ms")))
         d["committed_updates"] //= args.steps
         d["graphs_per_s"] = G / (d["batch_ms"] / 1e3)
+
+    # storage formats side by side: each schedule once per format, from
+    # uniform messages to convergence or the round cap
+    dtype_cmp = None
+    if wl.get("dtype_compare") and rank == 0:
+        dtype_cmp = {}
+        for dt in wl["dtype_compare"]:
+            for sched, p in wl["schedules"]:
+                o = bp.bp_default_options(msg_dtype=dt, cuda_stream=stream.cuda_stream)
+                bp.bp_run(g.handle, sched, p, wl["eps"], round_cap(sched, p), o)   # warm-up
+                flush.zero_()
+                st = bp.bp_run(g.handle, sched, p, wl["eps"], round_cap(sched, p), o)
+                gst = bp.bp_get_graph_stats(g.handle)
+                dtype_cmp[f"{sched}_p{p}_{dt}"] = {
+                    "ms": st["device_ms"], "rounds": st["rounds"],
+                    "ms_per_round": st["device_ms"] / max(st["rounds"], 1),
+                    "converged_fraction": float(np.mean([x["converged"] for x in gst])),
+                    "updates_per_s": st["committed_updates"] / (st["device_ms"] / 1e3)}
 
     # batches: the same graphs launched one handle per graph, on a sample of
     # 64 graphs spread over the batch (per-graph launches vs the batched run)
@@ -531,7 +572,7 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
-            "config": {"workload": args.workload, "graphs_per_gpu": G,
+            "config": {"workload": args.workload, "graphs_per_gpu": G, "autotune": tune,
                        "rounds_scale": args.rounds_scale, "direct_launch": bool(args.direct_launch),
                        "vertices": int(prob.n), "directed_messages": int(prob.m), "states": int(prob.k),
                        "potts_path": args.potts_path,
@@ -540,7 +581,7 @@ def main():
                        "parallelism": f"dp{world}" if world > 1 else "single"},
             "candidate_evals_per_s": evals / (total_ms / 1e3),
             "schedules": per_sched,
-            "per_graph_launches": per_graph, "tuning": tuning,
+            "per_graph_launches": per_graph, "tuning": tuning, "dtype_compare": dtype_cmp,
             "profiled_step_phase_ms": phase,
             "roofline": roofline, "update_kernel_roofline": update_roofline,
             "e2e": e2e, "cpu_baseline": cpu,

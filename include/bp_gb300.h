@@ -151,6 +151,7 @@ typedef struct {
     int64_t sweep_launches;    /* fused sweep-step launches (binary RS), counted with sweep_ms */
     int32_t select_ctas[2];    /* RBP, RS selection of the run: CTAs per graph of the cluster
                                   kernels (0 when the grid-wide kernels ran; always filled) */
+    int32_t kernel_variant;    /* the binary update mapping the run used (always filled) */
 } bp_profile;
 
 /* Fills *opt with the defaults listed above. */
@@ -164,6 +165,10 @@ typedef struct {
                                   floor(log2(n_graphs)) (9-13), largest vertex degree
                                   <= 4 / <= 8 / more (14-15) */
     double ms_per_round[6];    /* measured device ms per round, index = mapping; 0 = not tried */
+    int32_t select_path;       /* RBP / RS: the faster selection path measured (1 cluster, 2
+                                  grid-wide; bp_options.select_path), 0 for other schedules */
+    double ms_per_round_select[3]; /* device ms per round with the chosen mapping, index =
+                                  selection path; 0 = not tried */
 } bp_tune_result;
 
 /*
@@ -279,9 +284,10 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
  * graph) it runs bp_run(schedule, parallelism, eps, trial_rounds, opt) twice
  * (the first run captures the rounds; the second is timed by its device_ms)
  * and records the mapping with the least device time per round in a
- * process-wide table under the size class (see bp_tune_result). Later runs
- * with kernel_variant = 0 on any handle of that size class, schedule and
- * msg_dtype use it. Every mapping gives the same results, so tuning changes
+ * process-wide table under the size class (see bp_tune_result); for RBP and
+ * RS it then times both selection paths with that mapping and records the
+ * faster. Later runs with kernel_variant = 0 (select_path = 0) on any handle
+ * of that size class, schedule and msg_dtype use them. Every mapping gives the same results, so tuning changes
  * speed only. The trial runs leave no result (bp_get_beliefs fails with
  * BP_ERR_NO_RESULT until the next bp_run). Binary Ising handles only
  * (BP_ERR_UNSUPPORTED otherwise); trial_rounds >= 1; errors of bp_run pass

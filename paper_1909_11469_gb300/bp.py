@@ -68,7 +68,8 @@ class bp_profile(ctypes.Structure):
                 ("eval_ms", ctypes.c_double), ("decide_ms", ctypes.c_double),
                 ("frontier_ms", ctypes.c_double), ("batch_kernel_ms", ctypes.c_double),
                 ("select_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double),
-                ("sweep_launches", ctypes.c_int64), ("select_ctas", ctypes.c_int32 * 2)]
+                ("sweep_launches", ctypes.c_int64), ("select_ctas", ctypes.c_int32 * 2),
+                ("kernel_variant", ctypes.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -78,11 +79,13 @@ class bp_profile(ctypes.Structure):
 
 class bp_tune_result(ctypes.Structure):
     _fields_ = [("kernel_variant", ctypes.c_int32), ("size_class", ctypes.c_int32),
-                ("ms_per_round", ctypes.c_double * 6)]
+                ("ms_per_round", ctypes.c_double * 6), ("select_path", ctypes.c_int32),
+                ("ms_per_round_select", ctypes.c_double * 3)]
 
     def as_dict(self):
         return {"kernel_variant": self.kernel_variant, "size_class": self.size_class,
-                "ms_per_round": list(self.ms_per_round)}
+                "ms_per_round": list(self.ms_per_round), "select_path": self.select_path,
+                "ms_per_round_select": list(self.ms_per_round_select)}
 
 
 _P = ctypes.c_void_p

@@ -188,7 +188,8 @@ uint32_t size_class(const bp_graph *g, int schedule, int dtype)
 // Binary update mapping of a run: the requested one, else the tuned one of the
 // handle's size class, else thread per vertex with prefetched gathers for
 // graphs of degree <= 4 (every vertex's edges held in registers) and the plain
-// thread-per-vertex form otherwise.
+// thread-per-vertex form otherwise. Table values: mapping in bits 0-7, tuned
+// selection path in bits 8-15.
 int32_t resolve_variant(const bp_graph *g, int schedule, int dtype, int32_t requested)
 {
     if (requested != 0)
@@ -197,9 +198,20 @@ int32_t resolve_variant(const bp_graph *g, int schedule, int dtype, int32_t requ
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_table.find(size_class(g, schedule, dtype));
         if (it != g_tune_table.end())
-            return it->second;
+            return it->second & 0xff;
     }
-    return g->max_deg <= 4 ? 4 : 1;
+    return (g->max_deg <= 4 && dtype != DT_F64) ? 4 : 1;
+}
+
+// Selection path of a run: the requested one, else the tuned one of the
+// handle's size class (0 when none: the planner's estimate decides).
+int32_t resolve_select_path(const bp_graph *g, int schedule, int dtype, int32_t requested)
+{
+    if (requested != 0)
+        return requested;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_table.find(size_class(g, schedule, dtype));
+    return it != g_tune_table.end() ? (it->second >> 8) & 0xff : 0;
 }
 
 DevGraph dev_graph(const bp_graph *g)
@@ -791,8 +803,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "potts_path must be 0..3");
     if (opt.select_path < 0 || opt.select_path > 2)
         return fail(BP_ERR_INVALID_ARG, "select_path must be 0..2");
-    if (opt.kernel_variant < 0 || opt.kernel_variant > 5)
-        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 5]");
+    if (opt.kernel_variant < 0 || opt.kernel_variant > 6)
+        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 6]");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
         return fail(BP_ERR_INVALID_ARG, "splash_depth must be in [0, 16]");
     if (opt.record_trace && opt.trace_capacity < 0)
@@ -854,10 +866,11 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
 
     cudaStream_t s = (cudaStream_t)opt.cuda_stream;
     if ((schedule == BP_RBP || schedule == BP_RS) &&
-        (!g->sel_planned[dtype] || (opt.select_path == 2 && !g->d_gsel))) {
+        (!g->sel_planned[dtype] || (resolve_select_path(g, schedule, dtype, opt.select_path) == 2 && !g->d_gsel))) {
         int32_t c[2], dyn[2], grid[2];
         plan_select(dtype, g->G, g->max_graph_edges, g->max_graph_vertices, c, dyn, grid);
-        if ((grid[0] || grid[1] || opt.select_path == 2) && !g->d_gsel) {
+        if ((grid[0] || grid[1] || resolve_select_path(g, schedule, dtype, opt.select_path) == 2) &&
+            !g->d_gsel) {
             // buffers of the grid-wide selection, kept until the handle is destroyed
             std::vector<int32_t> co(2 * ((size_t)g->G + 1));
             g->n_chunks_rbp = grid_select_chunks(g->h_ge_off.data(), g->G, co.data());
@@ -882,9 +895,10 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     }
     DevGraph dg = dev_graph(g);
     {
+        const int32_t sp = resolve_select_path(g, schedule, dtype, opt.select_path);
         int bits = g->sel_planned[dtype] ? (g->sel_plan[dtype][2] | (g->sel_plan[dtype][5] << 1)) : 0;
-        if (opt.select_path != 0)
-            bits = opt.select_path == 2 ? 3 : 0;
+        if (sp != 0)
+            bits = sp == 2 ? 3 : 0;
         if (!g->d_gsel)
             bits = 0;
         apply_select_plan(g, dtype, bits, dg);
@@ -1053,6 +1067,7 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     }
     for (int w = 0; w < 2; ++w)
         prof.select_ctas[w] = (dg.sel_grid[w] && dr.gsel) ? 0 : dg.sel_c[w];
+    prof.kernel_variant = variant;
     g->last_profile = prof;
     g->has_result = true;
     g->res_dtype = dtype;
@@ -1213,12 +1228,35 @@ int bp_autotune(bp_graph *g, int32_t schedule, double parallelism, double eps, c
             best_v = cand[c];
         }
     }
+    // RBP and RS: the selection path (cluster kernels or grid-wide kernels)
+    // with the chosen mapping
+    int32_t best_sp = 0;
+    if (schedule == BP_RBP || schedule == BP_RS) {
+        double best_s = std::numeric_limits<double>::infinity();
+        o.kernel_variant = best_v;
+        for (int32_t sp = 1; sp <= 2; ++sp) {
+            o.select_path = sp;
+            bp_run_stats st;
+            int rc = bp_run(g, schedule, parallelism, eps, trial_rounds, &o, &st);
+            if (rc != BP_OK)
+                return rc;
+            if ((rc = bp_run(g, schedule, parallelism, eps, trial_rounds, &o, &st)) != BP_OK)
+                return rc;
+            const double ms = st.device_ms / (double)std::max(st.rounds, 1);
+            out->ms_per_round_select[sp] = ms;
+            if (ms < best_s) {
+                best_s = ms;
+                best_sp = sp;
+            }
+        }
+    }
     const uint32_t key = size_class(g, schedule, o.msg_dtype);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_table[key] = best_v;
+        g_tune_table[key] = best_v | (best_sp << 8);
     }
     out->kernel_variant = best_v;
+    out->select_path = best_sp;
     out->size_class = (int32_t)key;
     g->has_result = false;   // the trial runs leave no result to read
     return BP_OK;

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
 // The same mapping with the prefetching vertex routine (eval_vertex_bin_pf):
 // graph arrays and the graph's status load in parallel. MINB = resident
 // blocks per SM the register budget is fitted to.
-template <typename S, int MODE, int CACHE, int MINB>
+template <typename S, int MODE, int CACHE, int MINB, bool NC = false>
 __global__ void __launch_bounds__(BLOCK, MINB) k_eval_bin_pf(DevGraph g, DevRun dr, RunParams rp)
 {
     using A = typename Store<S>::A;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_eval_bin_pf(DevGraph g, DevRun 
     unsigned int cnt = 0;
     if (i < g.n) {
         gg = g.gid[i];
-        valid = eval_vertex_bin_pf<S, MODE == MODE_CAND, CACHE>(g, dr, (RT *)dr.resid, i, gg,
+        valid = eval_vertex_bin_pf<S, MODE == MODE_CAND, CACHE, NC>(g, dr, (RT *)dr.resid, i, gg,
                                                                  eps_in(rp, (A)0), maxa, cnt);
     }
     reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
@@ -911,9 +911,11 @@ static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams
     if (rp.variant >= 4) {
         if (mode == MODE_LBP) {
             if (rp.variant == 4) k_eval_bin_pf<S, MODE_LBP, 4, 6><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+            else if (rp.variant == 6) k_eval_bin_pf<S, MODE_LBP, 4, 5, true><<<nb, BLOCK, 0, s>>>(g, dr, rp);
             else k_eval_bin_pf<S, MODE_LBP, 8, 4><<<nb, BLOCK, 0, s>>>(g, dr, rp);
         } else {
             if (rp.variant == 4) k_eval_bin_pf<S, MODE_CAND, 4, 6><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+            else if (rp.variant == 6) k_eval_bin_pf<S, MODE_CAND, 4, 5, true><<<nb, BLOCK, 0, s>>>(g, dr, rp);
             else k_eval_bin_pf<S, MODE_CAND, 8, 4><<<nb, BLOCK, 0, s>>>(g, dr, rp);
         }
         return;

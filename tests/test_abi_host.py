@@ -46,8 +46,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bp_options), sizeof(bp_run_stats),
          offsetof(bp_options, cuda_stream), offsetof(bp_options, kernel_variant),
          offsetof(bp_run_stats, device_ms), offsetof(bp_run_stats, status),
-         sizeof(bp_profile), offsetof(bp_profile, sweep_launches),
-         sizeof(bp_tune_result), offsetof(bp_tune_result, ms_per_round));
+         sizeof(bp_profile), offsetof(bp_profile, kernel_variant),
+         sizeof(bp_tune_result), offsetof(bp_tune_result, ms_per_round_select));
   return 0;
 }
 """)
@@ -57,8 +57,8 @@ int main(void) {
     assert vals == [ctypes.sizeof(bp.bp_options), ctypes.sizeof(bp.bp_run_stats),
                     bp.bp_options.cuda_stream.offset, bp.bp_options.kernel_variant.offset,
                     bp.bp_run_stats.device_ms.offset, bp.bp_run_stats.status.offset,
-                    ctypes.sizeof(bp.bp_profile), bp.bp_profile.sweep_launches.offset,
-                    ctypes.sizeof(bp.bp_tune_result), bp.bp_tune_result.ms_per_round.offset]
+                    ctypes.sizeof(bp.bp_profile), bp.bp_profile.kernel_variant.offset,
+                    ctypes.sizeof(bp.bp_tune_result), bp.bp_tune_result.ms_per_round_select.offset]
 
 
 def test_status_strings(L):

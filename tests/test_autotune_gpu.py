@@ -5,8 +5,8 @@
   mappings compute the same bits, so only the speed changes).
 * bp_set_graph_parallelism gives each graph of a batch its own p: with FP64
   messages each graph replays the oracle run of that graph alone at its p
-  exactly (same frontiers, rounds, commits; beliefs to 1e-9 on graphs whose
-  run contracts, beta <= 0.6).
+  exactly (same frontiers, rounds, commits; beliefs to 1e-9 on the graphs that
+  converge, beta <= 0.6).
 * bp_autotune_parallelism picks per size class the candidate whose graphs
   converge in the fewest rounds; the test recomputes the scores from plain
   runs and checks the choice."""
@@ -52,6 +52,7 @@ def test_graph_parallelism_replays_each_graph(sched):
     prob = synth.er_batch(6, 11, n_max=400, beta_max=0.6)
     ps = np.array([0.15, 0.3, 0.5, 0.7, 0.9, 0.4])
     cap = 3000
+    n_conv = 0
     with bp.Graph(prob) as g:
         g.set_graph_parallelism(ps)
         g.run(sched, 0.99, eps=1e-6, max_rounds=cap, msg_dtype="f64", seed=4)
@@ -61,9 +62,11 @@ def test_graph_parallelism_replays_each_graph(sched):
         ref = oracle.run(prob.graph(q), sched, parallelism=ps[q], eps=1e-6, max_rounds=cap, seed=4, graph_id=q)
         assert (gst[q]["converged"], gst[q]["rounds"], gst[q]["committed_updates"]) == \
             (int(ref["converged"]), ref["rounds"], ref["committed_updates"]), q
-        assert ref["converged"], q
-        v0, v1 = prob.graph_var_offsets[q], prob.graph_var_offsets[q + 1]
-        assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < 1e-9, q
+        if ref["converged"]:
+            v0, v1 = prob.graph_var_offsets[q], prob.graph_var_offsets[q + 1]
+            assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < 1e-9, q
+            n_conv += 1
+    assert n_conv >= 3
     # the per-graph values matter: graphs with different p take different round counts
     assert len({x["rounds"] for x in gst}) > 1
 
@@ -102,3 +105,20 @@ def test_autotune_parallelism_choice():
         best = min(cand, key=lambda c: (scores[(cls[q], c)], cand.index(c)))
         assert chosen[q] == best, (q, cls[q], chosen[q], best)
     print("chosen p per size class:", {int(k): float(chosen[np.argmax(cls == k)]) for k in np.unique(cls)})
+
+
+def test_autotune_selection_path():
+    prob = synth.ising_grid_batch(60, 2.5, range(12))
+    with bp.Graph(prob) as g:
+        r = g.autotune("rbp", 0.1, eps=1e-4, trial_rounds=8)
+        ms = r["ms_per_round_select"]
+        assert ms[1] > 0 and ms[2] > 0
+        assert r["select_path"] == (1 if ms[1] <= ms[2] else 2)
+        st = g.run("rbp", 0.1, eps=1e-4, max_rounds=30, seed=0)
+        b = g.beliefs()
+        ctas = g.profile()["select_ctas"][0]   # the tuned path is the one that ran
+        assert (ctas == 0) == (r["select_path"] == 2)
+        other = 2 if r["select_path"] == 1 else 1
+        st2 = g.run("rbp", 0.1, eps=1e-4, max_rounds=30, seed=0, select_path=other)
+        assert (st["rounds"], st["committed_updates"]) == (st2["rounds"], st2["committed_updates"])
+        assert np.array_equal(b, g.beliefs())
