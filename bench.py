@@ -323,7 +323,7 @@ def main():
     ap.add_argument("--direct-launch", action="store_true",
                     help="timed steps launch kernels directly instead of replaying CUDA graphs "
                          "(profiler passes only)")
-    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
+    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="binary update mapping (0 = library's choice)")
     ap.add_argument("--potts-path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="shared-table update: 0 automatic, 1 CUDA cores, 2 tensor cores BF16, "

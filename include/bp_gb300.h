@@ -108,7 +108,8 @@ typedef struct {
     int32_t kernel_variant;   /* binary Ising update mapping (every mapping computes the
                                  same bits): 0 = automatic (the choice bp_autotune
                                  recorded for the handle's size class, else 4 when no
-                                 vertex has more than 4 edges and 1 otherwise), 1 =
+                                 vertex has more than 4 edges and messages are not FP64,
+                                 and 1 otherwise), 1 =
                                  per-round kernels, one thread per vertex, 2 = per-round,
                                  256-vertex tiles with 4-edge quads, 3 = persistent batch
                                  kernel: one thread-block cluster per graph runs all of

@@ -803,8 +803,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "potts_path must be 0..3");
     if (opt.select_path < 0 || opt.select_path > 2)
         return fail(BP_ERR_INVALID_ARG, "select_path must be 0..2");
-    if (opt.kernel_variant < 0 || opt.kernel_variant > 6)
-        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 6]");
+    if (opt.kernel_variant < 0 || opt.kernel_variant > 5)
+        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 5]");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
         return fail(BP_ERR_INVALID_ARG, "splash_depth must be in [0, 16]");
     if (opt.record_trace && opt.trace_capacity < 0)
@@ -937,8 +937,11 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         int64_t rounds_launched = 0;
         // Each replay runs `chunk` rounds (evaluations); graphs that finish turn the
         // rest of their kernels into no-ops. The host polls the running count once
-        // per replay.
+        // per replay. Automatic chunks double up to max_chunk and never run past
+        // the max_rounds + 1 evaluations a graph can need.
         for (;;) {
+            if (opt.rounds_per_launch <= 0)
+                chunk = (int)std::max<int64_t>(1, std::min<int64_t>(chunk, (int64_t)max_rounds + 1 - rounds_launched));
             if (opt.profile) {
                 // direct launches with events between the phases of every round
                 if (g->prof_events.size() < (size_t)chunk * 5) {

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
 // The same mapping with the prefetching vertex routine (eval_vertex_bin_pf):
 // graph arrays and the graph's status load in parallel. MINB = resident
 // blocks per SM the register budget is fitted to.
-template <typename S, int MODE, int CACHE, int MINB, bool NC = false>
+template <typename S, int MODE, int CACHE, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_eval_bin_pf(DevGraph g, DevRun dr, RunParams rp)
 {
     using A = typename Store<S>::A;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_eval_bin_pf(DevGraph g, DevRun 
     unsigned int cnt = 0;
     if (i < g.n) {
         gg = g.gid[i];
-        valid = eval_vertex_bin_pf<S, MODE == MODE_CAND, CACHE, NC>(g, dr, (RT *)dr.resid, i, gg,
+        valid = eval_vertex_bin_pf<S, MODE == MODE_CAND, CACHE>(g, dr, (RT *)dr.resid, i, gg,
                                                                  eps_in(rp, (A)0), maxa, cnt);
     }
     reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
@@ -582,6 +582,38 @@ __global__ void __launch_bounds__(TILE_V) k_commit_rnbp_tiled(DevGraph g, DevRun
         add_commit_counts(dr, uniform, g0, valid, gg, c, false);
         return;
     }
+    if (uniform) {
+        // one graph in the tile: its round state once, every residual of the
+        // tile's edges loaded up front (up to TILE_E / TILE_V per thread)
+        const GState st = dr.gs[g0];
+        const bool run = st.status == ST_RUNNING;
+        if (run) {
+            const int ge0 = g.ge_off[g0];
+            const bool tr = rp.record_trace && st.rounds <= rp.trace_capacity;
+            constexpr int J = (TILE_E + TILE_V - 1) / TILE_V;
+            RT r[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int t = vl + j * TILE_V;
+                r[j] = t < ne ? R[e0 + t] : (RT)0;
+            }
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int t = vl + j * TILE_V;
+                const int e = e0 + t;
+                if (t < ne && r[j] >= eps_in(rp, (RT)0) &&
+                    rnbp_pick(rp, (uint32_t)(e - ge0), (uint32_t)st.rounds, (uint32_t)g0, st)) {
+                    for (int x = 0; x < epm; ++x)
+                        dst[(size_t)e * epm + x] = src[(size_t)e * epm + x];
+                    ++c;
+                    if (tr)
+                        atomicOr(&dr.trace[(size_t)(st.rounds - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
+                }
+            }
+        }
+        add_commit_counts(dr, true, g0, run, g0, c, false);
+        return;
+    }
     if (vl < nv) {
         const int gg = g.gid[v];
         s_g[vl] = dr.gs[gg].status == ST_RUNNING ? gg : -1;
@@ -911,11 +943,9 @@ static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams
     if (rp.variant >= 4) {
         if (mode == MODE_LBP) {
             if (rp.variant == 4) k_eval_bin_pf<S, MODE_LBP, 4, 6><<<nb, BLOCK, 0, s>>>(g, dr, rp);
-            else if (rp.variant == 6) k_eval_bin_pf<S, MODE_LBP, 4, 5, true><<<nb, BLOCK, 0, s>>>(g, dr, rp);
             else k_eval_bin_pf<S, MODE_LBP, 8, 4><<<nb, BLOCK, 0, s>>>(g, dr, rp);
         } else {
             if (rp.variant == 4) k_eval_bin_pf<S, MODE_CAND, 4, 6><<<nb, BLOCK, 0, s>>>(g, dr, rp);
-            else if (rp.variant == 6) k_eval_bin_pf<S, MODE_CAND, 4, 5, true><<<nb, BLOCK, 0, s>>>(g, dr, rp);
             else k_eval_bin_pf<S, MODE_CAND, 8, 4><<<nb, BLOCK, 0, s>>>(g, dr, rp);
         }
         return;

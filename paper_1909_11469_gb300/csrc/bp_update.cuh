@@ -63,7 +63,7 @@ __device__ __forceinline__ void eval_vertex_bin(const DevGraph &g, const S *cur,
 // rev, q) are read before the graph's run status is known, so the message
 // gathers wait on one level of loads instead of three. gg = graph of vertex i.
 // Returns false (and touches nothing) when the graph is not running.
-template <typename S, bool STORE_R, int CACHE, bool NC = false>
+template <typename S, bool STORE_R, int CACHE>
 __device__ __forceinline__ bool eval_vertex_bin_pf(const DevGraph &g, const DevRun &dr,
                                                    typename ResidT<S>::T *R, int i, int gg,
                                                    typename Store<S>::A eps_a,
@@ -71,16 +71,15 @@ __device__ __forceinline__ bool eval_vertex_bin_pf(const DevGraph &g, const DevR
 {
     using A = typename Store<S>::A;
     using RT = typename ResidT<S>::T;
-    const int beg = NC ? __ldg(g.row_ptr + i) : g.row_ptr[i];
-    const int end = NC ? __ldg(g.row_ptr + i + 1) : g.row_ptr[i + 1];
+    const int beg = g.row_ptr[i], end = g.row_ptr[i + 1];
     const int deg = end - beg;
     A h;
     const A *q;
     if constexpr (sizeof(A) == 8) {
-        h = NC ? __ldg(g.udiff64 + i) : g.udiff64[i];
+        h = g.udiff64[i];
         q = (const A *)g.q64;
     } else {
-        h = NC ? __ldg(g.udiff32 + i) : g.udiff32[i];
+        h = g.udiff32[i];
         q = (const A *)g.q32;
     }
     int rv[CACHE];
@@ -88,13 +87,8 @@ __device__ __forceinline__ bool eval_vertex_bin_pf(const DevGraph &g, const DevR
 #pragma unroll
     for (int c = 0; c < CACHE; ++c) {
         if (c < deg) {
-            if constexpr (NC) {
-                rv[c] = __ldg(g.rev + beg + c);
-                qv[c] = __ldg(q + beg + c);
-            } else {
-                rv[c] = g.rev[beg + c];
-                qv[c] = q[beg + c];
-            }
+            rv[c] = g.rev[beg + c];
+            qv[c] = q[beg + c];
         }
     }
     const int status = dr.gs[gg].status;
@@ -107,13 +101,8 @@ __device__ __forceinline__ bool eval_vertex_bin_pf(const DevGraph &g, const DevR
 #pragma unroll
     for (int c = 0; c < CACHE; ++c) {
         if (c < deg) {
-            if constexpr (NC) {
-                uin[c] = Store<S>::val(__ldg(cur + rv[c]), g.qscale);
-                old[c] = Store<S>::val(__ldg(cur + beg + c), g.qscale);
-            } else {
-                uin[c] = Store<S>::ld(cur + rv[c], g.qscale);
-                old[c] = Store<S>::ld(cur + beg + c, g.qscale);
-            }
+            uin[c] = Store<S>::ld(cur + rv[c], g.qscale);
+            old[c] = Store<S>::ld(cur + beg + c, g.qscale);
         }
     }
 #pragma unroll
