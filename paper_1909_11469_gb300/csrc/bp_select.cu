@@ -45,12 +45,22 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_rbp(DevGraph g, DevRun d
     const RT *R = (const RT *)dr.resid + e0 + lo;
     KeyT *s_keys = reinterpret_cast<KeyT *>(sel_smem);
     const bool staged = (size_t)nl * sizeof(KeyT) <= (size_t)g.sel_smem_bytes;
-    if (staged)
+    bool pass1 = false;
+    if constexpr (sizeof(KeyT) == 4) {
+        if (staged) {
+            // the first radix pass rides on the staging loop
+            sel32_clear(sh);
+            __syncthreads();
+            stage_keys_hist(nl, s_keys, [&](int idx) { return key_bits(R[idx]); }, sh.hist1);
+            pass1 = true;
+        }
+    }
+    if (staged && !pass1)
         stage_keys<KeyT>(nl, s_keys, [&](int idx) { return key_bits(R[idx]); });
     auto key = [&](int idx) -> KeyT { return staged ? s_keys[idx] : key_bits(R[idx]); };
     KeyT thr;
     int take_eq, eq_total;
-    cluster_select_threshold<KeyT>(cl, sh, nl, st.k_sel, key, thr, take_eq, eq_total);
+    cluster_select_threshold<KeyT>(cl, sh, nl, st.k_sel, key, thr, take_eq, eq_total, pass1);
     S *dst = (S *)dr.msg[0];
     const S *src = (const S *)dr.msg[1];
     const int epm = g.epm;
@@ -99,7 +109,15 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun
     KeyT *vkeys = staged ? reinterpret_cast<KeyT *>(sel_smem) : reinterpret_cast<KeyT *>(dr.vres) + v0 + lo;
     const RT *R = (const RT *)dr.resid;
     constexpr int U = 4;
-    for (int base = threadIdx.x; base < nl; base += U * blockDim.x) {
+    // 32-bit keys: the first radix pass rides on this loop (uniform bounds:
+    // every warp calls hist_add with all lanes)
+    constexpr bool fuse1 = sizeof(KeyT) == 4;
+    if constexpr (fuse1) {
+        sel32_clear(sh);
+        __syncthreads();
+    }
+    for (int b0 = 0; b0 < nl; b0 += U * blockDim.x) {
+        const int base = b0 + (int)threadIdx.x;
         int rb[U], re[U];
         RT m[U];
 #pragma unroll
@@ -130,13 +148,15 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun
             const int idx = base + u * blockDim.x;
             if (idx < nl)
                 vkeys[idx] = key_bits(m[u]);
+            if constexpr (fuse1)
+                hist_add(sh.hist1, idx < nl ? sel32_digit1(key_bits(m[u])) : 0xffffffffu);
         }
     }
     __syncthreads();
     auto key = [&](int idx) -> KeyT { return vkeys[idx]; };
     KeyT thr;
     int take_eq, eq_total;
-    cluster_select_threshold<KeyT>(cl, sh, nl, st.k_sel, key, thr, take_eq, eq_total);
+    cluster_select_threshold<KeyT>(cl, sh, nl, st.k_sel, key, thr, take_eq, eq_total, fuse1);
     const bool tr = rp.record_trace && st.rounds <= rp.trace_capacity;
     cluster_select_apply<KeyT>(cl, sh, nl, thr, take_eq, eq_total, key, [&](int idx, bool take) {
         const int v = v0 + lo + idx;

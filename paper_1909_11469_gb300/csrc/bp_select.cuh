@@ -140,10 +140,9 @@ __device__ __forceinline__ void cluster_digit(cg::cluster_group &cl, SelShared<u
     __syncthreads();
 }
 
-// 32-bit cluster-wide threshold (see cluster_select_threshold).
-template <typename KeyFn>
-__device__ void cluster_select_threshold32(cg::cluster_group &cl, SelShared<uint32_t> &sh, int n_local, int k,
-                                           KeyFn key, uint32_t &thr, int &take_eq, int &eq_total)
+// Clears the histograms and the candidate count of the 32-bit select (every
+// thread of the CTA calls it; a __syncthreads must follow).
+__device__ __forceinline__ void sel32_clear(SelShared<uint32_t> &sh)
 {
     for (int t = threadIdx.x; t < 2048; t += blockDim.x) {
         sh.hist1[t] = 0u;
@@ -153,11 +152,27 @@ __device__ void cluster_select_threshold32(cg::cluster_group &cl, SelShared<uint
         sh.hist3[t] = 0u;
     if (threadIdx.x == 0)
         sh.n_cand = 0;
-    __syncthreads();
-    // pass 1: bits 31..21
-    for (int base = 0; base < n_local; base += blockDim.x) {
-        const int idx = base + threadIdx.x;
-        hist_add(sh.hist1, idx < n_local ? key(idx) >> 21 : 0xffffffffu);
+}
+
+// Pass-1 digit (key bits 31..21) of a 32-bit key; 0xffffffff = no key.
+__device__ __forceinline__ unsigned sel32_digit1(uint32_t key) { return key >> 21; }
+
+// 32-bit cluster-wide threshold (see cluster_select_threshold). pass1_done:
+// the caller has cleared the histograms (sel32_clear) and already added every
+// key's pass-1 digit to sh.hist1 (while staging the keys).
+template <typename KeyFn>
+__device__ void cluster_select_threshold32(cg::cluster_group &cl, SelShared<uint32_t> &sh, int n_local, int k,
+                                           KeyFn key, uint32_t &thr, int &take_eq, int &eq_total,
+                                           bool pass1_done)
+{
+    if (!pass1_done) {
+        sel32_clear(sh);
+        __syncthreads();
+        // pass 1: bits 31..21
+        for (int base = 0; base < n_local; base += blockDim.x) {
+            const int idx = base + threadIdx.x;
+            hist_add(sh.hist1, idx < n_local ? sel32_digit1(key(idx)) : 0xffffffffu);
+        }
     }
     cl.sync();   // every CTA's first histogram is complete
     cluster_digit<2048>(cl, sh, sh.hist1, k);
@@ -213,10 +228,11 @@ __device__ void cluster_select_threshold32(cg::cluster_group &cl, SelShared<uint
 // must call it.
 template <typename KeyT, typename KeyFn>
 __device__ void cluster_select_threshold(cg::cluster_group &cl, SelShared<KeyT> &sh, int n_local, int k,
-                                         KeyFn key, KeyT &thr, int &take_eq, int &eq_total)
+                                         KeyFn key, KeyT &thr, int &take_eq, int &eq_total,
+                                         bool pass1_done = false)
 {
     if constexpr (sizeof(KeyT) == 4) {
-        cluster_select_threshold32(cl, sh, n_local, k, key, thr, take_eq, eq_total);
+        cluster_select_threshold32(cl, sh, n_local, k, key, thr, take_eq, eq_total, pass1_done);
         return;
     } else {
     const unsigned C = cl.num_blocks();
@@ -351,6 +367,32 @@ __device__ void cluster_select_apply(cg::cluster_group &cl, SelShared<KeyT> &sh,
         }
         __syncthreads();
     }
+}
+
+// Copies n keys into shared memory (eight independent loads in flight per
+// thread) and adds each key's pass-1 digit to hist (whole warps: the loop
+// bounds are the same for every thread).
+template <typename LoadFn>
+__device__ void stage_keys_hist(int n, uint32_t *s_keys, LoadFn load, unsigned int *hist)
+{
+    constexpr int U = 8;
+    for (int b0 = 0; b0 < n; b0 += U * blockDim.x) {
+        uint32_t v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = b0 + threadIdx.x + u * blockDim.x;
+            if (idx < n)
+                v[u] = load(idx);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = b0 + threadIdx.x + u * blockDim.x;
+            if (idx < n)
+                s_keys[idx] = v[u];
+            hist_add(hist, idx < n ? sel32_digit1(v[u]) : 0xffffffffu);
+        }
+    }
+    __syncthreads();
 }
 
 // Copies n keys into shared memory with eight independent loads in flight per
