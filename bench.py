@@ -37,9 +37,14 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     # the configuration the metric is quoted on: 100x100, beta ~ U[-2.5, 2.5], 50 seeds
     # (update mapping and selection path tuned per schedule in setup)
+    # (update mapping and selection path tuned per schedule in setup; beside the
+    # metric, time-to-convergence of the same 50-seed batch at the paper's
+    # C = 2.5, i.e. beta ~ U[-1.25, 1.25], where the schedules converge, for
+    # FP32, BF16 and Q16 storage: ttc_converging)
     "ising100x100_b2.5_50seeds": dict(
         kind="grid_batch", side=100, beta_max=2.5, lam_max=1.0, n_seeds=50, eps=1e-4, dtype="f32",
-        schedules=[("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.1), ("rs", 0.1)], autotune="mapping"),
+        schedules=[("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.1), ("rs", 0.1)], autotune="mapping",
+        ttc_beta=1.25),
     # 1000x1000, beta ~ U[-3, 3]: one graph of 4M messages, LBP and RnBP
     # (the same schedules are also run once with BF16 and Q16 storage: dtype_compare)
     "ising1000x1000_b3": dict(
@@ -62,6 +67,16 @@ L2_FLUSH_BYTES = 512 << 20          # > 126 MB of L2
 # message (s), + residual (4) in the frontier modes; per processed vertex
 # row_ptr, unary log-odds and graph id (12). s = 4 (FP32) or 2 (BF16, Q16).
 MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# message-update kernel from one ncu capture on the workload, with the kernel as
+# it is now (the summaries and commands are in profiles/). Captures are cold
+# (ncu flushes the caches), so they bound the warm traffic from above.
+NCU_UPDATE_TRAFFIC = {
+    # k_eval_bin_pf<float, CAND, 4 edges, 6 blocks/SM>: 29.81 MB + 2.8 KB
+    ("ising100x100_b2.5_50seeds", "f32"): 29.806e6 + 2.8e3,
+    # k_eval_bin_pf<float, LBP, 4 edges, 6 blocks/SM>: 59.97 MB + 1.45 MB
+    ("ising1000x1000_b3", "f32"): 59.973e6 + 1.454e6,
+}
 BYTES_PER_VERTEX = 12
 
 
@@ -473,6 +488,8 @@ def main():
                      3: "k_potts_tc (tcgen05, split BF16 products)"}.get(
                         args.potts_path or (3 if prob.k >= 16 else 0), "k_eval_gen")
         update_roofline, phase = eval_roofline(prof_step, wl["dtype"], peak, peak_src, prob.k, kname)
+        if prob.k == 2 and all(pr.get("kernel_variant") == 4 for _, _, _, pr, _ in prof_step):
+            update_roofline["traffic"] = NCU_UPDATE_TRAFFIC.get((args.workload, wl["dtype"]))
         phase["select_ms"] = sum(pr["select_ms"] for _, _, _, pr, _ in prof_step)
         phase["sweep_ms"] = sum(pr["sweep_ms"] for _, _, _, pr, _ in prof_step)
         # the dominant kernel class of the step gets the roofline
@@ -494,6 +511,26 @@ def main():
         d["batch_ms"] = float(np.median(d.pop("ms")))
         d["committed_updates"] //= args.steps
         d["graphs_per_s"] = G / (d["batch_ms"] / 1e3)
+
+    # time-to-convergence on the converging companion batch (same sizes and
+    # seeds, milder couplings): batch time until every graph converged or hit
+    # its cap, per schedule and storage format
+    ttc = None
+    if wl.get("ttc_beta") and rank == 0:
+        from paper_1909_11469_gb300 import synth
+        mild = synth.ising_grid_batch(wl["side"], wl["ttc_beta"], range(wl["n_seeds"]), wl["lam_max"])
+        ttc = {"beta_max": wl["ttc_beta"], "graphs": mild.n_graphs}
+        with bp.Graph(mild) as h:
+            for dt in ("f32", "bf16", "q16"):
+                for sched, p in wl["schedules"]:
+                    o = bp.bp_default_options(msg_dtype=dt, cuda_stream=stream.cuda_stream)
+                    bp.bp_run(h.handle, sched, p, wl["eps"], round_cap(sched, p), o)   # warm-up
+                    st = bp.bp_run(h.handle, sched, p, wl["eps"], round_cap(sched, p), o)
+                    gst = bp.bp_get_graph_stats(h.handle)
+                    conv = [x["rounds"] for x in gst if x["converged"]]
+                    ttc[f"{sched}_p{p}_{dt}"] = {
+                        "batch_ms": st["device_ms"], "converged_fraction": len(conv) / len(gst),
+                        "median_rounds_converged": float(np.median(conv)) if conv else None}
 
     # storage formats side by side: each schedule once per format, from
     # uniform messages to convergence or the round cap
@@ -582,6 +619,7 @@ def main():
             "candidate_evals_per_s": evals / (total_ms / 1e3),
             "schedules": per_sched,
             "per_graph_launches": per_graph, "tuning": tuning, "dtype_compare": dtype_cmp,
+            "ttc_converging": ttc,
             "profiled_step_phase_ms": phase,
             "roofline": roofline, "update_kernel_roofline": update_roofline,
             "e2e": e2e, "cpu_baseline": cpu,
