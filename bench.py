@@ -115,8 +115,15 @@ def batch_kernel_bytes(sched: str, dtype: str, st: dict, pr: dict) -> float:
     return b
 
 
-def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kernel: str = ""):
-    """Roofline of the per-round message-update kernel from a profiled step."""
+def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kernel: str = "",
+                  isolated=None, n: int = 0, m: int = 0):
+    """Roofline of the per-round message-update kernel. achieved = algorithmic
+    bytes / device time. With isolated = {schedule: ms per launch} (the kernel
+    timed alone by bp_time_update: back-to-back launches between two CUDA
+    events, every graph running) the time is the kernel's own, weighted by the
+    profiled step's launches of each schedule; the profiled step's per-phase
+    events (a pair around every directly launched update, so launch overhead
+    included) give the in_step figure beside it."""
     alg_bytes, eval_ms, eval_launches = 0.0, 0.0, 0
     phase = {"eval_ms": 0.0, "decide_ms": 0.0, "frontier_ms": 0.0}
     for sched, p, st, pr, gst in step:
@@ -130,11 +137,29 @@ def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kern
     names = {1: "k_eval_bin", 2: "k_eval_bin_tiled", 3: "k_eval_bin", 4: "k_eval_bin_pf<4 edges>",
              5: "k_eval_bin_pf<8 edges>"}
     kname = " / ".join(dict.fromkeys(names.get(v, "k_eval_bin") for v in mappings))
-    return ({"bound": "hbm", "kernel": kernel or f"{kname} ({dtype} messages; Eq. 2 + Eq. 4 + reduction)",
-             "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_source": peak_src,
-             "frac": (achieved / peak) if achieved else None, "traffic": None,
-             "launches": eval_launches, "bytes_per_launch": alg_bytes / max(eval_launches, 1),
-             "avg_launch_us": 1e3 * eval_ms / max(eval_launches, 1)}, phase)
+    in_step = {"achieved": achieved, "frac": (achieved / peak) if achieved else None,
+               "avg_launch_us": 1e3 * eval_ms / max(eval_launches, 1)}
+    out = {"bound": "hbm", "kernel": kernel or f"{kname} ({dtype} messages; Eq. 2 + Eq. 4 + reduction)",
+           "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_source": peak_src,
+           "frac": (achieved / peak) if achieved else None, "traffic": None,
+           "launches": eval_launches, "bytes_per_launch": alg_bytes / max(eval_launches, 1),
+           "avg_launch_us": 1e3 * eval_ms / max(eval_launches, 1), "timing": "in-step phase events"}
+    if isolated:
+        b_tot, t_tot, w_tot = 0.0, 0.0, 0
+        for sched, p, st, pr, gst in step:
+            if sched not in isolated or pr["eval_launches"] == 0:
+                continue
+            w = pr["eval_launches"]
+            b_tot += w * (bytes_per_msg(sched, dtype, k) * m + bytes_per_vertex(k) * n)
+            t_tot += w * isolated[sched]
+            w_tot += w
+        if t_tot > 0:
+            a = b_tot / (t_tot / 1e3) / 1e9
+            out.update({"achieved": a, "frac": a / peak, "bytes_per_launch": b_tot / w_tot,
+                        "avg_launch_us": 1e3 * t_tot / w_tot,
+                        "timing": "kernel alone: back-to-back launches between CUDA events (bp_time_update)",
+                        "in_step": in_step})
+    return (out, phase)
 
 
 def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str):
@@ -487,7 +512,14 @@ def main():
             kname = {1: "k_potts_tc (CUDA cores)", 2: "k_potts_tc (tcgen05, BF16 products)",
                      3: "k_potts_tc (tcgen05, split BF16 products)"}.get(
                         args.potts_path or (3 if prob.k >= 16 else 0), "k_eval_gen")
-        update_roofline, phase = eval_roofline(prof_step, wl["dtype"], peak, peak_src, prob.k, kname)
+        iso = {}
+        for sched, p in wl["schedules"]:
+            try:
+                iso[sched] = bp.bp_time_update(g.handle, sched, p, opts(), 30)
+            except bp.BPError:
+                pass
+        update_roofline, phase = eval_roofline(prof_step, wl["dtype"], peak, peak_src, prob.k, kname,
+                                               isolated=iso, n=prob.n, m=prob.m)
         if prob.k == 2 and all(pr.get("kernel_variant") == 4 for _, _, _, pr, _ in prof_step):
             update_roofline["traffic"] = NCU_UPDATE_TRAFFIC.get((args.workload, wl["dtype"]))
         phase["select_ms"] = sum(pr["select_ms"] for _, _, _, pr, _ in prof_step)

@@ -324,6 +324,22 @@ int bp_set_graph_parallelism(bp_graph *g, const double *p);
 int bp_autotune_parallelism(bp_graph *g, int32_t schedule, const double *candidates, int32_t n_candidates,
                             double eps, int32_t max_rounds, const bp_options *opt, double *graph_p_out);
 
+/*
+ * bp_time_update - device time of the message-update kernel (Eq. 2 + Eq. 4 +
+ * convergence reduction) alone, for rooflines: the kernel that bp_run(schedule,
+ * parallelism, opt) would launch every round (same mapping, storage format and
+ * shared-table path) is launched `launches` times back to back on
+ * opt->cuda_stream from uniform messages, between two CUDA events;
+ * *ms_per_launch receives the mean. Every launch evaluates every message of
+ * every graph (no graph stops), so launches do identical work. The handle's
+ * previous result is discarded (bp_get_beliefs fails with BP_ERR_NO_RESULT
+ * until the next bp_run). BP_ERR_UNSUPPORTED for the persistent batch mapping
+ * (3), which has no separate update launch; launches >= 1. The paper has no
+ * counterpart (measurement support).
+ */
+int bp_time_update(bp_graph *g, int32_t schedule, double parallelism, const bp_options *opt, int32_t launches,
+                   double *ms_per_launch);
+
 /* Copies the phase profile of the last bp_run (see bp_profile). */
 int bp_get_profile(const bp_graph *g, bp_profile *out);
 

@@ -104,6 +104,7 @@ _SIGNATURES = {
     "bp_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P, ctypes.c_int32,
                                    _P]),
     "bp_set_graph_parallelism": (ctypes.c_int, [_P, _P]),
+    "bp_time_update": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, _P, ctypes.c_int32, _P]),
     "bp_autotune_parallelism": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_double,
                                                ctypes.c_int32, _P, _P]),
     "bp_lbp_run_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
@@ -285,6 +286,16 @@ def bp_autotune(handle, schedule, parallelism, eps, options: bp_options | None =
                              ctypes.byref(options) if options is not None else None, int(trial_rounds),
                              ctypes.byref(r)), "bp_autotune")
     return r.as_dict()
+
+
+def bp_time_update(handle, schedule, parallelism, options: bp_options | None = None, launches: int = 20) -> float:
+    """Mean device ms of the update kernel over back-to-back launches."""
+    sched = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    ms = ctypes.c_double()
+    _check(lib().bp_time_update(handle, sched, float(parallelism),
+                                ctypes.byref(options) if options is not None else None, int(launches),
+                                ctypes.byref(ms)), "bp_time_update")
+    return ms.value
 
 
 def bp_set_graph_parallelism(handle, p) -> None:

@@ -623,6 +623,44 @@ bool all_finite(const float *p, size_t n)
 
 }  // namespace
 
+// Run parameters of (schedule, parallelism, eps, max_rounds, opt) on handle g
+// with message storage dtype; variant receives the resolved update mapping.
+static int build_run_params(const bp_graph *g, int32_t schedule, double parallelism, double eps, int32_t max_rounds,
+                     const bp_options &opt, int dtype, RunParams &rp, int32_t &variant)
+{
+    memset(&rp, 0, sizeof(rp));
+    rp.schedule = schedule;
+    rp.max_rounds = max_rounds;
+    rp.eps = eps;
+    rp.low_p = schedule == BP_LBP ? 1.0 : parallelism;
+    rp.high_p = opt.high_p;
+    rp.ratio_threshold = opt.ratio_threshold;
+    rp.seed = opt.seed;
+    rp.graph_id_base = opt.graph_id_base;
+    rp.splash_depth = opt.splash_depth;
+    rp.rs_roots_mode = opt.rs_roots_mode;
+    rp.record_trace = (opt.record_trace && opt.trace_capacity > 0 && schedule != BP_LBP) ? 1 : 0;
+    rp.trace_capacity = rp.record_trace ? opt.trace_capacity : 0;
+    const int64_t trace_count = schedule == BP_RS ? g->n : g->M;
+    rp.trace_words = (int32_t)((trace_count + 31) / 32);
+    variant = epm_of(g) == 1 ? resolve_variant(g, schedule, dtype, opt.kernel_variant) : 1;
+    rp.variant = variant == 3 ? 1 : variant;
+    rp.eps_f = float_at_least(eps);
+    // shared-table update in vertex tiles: 0 = per-vertex k-state kernel,
+    // 1 = tiles on CUDA cores, 2 = tiles on tensor cores, 3 = tensor cores split
+    rp.tc_path = 0;
+    if (g->pair_kind == BP_PAIR_SHARED && g->tc_tiles_ok && (dtype == BP_F32 || dtype == BP_BF16)) {
+        if (opt.potts_path >= 1)
+            rp.tc_path = opt.potts_path;
+        else if (g->k >= 16)
+            rp.tc_path = 3;
+    }
+    if (opt.potts_path >= 1 && rp.tc_path == 0)
+        return fail(BP_ERR_UNSUPPORTED, "the tiled shared-table update needs a shared table, FP32/BF16 "
+                                        "storage and vertices with at most 128 out-edges");
+    return BP_OK;
+}
+
 // =========================================================================
 extern "C" {
 
@@ -823,36 +861,9 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     }
 
     RunParams rp;
-    memset(&rp, 0, sizeof(rp));
-    rp.schedule = schedule;
-    rp.max_rounds = max_rounds;
-    rp.eps = eps;
-    rp.low_p = schedule == BP_LBP ? 1.0 : parallelism;
-    rp.high_p = opt.high_p;
-    rp.ratio_threshold = opt.ratio_threshold;
-    rp.seed = opt.seed;
-    rp.graph_id_base = opt.graph_id_base;
-    rp.splash_depth = opt.splash_depth;
-    rp.rs_roots_mode = opt.rs_roots_mode;
-    rp.record_trace = (opt.record_trace && opt.trace_capacity > 0 && schedule != BP_LBP) ? 1 : 0;
-    rp.trace_capacity = rp.record_trace ? opt.trace_capacity : 0;
-    const int64_t trace_count = schedule == BP_RS ? g->n : g->M;
-    rp.trace_words = (int32_t)((trace_count + 31) / 32);
-    const int32_t variant = epm_of(g) == 1 ? resolve_variant(g, schedule, dtype, opt.kernel_variant) : 1;
-    rp.variant = variant == 3 ? 1 : variant;
-    rp.eps_f = float_at_least(eps);
-    // shared-table update in vertex tiles: 0 = per-vertex k-state kernel,
-    // 1 = tiles on CUDA cores, 2 = tiles on tensor cores, 3 = tensor cores split
-    rp.tc_path = 0;
-    if (g->pair_kind == BP_PAIR_SHARED && g->tc_tiles_ok && (dtype == BP_F32 || dtype == BP_BF16)) {
-        if (opt.potts_path >= 1)
-            rp.tc_path = opt.potts_path;
-        else if (g->k >= 16)
-            rp.tc_path = 3;
-    }
-    if (opt.potts_path >= 1 && rp.tc_path == 0)
-        return fail(BP_ERR_UNSUPPORTED, "the tiled shared-table update needs a shared table, FP32/BF16 "
-                                        "storage and vertices with at most 128 out-edges");
+    int32_t variant = 1;
+    if ((rc = build_run_params(g, schedule, parallelism, eps, max_rounds, opt, dtype, rp, variant)) != BP_OK)
+        return rc;
     if (rp.record_trace) {
         size_t words = (size_t)rp.trace_capacity * (size_t)rp.trace_words;
         if (words > g->trace_alloc_words) {
@@ -1318,6 +1329,55 @@ int bp_autotune_parallelism(bp_graph *g, int32_t schedule, const double *candida
     if (graph_p_out)
         memcpy(graph_p_out, p.data(), sizeof(double) * p.size());
     g->has_result = false;
+    return BP_OK;
+}
+
+int bp_time_update(bp_graph *g, int32_t schedule, double parallelism, const bp_options *opt_in, int32_t launches,
+                   double *ms_per_launch)
+{
+    if (!g || !ms_per_launch)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (launches < 1)
+        return fail(BP_ERR_INVALID_ARG, "launches must be >= 1");
+    bp_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        bp_default_options(&opt);
+    opt.profile = 0;
+    opt.record_trace = 0;
+    opt.time_budget_ms = 0.0;
+    // a run stopped after its first evaluation sets up every buffer of this
+    // configuration (and validates the arguments)
+    int rc = bp_run(g, schedule, parallelism, 1e-4, 0, &opt, nullptr);
+    if (rc != BP_OK)
+        return rc;
+    const int dtype = opt.msg_dtype;
+    RunParams rp;
+    int32_t variant = 1;
+    if ((rc = build_run_params(g, schedule, parallelism, 1e-4, 0, opt, dtype, rp, variant)) != BP_OK)
+        return rc;
+    if (epm_of(g) == 1 && variant == 3)
+        return fail(BP_ERR_UNSUPPORTED, "the persistent batch kernel has no separate update launch");
+    cudaStream_t s = (cudaStream_t)opt.cuda_stream;
+    const DevGraph dg = dev_graph(g);
+    const DevRun dr = dev_run(g);
+    const int emode = rp.schedule == SCHED_LBP ? MODE_LBP : MODE_CAND;
+    launch_init(dtype, dg, dr, s);
+    BP_CK(cudaEventRecord(g->ev0, s));
+    for (int32_t l = 0; l < launches; ++l) {
+        if (rp.tc_path)
+            launch_potts_tc(dtype, dg, dr, rp, emode, g->d_tc_tiles, g->n_tc_tiles, rp.tc_path, g->d_err, s);
+        else
+            launch_eval(dtype, dg, dr, rp, emode, 0, g->kp, s);
+    }
+    BP_CK(cudaEventRecord(g->ev1, s));
+    BP_CK(cudaGetLastError());
+    BP_CK(cudaEventSynchronize(g->ev1));
+    float ms = 0.f;
+    BP_CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    *ms_per_launch = (double)ms / launches;
+    g->has_result = false;   // the message state is not a run's result
     return BP_OK;
 }
 

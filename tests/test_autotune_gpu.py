@@ -122,3 +122,17 @@ def test_autotune_selection_path():
         st2 = g.run("rbp", 0.1, eps=1e-4, max_rounds=30, seed=0, select_path=other)
         assert (st["rounds"], st["committed_updates"]) == (st2["rounds"], st2["committed_updates"])
         assert np.array_equal(b, g.beliefs())
+
+
+def test_time_update_kernel_alone():
+    prob = synth.ising_grid_batch(40, 2.5, range(4))
+    with bp.Graph(prob) as g:
+        for sched, p in [("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.1)]:
+            ms = bp.bp_time_update(g.handle, sched, p, bp.bp_default_options(), 10)
+            assert 0.0 < ms < 5.0, (sched, ms)
+        with pytest.raises(bp.BPError):
+            g.beliefs()   # the timing leaves no run result
+        with pytest.raises(bp.BPError):
+            bp.bp_time_update(g.handle, "lbp", 1.0, bp.bp_default_options(kernel_variant=3), 10)
+        g.run("lbp", 1.0, eps=1e-4, max_rounds=5)
+        assert g.beliefs().shape == (prob.n, 2)
