@@ -189,36 +189,33 @@ def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str)
             "launches": launches, "bytes_per_launch": b / launches, "avg_launch_us": 1e3 * ms / launches}
 
 
-def select_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str):
-    """Roofline of the frontier kernels (RBP / RS top-k, RnBP commit) from a
-    profiled step: RBP and RnBP read every residual once per round (4 B) and
-    read and write each committed message (2 s B); RS gathers the residuals of
-    every vertex's incoming messages (rev 4 + residual 4 B per message) and,
-    when its sweeps run inside the selection kernel, moves the splash bytes of
-    sweep_roofline as well."""
+def select_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str, which: str):
+    """Roofline of one frontier kernel from a profiled step (which = "rbp":
+    k_select_rbp, "rs": k_select_rs, "rnbp": k_commit_rnbp_tiled). RBP and
+    RnBP read every residual once per round (4 B) and read and write each
+    committed message (2 s B); the RS selection gathers the residuals of every
+    vertex's incoming messages (rev 4 + residual 4 B per message) and writes
+    the splash levels and level lists (1 + 4 B per vertex)."""
     s = MSG_BYTES[dtype]
-    dbar = m / max(n, 1)
     b, ms, launches = 0.0, 0.0, 0
     for sched, p, st, pr, gst in step:
-        if sched == "lbp":
+        if sched != which:
             continue
         if sched == "rs":
-            b += 8 * pr["full_evals"]
-            if pr["sweep_ms"] == 0:
-                upd = st["committed_updates"]
-                b += upd * (13 + 2 * s + 16 / dbar) + upd * (2 * s + 12 / dbar)
+            b += 8 * pr["full_evals"] + 5 * pr["active_vertices"]
         else:
             b += 4 * pr["full_evals"] + 2 * s * st["committed_updates"]
         ms += pr["select_ms"]
-        launches += pr["eval_launches"]
-    if ms <= 0:
+        launches += max(pr["eval_launches"] - 1, 0)   # the last evaluation selects nothing
+    if ms <= 0 or launches == 0:
         return None
     a = b / (ms / 1e3) / 1e9
-    return {"bound": "hbm", "kernel": "k_select_rbp / k_select_rs / k_commit_rnbp (frontier: top-k selection; "
-            "RS: BFS levels and splash sweeps in the same cluster kernel)",
-            "achieved": a, "peak": peak, "unit": "GB/s", "peak_source": peak_src, "frac": a / peak,
-            "traffic": None, "launches": launches, "bytes_per_launch": b / max(launches, 1),
-            "avg_launch_us": 1e3 * ms / max(launches, 1)}
+    name = {"rbp": "k_select_rbp (cluster radix top-k of the residuals + commit)",
+            "rs": "k_select_rs (vertex residuals, cluster top-k roots, BFS levels, level lists)",
+            "rnbp": "k_commit_rnbp_tiled (eps filter + Philox Bernoulli + commit)"}[which]
+    return {"bound": "hbm", "kernel": f"{name}, {dtype} messages", "achieved": a, "peak": peak, "unit": "GB/s",
+            "peak_source": peak_src, "frac": a / peak, "traffic": None, "launches": launches,
+            "bytes_per_launch": b / launches, "avg_launch_us": 1e3 * ms / launches}
 
 
 def round_cap(sched: str, p: float) -> int:
@@ -525,9 +522,14 @@ def main():
         phase["select_ms"] = sum(pr["select_ms"] for _, _, _, pr, _ in prof_step)
         phase["sweep_ms"] = sum(pr["sweep_ms"] for _, _, _, pr, _ in prof_step)
         # the dominant kernel class of the step gets the roofline
+        # the kernel with the largest share of the profiled step gets the roofline
+        def sel_ms(which):
+            return sum(pr["select_ms"] for sc, _, _, pr, _ in prof_step if sc == which)
         cands = [(phase["eval_ms"], update_roofline),
-                 (phase["sweep_ms"], sweep_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src)),
-                 (phase["select_ms"], select_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src))]
+                 (phase["sweep_ms"], sweep_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src))]
+        for which in ("rbp", "rs", "rnbp"):
+            cands.append((sel_ms(which), select_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src,
+                                                         which)))
         roofline = max((c for c in cands if c[1] is not None), key=lambda c: c[0])[1]
     per_sched = {}
     for step in results:
