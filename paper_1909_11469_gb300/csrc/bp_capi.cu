@@ -112,7 +112,8 @@ struct bp_graph {
     void *d_msg[2] = {nullptr, nullptr};
     void *d_resid = nullptr, *d_vres = nullptr;
     int8_t *d_level = nullptr;
-    int32_t *d_lvl_list = nullptr, *d_lvl_cnt = nullptr;   // Residual Splash level lists (lazy)
+    int2 *d_lvl_list = nullptr;                 // Residual Splash level lists (lazy)
+    int32_t *d_lvl_cnt = nullptr;
     double *d_graph_p = nullptr;   // per-graph parallelism (bp_set_graph_parallelism)
     bool graph_p_set = false;
     int32_t max_deg = 0;           // largest vertex degree (size class, mapping heuristic)

@@ -109,7 +109,8 @@ struct DevRun {
     uint32_t *trace;              // [trace_capacity * trace_words]
     double *beliefs;              // [n*k]
     int32_t *queue;               // [1] next graph for the persistent batch kernel
-    int32_t *lvl_list;            // [(LVL_MAX+1) * n] Residual Splash vertices of each level
+    int2 *lvl_list;               // [(LVL_MAX+1) * n] Residual Splash vertices of each level:
+                                  // (vertex, its first out-edge)
     int32_t *lvl_cnt;             // [LVL_MAX+1] entries of each level list
     const double *graph_p;        // [G] per-graph parallelism, or null: every graph uses rp.low_p
     // grid-wide selection (large graphs; null when unused)

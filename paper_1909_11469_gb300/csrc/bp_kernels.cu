@@ -765,7 +765,7 @@ __global__ void __launch_bounds__(BLOCK) k_bfs_level_lists(DevGraph g, DevRun dr
             int before = s_base[L];
             for (unsigned w = 0; w < warp; ++w)
                 before += s_wcnt[L][w];
-            dr.lvl_list[(size_t)L * g.n + before + __popc(mask & ((1u << lane) - 1u))] = i;
+            dr.lvl_list[(size_t)L * g.n + before + __popc(mask & ((1u << lane) - 1u))] = make_int2(i, g.row_ptr[i]);
         }
     }
     add_commit_counts(dr, uniform, g0, lv >= 0, gg, c, true);
@@ -779,13 +779,16 @@ __global__ void __launch_bounds__(BLOCK, 6) k_splash_list_step(DevGraph g, DevRu
 {
     const int nc = Lc >= 0 ? dr.lvl_cnt[Lc] : 0;
     const int ne = Le >= 0 ? dr.lvl_cnt[Le] : 0;
-    const int *lc = dr.lvl_list + (size_t)(Lc >= 0 ? Lc : 0) * g.n;
-    const int *le = dr.lvl_list + (size_t)(Le >= 0 ? Le : 0) * g.n;
+    const int2 *lc = dr.lvl_list + (size_t)(Lc >= 0 ? Lc : 0) * g.n;
+    const int2 *le = dr.lvl_list + (size_t)(Le >= 0 ? Le : 0) * g.n;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc + ne; t += gridDim.x * blockDim.x) {
-        if (t < nc)
-            splash_commit_vertex<S>(g, dr, lc[t]);
-        else
-            splash_eval_vertex<S, 4>(g, dr, le[t - nc], Lc);
+        if (t < nc) {
+            const int2 vb = lc[t];
+            splash_commit_vertex_b<S>(g, dr, vb.x, vb.y);
+        } else {
+            const int2 vb = le[t - nc];
+            splash_eval_vertex_b<S, 4>(g, dr, vb.x, vb.y, Lc);
+        }
     }
 }
 

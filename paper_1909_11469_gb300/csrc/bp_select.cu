@@ -214,8 +214,10 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun
                     wpos = atomicAdd(&s_cnt[L], __popc(m));
                 wpos = __shfl_sync(0xffffffffu, wpos, 0);
                 if (lv == L) {
-                    dr.lvl_list[(size_t)L * g.n + s_base[L] + wpos + __popc(m & ((1u << lane) - 1u))] = v;
-                    c += (unsigned long long)(g.row_ptr[v + 1] - g.row_ptr[v]) * (L == 0 ? 1u : 2u);
+                    const int beg = g.row_ptr[v];
+                    dr.lvl_list[(size_t)L * g.n + s_base[L] + wpos + __popc(m & ((1u << lane) - 1u))] =
+                        make_int2(v, beg);
+                    c += (unsigned long long)(g.row_ptr[v + 1] - beg) * (L == 0 ? 1u : 2u);
                 }
             }
         }

@@ -205,6 +205,89 @@ __device__ __forceinline__ void splash_eval_vertex(const DevGraph &g, const DevR
         Store<S>::st(b1 + e, ising_logodds(q[e], h - incoming(e)), g.qscale);
 }
 
+// The same commit and evaluation for a list entry that carries the vertex's
+// first out-edge beg: the first out-edges' graph arrays (and, for the commit,
+// the candidates) load next to row_ptr[i + 1] instead of after it. Loads
+// past the vertex's last edge stay inside the arrays (index < M) and are not
+// used.
+template <typename S>
+__device__ __forceinline__ unsigned int splash_commit_vertex_b(const DevGraph &g, const DevRun &dr, int i, int beg)
+{
+    S *b0 = (S *)dr.msg[0];
+    const S *b1 = (const S *)dr.msg[1];
+    constexpr int CACHE = 4;
+    S v[CACHE];
+#pragma unroll
+    for (int k = 0; k < CACHE; ++k)
+        if (beg + k < g.M)
+            v[k] = b1[beg + k];
+    const int end = g.row_ptr[i + 1];
+#pragma unroll
+    for (int k = 0; k < CACHE; ++k)
+        if (beg + k < end)
+            b0[beg + k] = v[k];
+    for (int e = beg + CACHE; e < end; ++e)
+        b0[e] = b1[e];
+    return (unsigned int)(end - beg);
+}
+
+template <typename S, int CACHE>
+__device__ __forceinline__ void splash_eval_vertex_b(const DevGraph &g, const DevRun &dr, int i, int beg, int Lc)
+{
+    using A = typename Store<S>::A;
+    const S *b0 = (const S *)dr.msg[0];
+    S *b1 = (S *)dr.msg[1];
+    A h;
+    const A *q;
+    if constexpr (sizeof(A) == 8) {
+        h = g.udiff64[i];
+        q = (const A *)g.q64;
+    } else {
+        h = g.udiff32[i];
+        q = (const A *)g.q32;
+    }
+    int rf[CACHE], rc[CACHE];
+#pragma unroll
+    for (int k = 0; k < CACHE; ++k) {
+        if (beg + k < g.M) {
+            rf[k] = g.rev[beg + k];
+            rc[k] = g.col[beg + k];
+        }
+    }
+    const int end = g.row_ptr[i + 1];
+    const int deg = end - beg;
+    A uin[CACHE];
+#pragma unroll
+    for (int k = 0; k < CACHE; ++k) {
+        if (k < deg) {
+            const A u0 = Store<S>::ld(b0 + rf[k], g.qscale);
+            if (Lc >= 0) {
+                const A u1 = Store<S>::ld((const S *)b1 + rf[k], g.qscale);
+                uin[k] = dr.level[rc[k]] == Lc ? u1 : u0;
+            } else {
+                uin[k] = u0;
+            }
+        }
+    }
+    auto incoming = [&](int e) -> A {
+        const int f = g.rev[e];
+        const bool fresh = Lc >= 0 && dr.level[g.col[e]] == Lc;
+        return Store<S>::ld((fresh ? (const S *)b1 : b0) + f, g.qscale);
+    };
+#pragma unroll
+    for (int k = 0; k < CACHE; ++k)
+        if (k < deg)
+            h += uin[k];
+    for (int e = beg + CACHE; e < end; ++e)
+        h += incoming(e);
+#pragma unroll
+    for (int k = 0; k < CACHE; ++k)
+        if (k < deg)
+            Store<S>::st(b1 + beg + k, ising_logodds(q[beg + k], h - uin[k]), g.qscale);
+    for (int e = beg + CACHE; e < end; ++e)
+        Store<S>::st(b1 + e, ising_logodds(q[e], h - incoming(e)), g.qscale);
+}
+
 // Residual Splash sweep step for vertex i with level lv: commit its
 // out-messages when lv == Lc, or evaluate them when lv == Le. Returns the
 // number of messages committed.
