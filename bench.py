@@ -11,9 +11,15 @@ RBP/RS ceil(1000/p)), beliefs included.
 Metric: committed message updates per second (messages written by frontier
 commits) over the timed steps, with the per-schedule converged fraction and
 batch time-to-convergence reported beside it. The timed steps replay captured
-CUDA graphs; one further step of the same workload runs with CUDA events
-between the kernels of every round, which gives the message-update kernel's
-duration for the roofline and the share of each phase.
+CUDA graphs (after an untimed setup that tunes the update mapping and the
+selection path). One further step of the same workload runs with CUDA events
+between the kernels of every round: its phase split picks the dominant kernel
+for the roofline; the message-update kernel is also timed alone (back-to-back
+launches between two events) for its own roofline. Beside the metric: the
+storage formats side by side (1000x1000), time to convergence on a converging
+companion batch (100x100 at C = 2.5), per-graph launches against the batch
+(ER), the e2e figure through the C ABI with host buffers, and the FP64 CPU
+oracle on a bounded sample.
 
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload (the method has no other reference implementation).
@@ -355,6 +361,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile-step", action="store_true",
                     help="skip the extra step with per-phase CUDA events")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the side measurements (storage formats, converging companion batch, "
+                         "per-graph launches), e.g. for profiler passes")
     ap.add_argument("--rounds-scale", type=float, default=1.0,
                     help="scale every round cap (profiler passes only)")
     ap.add_argument("--direct-launch", action="store_true",
@@ -550,7 +559,7 @@ def main():
     # seeds, milder couplings): batch time until every graph converged or hit
     # its cap, per schedule and storage format
     ttc = None
-    if wl.get("ttc_beta") and rank == 0:
+    if wl.get("ttc_beta") and rank == 0 and not args.no_extras:
         from paper_1909_11469_gb300 import synth
         mild = synth.ising_grid_batch(wl["side"], wl["ttc_beta"], range(wl["n_seeds"]), wl["lam_max"])
         ttc = {"beta_max": wl["ttc_beta"], "graphs": mild.n_graphs}
@@ -569,7 +578,7 @@ def main():
     # storage formats side by side: each schedule once per format, from
     # uniform messages to convergence or the round cap
     dtype_cmp = None
-    if wl.get("dtype_compare") and rank == 0:
+    if wl.get("dtype_compare") and rank == 0 and not args.no_extras:
         dtype_cmp = {}
         for dt in wl["dtype_compare"]:
             for sched, p in wl["schedules"]:
@@ -587,7 +596,7 @@ def main():
     # batches: the same graphs launched one handle per graph, on a sample of
     # 64 graphs spread over the batch (per-graph launches vs the batched run)
     per_graph = None
-    if G >= 256 and rank == 0:
+    if G >= 256 and rank == 0 and not args.no_extras:
         idx = np.linspace(0, G - 1, 64).astype(int)
         tot_ms = {f"{sched}_p{p}": 0.0 for sched, p in wl["schedules"]}
         for q in idx:
