@@ -77,6 +77,9 @@ MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
 # message-update kernel from one ncu capture on the workload, with the kernel as
 # it is now (the summaries and commands are in profiles/). Captures are cold
 # (ncu flushes the caches), so they bound the warm traffic from above.
+# k_splash_list_step on the default workload: mean DRAM bytes of three captured
+# launches (26.8, 43.1 and 45.0 MB: the sub-steps move different level sizes).
+NCU_SWEEP_TRAFFIC = {("ising100x100_b2.5_50seeds", "f32"): (26.758e6 + 43.094e6 + 45.042e6) / 3}
 NCU_UPDATE_TRAFFIC = {
     # k_eval_bin_pf<float, CAND, 4 edges, 6 blocks/SM>: 29.81 MB + 2.8 KB
     ("ising100x100_b2.5_50seeds", "f32"): 29.806e6 + 2.8e3,
@@ -534,8 +537,10 @@ def main():
         # the kernel with the largest share of the profiled step gets the roofline
         def sel_ms(which):
             return sum(pr["select_ms"] for sc, _, _, pr, _ in prof_step if sc == which)
-        cands = [(phase["eval_ms"], update_roofline),
-                 (phase["sweep_ms"], sweep_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src))]
+        sweep_rf = sweep_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src)
+        if sweep_rf is not None:
+            sweep_rf["traffic"] = NCU_SWEEP_TRAFFIC.get((args.workload, wl["dtype"]))
+        cands = [(phase["eval_ms"], update_roofline), (phase["sweep_ms"], sweep_rf)]
         for which in ("rbp", "rs", "rnbp"):
             cands.append((sel_ms(which), select_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src,
                                                          which)))
