@@ -67,3 +67,58 @@ def test_philox_streams_differ_across_ranks():
 def test_shard_rejects_bad_rank():
     with pytest.raises(ValueError):
         shard.shard_seeds(2, 2, 5)
+
+
+def test_balanced_ranges_cover_and_balance():
+    batch = synth.er_batch(300, 7, n_max=3000)
+    m = np.diff(batch.row_ptr[batch.graph_var_offsets])
+    for world in (1, 2, 3, 8):
+        rs = shard.balanced_ranges(m, world)
+        assert len(rs) == world
+        assert [g for r in rs for g in r] == list(range(batch.n_graphs))
+        loads = [int(m[list(r)].sum()) for r in rs]
+        assert max(loads) - m.sum() / world < m.max() + 1
+
+
+def _worker_ranges(rank, world, port, out):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        batch = synth.er_batch(40, 3, n_max=300)
+        m = np.diff(batch.row_ptr[batch.graph_var_offsets])
+        mine = shard.balanced_ranges(m, world)[rank]
+        # the rank's first graph under its batch-wide id replays the one-process run
+        g0 = mine.start
+        res = oracle.run(batch.graph(g0), "rnbp", parallelism=0.5, eps=1e-6, max_rounds=30, seed=2,
+                         graph_id=mine.start + 0)
+        load = int(m[list(mine)].sum())
+        gathered = [None] * world
+        dist.all_gather_object(gathered, {"range": [mine.start, mine.stop], "load": load,
+                                          "committed": res["committed_updates"]})
+        if rank == 0:
+            out.put(gathered)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_balanced_batch():
+    """Each rank takes its balanced range of one batch and numbers its graphs
+    from the range start: the rank's graphs replay the one-process run."""
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 30500 + (os.getpid() % 1000)
+    procs = [ctx.Process(target=_worker_ranges, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (a0, b0), (a1, b1) = res[0]["range"], res[1]["range"]
+    assert a0 == 0 and b0 == a1 and b1 == 40
+    batch = synth.er_batch(40, 3, n_max=300)
+    ref = oracle.run(batch.graph(a1), "rnbp", parallelism=0.5, eps=1e-6, max_rounds=30, seed=2, graph_id=a1)
+    assert res[1]["committed"] == ref["committed_updates"]
