@@ -79,7 +79,7 @@ MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
 # (ncu flushes the caches), so they bound the warm traffic from above.
 # k_splash_list_step on the default workload: mean DRAM bytes of three captured
 # launches (26.8, 43.1 and 45.0 MB: the sub-steps move different level sizes).
-NCU_SWEEP_TRAFFIC = {("ising100x100_b2.5_50seeds", "f32"): (26.758e6 + 43.094e6 + 45.042e6) / 3}
+NCU_SWEEP_TRAFFIC = {("ising100x100_b2.5_50seeds", "f32", "per_sub_step"): (26.758e6 + 43.094e6 + 45.042e6) / 3}
 NCU_UPDATE_TRAFFIC = {
     # k_eval_bin_pf<float, CAND, 4 edges, 6 blocks/SM>: 29.81 MB + 2.8 KB
     ("ising100x100_b2.5_50seeds", "f32"): 29.806e6 + 2.8e3,
@@ -172,8 +172,10 @@ def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kern
 
 
 def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str):
-    """Roofline of the Residual Splash sweep kernel (k_splash_list_step) from a
-    profiled step. The sweeps run over per-level vertex lists: per evaluated
+    """Roofline of the Residual Splash sweep kernel from a profiled step:
+    k_splash_sweep_cluster (every sub-step of a round in one launch, a cluster
+    per graph) or k_splash_list_step (one launch per sub-step), whichever the
+    runs used. The sweeps run over per-level vertex lists: per evaluated
     message rev, col, the source's level, the incoming message, exp(-2 beta) and
     the written candidate (13 + 2 s B), per evaluated vertex its list entry,
     row_ptr and unary log-odds (16 B, spread over its d-bar out-messages); per
@@ -181,10 +183,11 @@ def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str)
     list entry and row_ptr (12 B). Every evaluated message is committed once."""
     s = MSG_BYTES[dtype]
     dbar = m / max(n, 1)
-    b, ms, launches = 0.0, 0.0, 0
+    b, ms, launches, cluster = 0.0, 0.0, 0, False
     for sched, p, st, pr, gst in step:
         if sched != "rs" or pr["sweep_launches"] == 0:
             continue
+        cluster = cluster or pr.get("sweep_ctas", 0) > 0
         upd = st["committed_updates"]
         b += upd * (13 + 2 * s + 16 / dbar) + upd * (2 * s + 12 / dbar)
         ms += pr["sweep_ms"]
@@ -192,8 +195,12 @@ def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str)
     if ms <= 0:
         return None
     a = b / (ms / 1e3) / 1e9
-    return {"bound": "hbm", "kernel": f"k_splash_list_step ({dtype} messages; Residual Splash sweep over "
-            "level lists: commit of one level fused with the evaluation of the next)", "achieved": a,
+    name = ("k_splash_sweep_cluster ({dtype} messages; all Residual Splash sub-steps of a round in one "
+            "launch, one thread-block cluster per graph, cluster barriers between sub-steps)" if cluster else
+            "k_splash_list_step ({dtype} messages; Residual Splash sweep over level lists: commit of one "
+            "level fused with the evaluation of the next)").format(dtype=dtype)
+    return {"bound": "hbm", "kernel": name, "sweep_form": "cluster" if cluster else "per_sub_step",
+            "achieved": a,
             "peak": peak, "unit": "GB/s", "peak_source": peak_src, "frac": a / peak, "traffic": None,
             "launches": launches, "bytes_per_launch": b / launches, "avg_launch_us": 1e3 * ms / launches}
 
@@ -377,6 +384,9 @@ def main():
     ap.add_argument("--potts-path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="shared-table update: 0 automatic, 1 CUDA cores, 2 tensor cores BF16, "
                          "3 tensor cores split")
+    ap.add_argument("--splash-sweep", type=int, default=0, choices=[0, 1, 2],
+                    help="Residual Splash sweeps: 0 library's choice, 1 one launch per sub-step, "
+                         "2 one cluster kernel per round")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "q16", "f64"],
                     help="message storage (default: the workload's)")
     ap.add_argument("--autotune", default=None, choices=["none", "mapping", "mapping+p"],
@@ -421,7 +431,7 @@ def main():
         return bp.bp_default_options(msg_dtype=wl["dtype"], cuda_stream=stream.cuda_stream,
                                      graph_id_base=shard.graph_id_base(rank, G),
                                      kernel_variant=args.kernel_variant,
-                                     potts_path=args.potts_path, **kw)
+                                     potts_path=args.potts_path, splash_sweep=args.splash_sweep, **kw)
 
     def one_step(profile: int):
         out = []
@@ -539,7 +549,7 @@ def main():
             return sum(pr["select_ms"] for sc, _, _, pr, _ in prof_step if sc == which)
         sweep_rf = sweep_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src)
         if sweep_rf is not None:
-            sweep_rf["traffic"] = NCU_SWEEP_TRAFFIC.get((args.workload, wl["dtype"]))
+            sweep_rf["traffic"] = NCU_SWEEP_TRAFFIC.get((args.workload, wl["dtype"], sweep_rf["sweep_form"]))
         cands = [(phase["eval_ms"], update_roofline), (phase["sweep_ms"], sweep_rf)]
         for which in ("rbp", "rs", "rnbp"):
             cands.append((sel_ms(which), select_roofline(prof_step, wl["dtype"], prob.n, prob.m, peak, peak_src,

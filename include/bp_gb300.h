@@ -127,6 +127,13 @@ typedef struct {
                                  0 = automatic (by an occupancy-based time estimate), 1 =
                                  one thread-block cluster per graph, 2 = grid-wide
                                  kernels (for a few large graphs) */
+    int32_t splash_sweep;     /* RS sweeps (binary messages, splash_depth <= 3; the same
+                                 bits either way): 0 = automatic (one launch per
+                                 sub-step, the faster form measured), 1 = one launch
+                                 per sub-step, 2 = all sub-steps of a round in one
+                                 launch, one thread-block cluster per graph (used only
+                                 with the cluster selection; with the grid-wide
+                                 selection the sweeps are per sub-step) */
 } bp_options;
 
 /* Phase timings and launch counts of the last bp_run. The timings are filled
@@ -153,6 +160,8 @@ typedef struct {
     int32_t select_ctas[2];    /* RBP, RS selection of the run: CTAs per graph of the cluster
                                   kernels (0 when the grid-wide kernels ran; always filled) */
     int32_t kernel_variant;    /* the binary update mapping the run used (always filled) */
+    int32_t sweep_ctas;        /* RS: CTAs per graph of the cluster sweep, 0 when the sweeps
+                                  ran one launch per sub-step (always filled) */
 } bp_profile;
 
 /* Fills *opt with the defaults listed above. */

@@ -114,6 +114,7 @@ struct bp_graph {
     int8_t *d_level = nullptr;
     int2 *d_lvl_list = nullptr;                 // Residual Splash level lists (lazy)
     int32_t *d_lvl_cnt = nullptr;
+    int32_t *d_lvl_gcnt = nullptr;              // per-graph level list lengths (cluster sweep)
     double *d_graph_p = nullptr;   // per-graph parallelism (bp_set_graph_parallelism)
     bool graph_p_set = false;
     int32_t max_deg = 0;           // largest vertex degree (size class, mapping heuristic)
@@ -126,6 +127,9 @@ struct bp_graph {
     int32_t max_graph_edges = 0;
     int32_t sel_plan[4][6];          // per message dtype: RBP CTAs, bytes, grid flag; RS the same
     bool sel_planned[4] = {false, false, false, false};
+    int32_t sweep_plan[4][2];        // per message dtype: cluster-sweep CTAs per graph, 1 = the
+                                     // estimate prefers the cluster sweep
+    bool sweep_planned[4] = {false, false, false, false};
     // grid-wide selection buffers (allocated when a plan picks the grid kernels)
     GSelState *d_gsel = nullptr;
     unsigned int *d_gsel_hist = nullptr;
@@ -231,6 +235,7 @@ DevGraph dev_graph(const bp_graph *g)
     d.sel_c[0] = d.sel_c[1] = 1;
     d.sel_dyn[0] = d.sel_dyn[1] = 0;
     d.sel_grid[0] = d.sel_grid[1] = 0;
+    d.sweep_c = 1;
     d.row_ptr = g->d_row_ptr;
     d.col = g->d_col;
     d.rev = g->d_rev;
@@ -265,6 +270,7 @@ DevRun dev_run(const bp_graph *g)
     r.queue = g->d_queue;
     r.lvl_list = g->d_lvl_list;
     r.lvl_cnt = g->d_lvl_cnt;
+    r.lvl_gcnt = g->d_lvl_gcnt;
     r.graph_p = g->graph_p_set ? g->d_graph_p : nullptr;
     r.gsel = g->d_gsel;
     r.gsel_hist = g->d_gsel_hist;
@@ -276,7 +282,8 @@ DevRun dev_run(const bp_graph *g)
 }
 
 // Selection shape of a run: the cluster plan of the handle for this storage
-// format and the grid-wide flags the run chose (bit 0 RBP, bit 1 RS).
+// format and the grid-wide flags the run chose (bit 0 RBP, bit 1 RS), and the
+// cluster size of the splash sweep.
 void apply_select_plan(const bp_graph *g, int dtype, int sel_grid_bits, DevGraph &dg)
 {
     if (g->sel_planned[dtype]) {
@@ -285,6 +292,8 @@ void apply_select_plan(const bp_graph *g, int dtype, int sel_grid_bits, DevGraph
         dg.sel_c[1] = g->sel_plan[dtype][3];
         dg.sel_dyn[1] = g->sel_plan[dtype][4];
     }
+    if (g->sweep_planned[dtype])
+        dg.sweep_c = g->sweep_plan[dtype][0];
     dg.sel_grid[0] = sel_grid_bits & 1;
     dg.sel_grid[1] = (sel_grid_bits >> 1) & 1;
 }
@@ -525,6 +534,12 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
             }
             if (ev)
                 cudaEventRecord(ev[3], s);
+            if (rp.sweep_cluster) {
+                // every sub-step of the round in one launch, a cluster per graph
+                launch_splash_sweep_cluster(dtype, dg, dr, rp, s);
+                kernels += any;
+                break;
+            }
             launch_splash_list_step(dtype, dg, dr, -1, level_of(0), s);
             for (int step = 0; step < 2 * h; ++step)
                 launch_splash_list_step(dtype, dg, dr, level_of(step), level_of(step + 1), s);
@@ -842,6 +857,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "potts_path must be 0..3");
     if (opt.select_path < 0 || opt.select_path > 2)
         return fail(BP_ERR_INVALID_ARG, "select_path must be 0..2");
+    if (opt.splash_sweep < 0 || opt.splash_sweep > 2)
+        return fail(BP_ERR_INVALID_ARG, "splash_sweep must be 0..2");
     if (opt.kernel_variant < 0 || opt.kernel_variant > 5)
         return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 5]");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
@@ -856,7 +873,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     if (schedule == BP_RS && epm_of(g) == 1 && opt.splash_depth <= LVL_MAX && !g->d_lvl_list) {
         // level lists of the Residual Splash sweeps, kept until the handle is destroyed
         if ((rc = dalloc(&g->d_lvl_list, (size_t)(LVL_MAX + 1) * (size_t)std::max(g->n, 1))) != BP_OK ||
-            (rc = dalloc(&g->d_lvl_cnt, (size_t)(LVL_MAX + 1))) != BP_OK)
+            (rc = dalloc(&g->d_lvl_cnt, (size_t)(LVL_MAX + 1))) != BP_OK ||
+            (rc = dalloc(&g->d_lvl_gcnt, (size_t)(LVL_MAX + 1) * (size_t)std::max(g->G, 1))) != BP_OK)
             return rc;
         BP_CK(cudaMemset(g->d_lvl_cnt, 0, sizeof(int32_t) * (LVL_MAX + 1)));
     }
@@ -915,6 +933,16 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
             bits = 0;
         apply_select_plan(g, dtype, bits, dg);
         rp.sel_grid = bits;
+    }
+    if (schedule == BP_RS && epm_of(g) == 1 && opt.splash_depth <= LVL_MAX && g->d_lvl_list &&
+        !(rp.sel_grid & 2) && variant != 3) {
+        // the cluster selection writes per-graph level lists for the cluster sweep
+        if (!g->sweep_planned[dtype]) {
+            plan_sweep(dtype, g->G, g->n, g->max_graph_vertices, g->sweep_plan[dtype]);
+            g->sweep_planned[dtype] = true;
+        }
+        rp.sweep_cluster = opt.splash_sweep == 2 ? 1 : (opt.splash_sweep == 1 ? 0 : g->sweep_plan[dtype][1]);
+        dg.sweep_c = g->sweep_plan[dtype][0];
     }
     DevRun dr = dev_run(g);
     g->has_result = false;
@@ -1078,11 +1106,12 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         prof.eval_launches = (int64_t)live;
         // every committing round of an RS run sweeps 2h + 2 fused steps (binary)
         if (schedule == BP_RS && epm_of(g) == 1)
-            prof.sweep_launches = (int64_t)(live > 0 ? live - 1 : 0) * (2 * opt.splash_depth + 2);
+            prof.sweep_launches = (int64_t)(live > 0 ? live - 1 : 0) * (rp.sweep_cluster ? 1 : 2 * opt.splash_depth + 2);
     }
     for (int w = 0; w < 2; ++w)
         prof.select_ctas[w] = (dg.sel_grid[w] && dr.gsel) ? 0 : dg.sel_c[w];
     prof.kernel_variant = variant;
+    prof.sweep_ctas = rp.sweep_cluster ? dg.sweep_c : 0;
     g->last_profile = prof;
     g->has_result = true;
     g->res_dtype = dtype;
@@ -1429,6 +1458,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_level);
     dfree(g->d_lvl_list);
     dfree(g->d_lvl_cnt);
+    dfree(g->d_lvl_gcnt);
     dfree(g->d_graph_p);
     dfree(g->d_gsel);
     dfree(g->d_gsel_hist);

@@ -43,6 +43,7 @@ struct DevGraph {
     int32_t sel_c[2];         // selection clusters: CTAs per graph (RBP, RS), planned per run
     int32_t sel_dyn[2];       // selection clusters: staged-key bytes per CTA (RBP, RS)
     int32_t sel_grid[2];      // 1: select with the grid-wide kernels instead (RBP, RS)
+    int32_t sweep_c;          // CTAs per graph of the cluster splash sweep, planned per run
     const int32_t *row_ptr;   // [n+1]
     const int32_t *col;       // [M]
     const int32_t *rev;       // [M]
@@ -80,6 +81,8 @@ struct RunParams {
     int32_t tc_path;          // shared-table update: 0 per-vertex, 1 tiles/CUDA cores, 2 tiles/tensor
                               // cores, 3 tiles/tensor cores with residual products
     int32_t sel_grid;         // grid-wide selection: bit 0 RBP, bit 1 RS (keys the captured rounds)
+    int32_t sweep_cluster;    // RS: 1 = the round's sweeps run in one cluster kernel over
+                              // per-graph level lists, 0 = one launch per sub-step
 };
 
 // eps in the residual type, chosen so that the comparison equals the FP64 test.
@@ -112,6 +115,9 @@ struct DevRun {
     int2 *lvl_list;               // [(LVL_MAX+1) * n] Residual Splash vertices of each level:
                                   // (vertex, its first out-edge)
     int32_t *lvl_cnt;             // [LVL_MAX+1] entries of each level list
+    int32_t *lvl_gcnt;            // [G * (LVL_MAX+1)] entries of each graph's level lists, when
+                                  // the lists are per graph: graph gg's level L at
+                                  // lvl_list[L * n + gv_off[gg] + j], j < lvl_gcnt[gg * (LVL_MAX+1) + L]
     const double *graph_p;        // [G] per-graph parallelism, or null: every graph uses rp.low_p
     // grid-wide selection (large graphs; null when unused)
     GSelState *gsel;              // [G]

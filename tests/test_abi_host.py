@@ -43,11 +43,12 @@ def test_struct_layout_matches_header(tmp_path):
 #include <stdio.h>
 #include "bp_gb300.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bp_options), sizeof(bp_run_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bp_options), sizeof(bp_run_stats),
          offsetof(bp_options, cuda_stream), offsetof(bp_options, kernel_variant),
          offsetof(bp_run_stats, device_ms), offsetof(bp_run_stats, status),
          sizeof(bp_profile), offsetof(bp_profile, kernel_variant),
-         sizeof(bp_tune_result), offsetof(bp_tune_result, ms_per_round_select));
+         sizeof(bp_tune_result), offsetof(bp_tune_result, ms_per_round_select),
+         offsetof(bp_options, splash_sweep), offsetof(bp_profile, sweep_ctas));
   return 0;
 }
 """)
@@ -58,7 +59,8 @@ int main(void) {
                     bp.bp_options.cuda_stream.offset, bp.bp_options.kernel_variant.offset,
                     bp.bp_run_stats.device_ms.offset, bp.bp_run_stats.status.offset,
                     ctypes.sizeof(bp.bp_profile), bp.bp_profile.kernel_variant.offset,
-                    ctypes.sizeof(bp.bp_tune_result), bp.bp_tune_result.ms_per_round_select.offset]
+                    ctypes.sizeof(bp.bp_tune_result), bp.bp_tune_result.ms_per_round_select.offset,
+                    bp.bp_options.splash_sweep.offset, bp.bp_profile.sweep_ctas.offset]
 
 
 def test_status_strings(L):

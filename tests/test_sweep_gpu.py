@@ -1,0 +1,125 @@
+"""The two forms of the Residual Splash sweeps (binary messages): one launch
+per sub-step over batch-wide level lists, or every sub-step of a round in one
+launch with a thread-block cluster per graph over per-graph level lists
+(bp_options.splash_sweep = 1 / 2). Both perform the same reads and writes in
+every sub-step (the splash of Section III-C with the level order h, ..., 0,
+..., h), so FP64 runs replay the oracle exactly and every storage format gives
+bit-identical results in either form."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_11469_gb300 import bp, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def uneven_batch():
+    members = [synth.ising_grid(9, 1.0, seed=1), synth.ising_chain(300, 2.0, seed=2),
+               synth.ising_grid(20, 2.0, seed=3, cols=7), synth.ising_tree(50, 1.5, seed=4),
+               synth.ising_grid(3, 0.0, seed=5)]
+    members += [synth.er_batch(1, seed=s, n_min=30, n_max=400).graph(0) for s in range(5)]
+    return members, synth.concat_batch(members)
+
+
+def run(prob, dtype, sweep, depth=2, par=0.1, rounds=40, eps=1e-5, profile=0, **opts):
+    """RS run; profile = 1 launches the rounds directly, 0 replays captured rounds."""
+    with bp.Graph(prob) as g:
+        st = g.run("rs", par, eps=eps, max_rounds=rounds, msg_dtype=dtype, splash_sweep=sweep,
+                   splash_depth=depth, profile=profile, **opts)
+        return (st, g.beliefs(), g.messages(), [(x["converged"], x["rounds"], x["committed_updates"])
+                                                 for x in g.graph_stats()], g.profile())
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2, 3])
+@pytest.mark.parametrize("sweep", [1, 2])
+def test_fp64_batch_replays_oracle(sweep, depth):
+    """Every graph of an uneven batch matches the oracle run of that graph
+    alone over 40 rounds: rounds, convergence, committed updates, beliefs.
+    (The horizon is short: the 156-vertex ER member is not contracting -- the
+    k-th largest vertex residual stays near 0.5 for 170 rounds -- so the
+    rounding differences of two FP64 implementations grow from round to round
+    until one of them takes other splash roots, although the smallest relative
+    gap at the k-th root in the oracle's 214 rounds is 1.2e-6, at round 132.)"""
+    members, batch = uneven_batch()
+    T = 40
+    st, bel, msg, gst, prof = run(batch, "f64", sweep, depth=depth, par=0.05, rounds=T)
+    assert (prof["sweep_ctas"] > 0) == (sweep == 2)
+    for gi, m in enumerate(members):
+        ref = oracle.run(m, "rs", parallelism=0.05, eps=1e-5, max_rounds=T, splash_depth=depth,
+                         graph_id=gi)
+        assert gst[gi][1] == ref["rounds"], gi
+        assert bool(gst[gi][0]) == ref["converged"], gi
+        assert gst[gi][2] == ref["committed_updates"], gi
+        v0, v1 = batch.graph_var_offsets[gi], batch.graph_var_offsets[gi + 1]
+        assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < 1e-9, gi
+
+
+@pytest.mark.parametrize("sweep", [1, 2])
+def test_fp64_trace_replay(sweep):
+    """Same splash roots every round and the same state after 60 rounds of a
+    ragged 13 x 11 grid."""
+    prob = synth.ising_grid(13, 2.0, seed=4, cols=11)
+    T = 60
+    ref = oracle.run(prob, "rs", parallelism=0.1, eps=1e-7, max_rounds=T, trace_cap=T)
+    with bp.Graph(prob) as g:
+        st = g.run("rs", 0.1, eps=1e-7, max_rounds=T, msg_dtype="f64", splash_sweep=sweep,
+                   record_trace=1, trace_capacity=T)
+        tr = g.trace("rs")
+        assert st["rounds"] == ref["rounds"]
+        assert np.array_equal(tr, ref["trace"][:ref["rounds"]])
+        assert st["committed_updates"] == ref["committed_updates"]
+        assert np.abs(g.beliefs() - ref["beliefs"]).max() < TOL_F64
+        assert np.abs(g.messages() - ref["messages"]).max() < TOL_F64
+
+
+@pytest.mark.parametrize("name", ["uneven", "er", "grids"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "q16"])
+@pytest.mark.parametrize("depth", [2, 3])
+def test_forms_bit_identical(name, dtype, depth):
+    if name == "uneven":
+        prob = uneven_batch()[1]
+    elif name == "er":
+        prob = synth.er_batch(60, 7, n_max=1500)
+    else:
+        prob = synth.ising_grid_batch(40, 2.5, range(6))
+    a = run(prob, dtype, 1, depth=depth)
+    b = run(prob, dtype, 2, depth=depth, profile=1 if depth == 3 else 0)
+    assert a[4]["sweep_ctas"] == 0 and b[4]["sweep_ctas"] > 0
+    keys = ("rounds", "committed_updates", "candidate_evals", "converged")
+    assert [a[0][k] for k in keys] == [b[0][k] for k in keys]
+    assert a[3] == b[3]
+    assert np.array_equal(a[1], b[1]), float(np.abs(a[1] - b[1]).max())
+    assert np.array_equal(a[2], b[2])
+
+
+def test_default_batch_shape_sweep_forms():
+    """50 Ising 100 x 100 grids: the automatic choice keeps the per-sub-step
+    launches, and a few rounds of the cluster sweep equal them bit for bit.
+    With the grid-wide selection a requested cluster sweep falls back to
+    per-sub-step launches."""
+    prob = synth.ising_grid_batch(100, 2.5, range(50))
+    auto = run(prob, "f32", 0, rounds=6)
+    assert auto[4]["sweep_ctas"] == 0
+    cluster = run(prob, "f32", 2, rounds=6)
+    assert cluster[4]["sweep_ctas"] > 0
+    assert np.array_equal(auto[1], cluster[1])
+    assert auto[0]["committed_updates"] == cluster[0]["committed_updates"]
+    grid = run(prob, "f32", 2, rounds=6, select_path=2)
+    assert grid[4]["sweep_ctas"] == 0
+    assert np.array_equal(grid[1], auto[1])
+
+
+def test_bad_splash_sweep_rejected():
+    prob = synth.ising_grid(5, 1.0, seed=0)
+    with bp.Graph(prob) as g:
+        with pytest.raises(bp.BPError):
+            g.run("rs", 0.1, splash_sweep=3)
