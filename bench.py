@@ -183,11 +183,11 @@ def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str)
     list entry and row_ptr (12 B). Every evaluated message is committed once."""
     s = MSG_BYTES[dtype]
     dbar = m / max(n, 1)
-    b, ms, launches, cluster = 0.0, 0.0, 0, False
+    b, ms, launches, form = 0.0, 0.0, 0, 0
     for sched, p, st, pr, gst in step:
         if sched != "rs" or pr["sweep_launches"] == 0:
             continue
-        cluster = cluster or pr.get("sweep_ctas", 0) > 0
+        form = max(form, pr.get("sweep_form", 0))
         upd = st["committed_updates"]
         b += upd * (13 + 2 * s + 16 / dbar) + upd * (2 * s + 12 / dbar)
         ms += pr["sweep_ms"]
@@ -195,11 +195,13 @@ def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str)
     if ms <= 0:
         return None
     a = b / (ms / 1e3) / 1e9
-    name = ("k_splash_sweep_cluster ({dtype} messages; all Residual Splash sub-steps of a round in one "
-            "launch, one thread-block cluster per graph, cluster barriers between sub-steps)" if cluster else
-            "k_splash_list_step ({dtype} messages; Residual Splash sweep over level lists: commit of one "
-            "level fused with the evaluation of the next)").format(dtype=dtype)
-    return {"bound": "hbm", "kernel": name, "sweep_form": "cluster" if cluster else "per_sub_step",
+    name = {1: "k_splash_sweep_cluster ({dtype} messages; all Residual Splash sub-steps of a round in one "
+               "launch, one thread-block cluster per graph, cluster barriers between sub-steps)",
+            2: "k_splash_list_pair ({dtype} messages; Residual Splash sweep over level lists: commit of one "
+               "level fused with the evaluation of the next, a commit and an evaluation entry per thread)",
+            0: "k_splash_list_step ({dtype} messages; Residual Splash sweep over level lists: commit of one "
+               "level fused with the evaluation of the next)"}[form].format(dtype=dtype)
+    return {"bound": "hbm", "kernel": name, "sweep_form": ["per_sub_step", "cluster", "per_sub_step_pair"][form],
             "achieved": a,
             "peak": peak, "unit": "GB/s", "peak_source": peak_src, "frac": a / peak, "traffic": None,
             "launches": launches, "bytes_per_launch": b / launches, "avg_launch_us": 1e3 * ms / launches}
@@ -384,9 +386,10 @@ def main():
     ap.add_argument("--potts-path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="shared-table update: 0 automatic, 1 CUDA cores, 2 tensor cores BF16, "
                          "3 tensor cores split")
-    ap.add_argument("--splash-sweep", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--splash-sweep", type=int, default=0, choices=[0, 1, 2, 3],
                     help="Residual Splash sweeps: 0 library's choice, 1 one launch per sub-step, "
-                         "2 one cluster kernel per round")
+                         "2 one cluster kernel per round, 3 one launch per sub-step with a commit "
+                         "and an evaluation entry per thread")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "q16", "f64"],
                     help="message storage (default: the workload's)")
     ap.add_argument("--autotune", default=None, choices=["none", "mapping", "mapping+p"],

@@ -128,12 +128,13 @@ typedef struct {
                                  one thread-block cluster per graph, 2 = grid-wide
                                  kernels (for a few large graphs) */
     int32_t splash_sweep;     /* RS sweeps (binary messages, splash_depth <= 3; the same
-                                 bits either way): 0 = automatic (one launch per
-                                 sub-step, the faster form measured), 1 = one launch
-                                 per sub-step, 2 = all sub-steps of a round in one
-                                 launch, one thread-block cluster per graph (used only
-                                 with the cluster selection; with the grid-wide
-                                 selection the sweeps are per sub-step) */
+                                 bits in every form): 0 = automatic (1), 1 = one
+                                 launch per sub-step, one list entry per thread, 2 =
+                                 all sub-steps of a round in one launch, one
+                                 thread-block cluster per graph (used only with the
+                                 cluster selection; with the grid-wide selection it
+                                 runs as 1), 3 = one launch per sub-step, a commit
+                                 entry and an evaluation entry per thread */
 } bp_options;
 
 /* Phase timings and launch counts of the last bp_run. The timings are filled
@@ -162,6 +163,8 @@ typedef struct {
     int32_t kernel_variant;    /* the binary update mapping the run used (always filled) */
     int32_t sweep_ctas;        /* RS: CTAs per graph of the cluster sweep, 0 when the sweeps
                                   ran one launch per sub-step (always filled) */
+    int32_t sweep_form;        /* RS sweep form of the run: 0 per-sub-step launches, 1 cluster
+                                  kernel, 2 per-sub-step launches with paired entries */
 } bp_profile;
 
 /* Fills *opt with the defaults listed above. */

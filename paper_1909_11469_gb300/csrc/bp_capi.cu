@@ -534,16 +534,17 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
             }
             if (ev)
                 cudaEventRecord(ev[3], s);
-            if (rp.sweep_cluster) {
+            if (rp.sweep_form == SWEEP_CLUSTER) {
                 // every sub-step of the round in one launch, a cluster per graph
                 launch_splash_sweep_cluster(dtype, dg, dr, rp, s);
                 kernels += any;
                 break;
             }
-            launch_splash_list_step(dtype, dg, dr, -1, level_of(0), s);
+            auto step_launch = rp.sweep_form == SWEEP_PAIR ? launch_splash_list_pair : launch_splash_list_step;
+            step_launch(dtype, dg, dr, -1, level_of(0), s);
             for (int step = 0; step < 2 * h; ++step)
-                launch_splash_list_step(dtype, dg, dr, level_of(step), level_of(step + 1), s);
-            launch_splash_list_step(dtype, dg, dr, level_of(2 * h), -1, s);
+                step_launch(dtype, dg, dr, level_of(step), level_of(step + 1), s);
+            step_launch(dtype, dg, dr, level_of(2 * h), -1, s);
             kernels += any ? 2 * h + 2 : 0;
             break;
         }
@@ -857,8 +858,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "potts_path must be 0..3");
     if (opt.select_path < 0 || opt.select_path > 2)
         return fail(BP_ERR_INVALID_ARG, "select_path must be 0..2");
-    if (opt.splash_sweep < 0 || opt.splash_sweep > 2)
-        return fail(BP_ERR_INVALID_ARG, "splash_sweep must be 0..2");
+    if (opt.splash_sweep < 0 || opt.splash_sweep > 3)
+        return fail(BP_ERR_INVALID_ARG, "splash_sweep must be 0..3");
     if (opt.kernel_variant < 0 || opt.kernel_variant > 5)
         return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 5]");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
@@ -934,15 +935,24 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         apply_select_plan(g, dtype, bits, dg);
         rp.sel_grid = bits;
     }
-    if (schedule == BP_RS && epm_of(g) == 1 && opt.splash_depth <= LVL_MAX && g->d_lvl_list &&
-        !(rp.sel_grid & 2) && variant != 3) {
-        // the cluster selection writes per-graph level lists for the cluster sweep
-        if (!g->sweep_planned[dtype]) {
+    if (schedule == BP_RS && epm_of(g) == 1 && opt.splash_depth <= LVL_MAX && g->d_lvl_list && variant != 3) {
+        // sweeps over level lists: the per-sub-step forms over the batch-wide
+        // lists, or the cluster sweep over the per-graph lists that only the
+        // cluster selection writes
+        const bool cluster_ok = !(rp.sel_grid & 2);
+        if (cluster_ok && !g->sweep_planned[dtype]) {
             plan_sweep(dtype, g->G, g->n, g->max_graph_vertices, g->sweep_plan[dtype]);
             g->sweep_planned[dtype] = true;
         }
-        rp.sweep_cluster = opt.splash_sweep == 2 ? 1 : (opt.splash_sweep == 1 ? 0 : g->sweep_plan[dtype][1]);
-        dg.sweep_c = g->sweep_plan[dtype][0];
+        static const int32_t form_of[4] = {SWEEP_LIST, SWEEP_LIST, SWEEP_CLUSTER, SWEEP_PAIR};
+        int32_t form = form_of[opt.splash_sweep];
+        if (opt.splash_sweep == 0 && cluster_ok && g->sweep_plan[dtype][1])
+            form = SWEEP_CLUSTER;
+        if (form == SWEEP_CLUSTER && !cluster_ok)
+            form = SWEEP_LIST;
+        rp.sweep_form = form;
+        if (form == SWEEP_CLUSTER)
+            dg.sweep_c = g->sweep_plan[dtype][0];
     }
     DevRun dr = dev_run(g);
     g->has_result = false;
@@ -1106,12 +1116,13 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         prof.eval_launches = (int64_t)live;
         // every committing round of an RS run sweeps 2h + 2 fused steps (binary)
         if (schedule == BP_RS && epm_of(g) == 1)
-            prof.sweep_launches = (int64_t)(live > 0 ? live - 1 : 0) * (rp.sweep_cluster ? 1 : 2 * opt.splash_depth + 2);
+            prof.sweep_launches = (int64_t)(live > 0 ? live - 1 : 0) * (rp.sweep_form == SWEEP_CLUSTER ? 1 : 2 * opt.splash_depth + 2);
     }
     for (int w = 0; w < 2; ++w)
         prof.select_ctas[w] = (dg.sel_grid[w] && dr.gsel) ? 0 : dg.sel_c[w];
     prof.kernel_variant = variant;
-    prof.sweep_ctas = rp.sweep_cluster ? dg.sweep_c : 0;
+    prof.sweep_ctas = rp.sweep_form == SWEEP_CLUSTER ? dg.sweep_c : 0;
+    prof.sweep_form = rp.sweep_form;
     g->last_profile = prof;
     g->has_result = true;
     g->res_dtype = dtype;

@@ -81,9 +81,13 @@ struct RunParams {
     int32_t tc_path;          // shared-table update: 0 per-vertex, 1 tiles/CUDA cores, 2 tiles/tensor
                               // cores, 3 tiles/tensor cores with residual products
     int32_t sel_grid;         // grid-wide selection: bit 0 RBP, bit 1 RS (keys the captured rounds)
-    int32_t sweep_cluster;    // RS: 1 = the round's sweeps run in one cluster kernel over
-                              // per-graph level lists, 0 = one launch per sub-step
+    int32_t sweep_form;       // RS sweeps (binary, level lists): SWEEP_LIST one launch per
+                              // sub-step, SWEEP_CLUSTER one cluster kernel per round over
+                              // per-graph level lists, SWEEP_PAIR one launch per sub-step
+                              // with a commit and an evaluation per thread
 };
+
+enum { SWEEP_LIST = 0, SWEEP_CLUSTER = 1, SWEEP_PAIR = 2 };
 
 // eps in the residual type, chosen so that the comparison equals the FP64 test.
 __device__ __forceinline__ float eps_in(const RunParams &rp, float) { return rp.eps_f; }

@@ -792,6 +792,24 @@ __global__ void __launch_bounds__(BLOCK, 6) k_splash_list_step(DevGraph g, DevRu
     }
 }
 
+// The same sub-step with thread t taking commit entry t and evaluation entry
+// t together (max(nc, ne) threads instead of nc + ne). Entries at t >= the
+// count are not used; every index t < max(nc, ne) <= n stays inside a list.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK, 6) k_splash_list_pair(DevGraph g, DevRun dr, int Lc, int Le)
+{
+    const int nc = Lc >= 0 ? dr.lvl_cnt[Lc] : 0;
+    const int ne = Le >= 0 ? dr.lvl_cnt[Le] : 0;
+    const int2 *lc = dr.lvl_list + (size_t)(Lc >= 0 ? Lc : 0) * g.n;
+    const int2 *le = dr.lvl_list + (size_t)(Le >= 0 ? Le : 0) * g.n;
+    const int total = nc > ne ? nc : ne;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int2 vc = lc[t];
+        const int2 ve = le[t];
+        splash_pair_vertex_b<S>(g, dr, t < nc, vc.x, vc.y, t < ne, ve.x, ve.y, Lc);
+    }
+}
+
 // --------------------------------------------------------------------------
 // Set-up of a run.
 template <typename S>
@@ -1031,6 +1049,14 @@ void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int
         return;
     const int nb = std::min(blocks_for(g.n, BLOCK), 152 * 6);   // one wave at 6 blocks per SM
     BPG_DISPATCH4(dtype, (k_splash_list_step<S><<<nb, BLOCK, 0, s>>>(g, dr, Lc, Le)));
+}
+
+void launch_splash_list_pair(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s)
+{
+    if (g.n == 0)
+        return;
+    const int nb = std::min(blocks_for(g.n, BLOCK), 152 * 6);   // one wave at 6 blocks per SM
+    BPG_DISPATCH4(dtype, (k_splash_list_pair<S><<<nb, BLOCK, 0, s>>>(g, dr, Lc, Le)));
 }
 
 void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int level_L, cudaStream_t s)

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_rbp(DevGraph g, DevRun d
 // the top k_sel vertices as splash roots (level 0), every other vertex gets
 // level -1, then the BFS levels 1..h and (binary messages) the per-level
 // vertex lists of the sweeps: one list per level for the whole batch, or,
-// for the cluster sweep (rp.sweep_cluster), one per graph and level inside
+// for the cluster sweep (rp.sweep_form == SWEEP_CLUSTER), one per graph and level inside
 // the graph's vertex range. Each CTA owns a slice of the graph's vertices.
 template <typename S>
 __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun dr, RunParams rp)
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun
     const int nv = g.gv_off[gg + 1] - v0;
     if (nv == 0)
         return;
-    const bool per_graph = rp.sweep_cluster != 0;
+    const bool per_graph = rp.sweep_form == SWEEP_CLUSTER;
     // (the selection's cluster barriers order this before the peers' additions)
     if (per_graph && rank == 0 && threadIdx.x <= (unsigned)LVL_MAX)
         s_gcnt[threadIdx.x] = 0;

@@ -1,10 +1,11 @@
-"""The two forms of the Residual Splash sweeps (binary messages): one launch
-per sub-step over batch-wide level lists, or every sub-step of a round in one
-launch with a thread-block cluster per graph over per-graph level lists
-(bp_options.splash_sweep = 1 / 2). Both perform the same reads and writes in
-every sub-step (the splash of Section III-C with the level order h, ..., 0,
-..., h), so FP64 runs replay the oracle exactly and every storage format gives
-bit-identical results in either form."""
+"""The forms of the Residual Splash sweeps (binary messages): one launch per
+sub-step over batch-wide level lists with one entry per thread, the same with
+a commit entry and an evaluation entry per thread, or every sub-step of a
+round in one launch with a thread-block cluster per graph over per-graph level
+lists (bp_options.splash_sweep = 1 / 3 / 2). All perform the same reads and
+writes in every sub-step (the splash of Section III-C with the level order h,
+..., 0, ..., h), so FP64 runs replay the oracle exactly and every storage
+format gives bit-identical results in every form."""
 import numpy as np
 import pytest
 
@@ -40,7 +41,7 @@ def run(prob, dtype, sweep, depth=2, par=0.1, rounds=40, eps=1e-5, profile=0, **
 
 
 @pytest.mark.parametrize("depth", [0, 1, 2, 3])
-@pytest.mark.parametrize("sweep", [1, 2])
+@pytest.mark.parametrize("sweep", [1, 2, 3])
 def test_fp64_batch_replays_oracle(sweep, depth):
     """Every graph of an uneven batch matches the oracle run of that graph
     alone over 40 rounds: rounds, convergence, committed updates, beliefs.
@@ -63,7 +64,7 @@ def test_fp64_batch_replays_oracle(sweep, depth):
         assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < 1e-9, gi
 
 
-@pytest.mark.parametrize("sweep", [1, 2])
+@pytest.mark.parametrize("sweep", [1, 2, 3])
 def test_fp64_trace_replay(sweep):
     """Same splash roots every round and the same state after 60 rounds of a
     ragged 13 x 11 grid."""
@@ -92,13 +93,16 @@ def test_forms_bit_identical(name, dtype, depth):
     else:
         prob = synth.ising_grid_batch(40, 2.5, range(6))
     a = run(prob, dtype, 1, depth=depth)
-    b = run(prob, dtype, 2, depth=depth, profile=1 if depth == 3 else 0)
-    assert a[4]["sweep_ctas"] == 0 and b[4]["sweep_ctas"] > 0
-    keys = ("rounds", "committed_updates", "candidate_evals", "converged")
-    assert [a[0][k] for k in keys] == [b[0][k] for k in keys]
-    assert a[3] == b[3]
-    assert np.array_equal(a[1], b[1]), float(np.abs(a[1] - b[1]).max())
-    assert np.array_equal(a[2], b[2])
+    assert a[4]["sweep_ctas"] == 0 and a[4]["sweep_form"] == 0
+    for sweep, form in ((2, 1), (3, 2)):
+        b = run(prob, dtype, sweep, depth=depth, profile=1 if depth == 3 else 0)
+        assert b[4]["sweep_form"] == form
+        assert (b[4]["sweep_ctas"] > 0) == (form == 1)
+        keys = ("rounds", "committed_updates", "candidate_evals", "converged")
+        assert [a[0][k] for k in keys] == [b[0][k] for k in keys], sweep
+        assert a[3] == b[3], sweep
+        assert np.array_equal(a[1], b[1]), (sweep, float(np.abs(a[1] - b[1]).max()))
+        assert np.array_equal(a[2], b[2]), sweep
 
 
 def test_default_batch_shape_sweep_forms():
@@ -114,12 +118,15 @@ def test_default_batch_shape_sweep_forms():
     assert np.array_equal(auto[1], cluster[1])
     assert auto[0]["committed_updates"] == cluster[0]["committed_updates"]
     grid = run(prob, "f32", 2, rounds=6, select_path=2)
-    assert grid[4]["sweep_ctas"] == 0
+    assert grid[4]["sweep_ctas"] == 0 and grid[4]["sweep_form"] == 0
     assert np.array_equal(grid[1], auto[1])
+    pair_grid = run(prob, "f32", 3, rounds=6, select_path=2)
+    assert pair_grid[4]["sweep_form"] == 2
+    assert np.array_equal(pair_grid[1], auto[1])
 
 
 def test_bad_splash_sweep_rejected():
     prob = synth.ising_grid(5, 1.0, seed=0)
     with bp.Graph(prob) as g:
         with pytest.raises(bp.BPError):
-            g.run("rs", 0.1, splash_sweep=3)
+            g.run("rs", 0.1, splash_sweep=4)
