@@ -390,6 +390,8 @@ def main():
                     help="Residual Splash sweeps: 0 library's choice, 1 one launch per sub-step, "
                          "2 one cluster kernel per round, 3 one launch per sub-step with a commit "
                          "and an evaluation entry per thread")
+    ap.add_argument("--overlap-launches", type=int, default=0, choices=[0, 1, 2],
+                    help="programmatic dependent launches: 0 library's choice, 1 on, 2 off")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "q16", "f64"],
                     help="message storage (default: the workload's)")
     ap.add_argument("--autotune", default=None, choices=["none", "mapping", "mapping+p"],
@@ -434,7 +436,8 @@ def main():
         return bp.bp_default_options(msg_dtype=wl["dtype"], cuda_stream=stream.cuda_stream,
                                      graph_id_base=shard.graph_id_base(rank, G),
                                      kernel_variant=args.kernel_variant,
-                                     potts_path=args.potts_path, splash_sweep=args.splash_sweep, **kw)
+                                     potts_path=args.potts_path, splash_sweep=args.splash_sweep,
+                                     overlap_launches=args.overlap_launches, **kw)
 
     def one_step(profile: int):
         out = []

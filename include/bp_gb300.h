@@ -135,6 +135,11 @@ typedef struct {
                                  cluster selection; with the grid-wide selection it
                                  runs as 1), 3 = one launch per sub-step, a commit
                                  entry and an evaluation entry per thread */
+    int32_t overlap_launches; /* programmatic dependent launches of the per-round update,
+                                 decision, RnBP commit and sweep-step kernels (each
+                                 grid may be scheduled while the previous kernel
+                                 drains; it waits for it before reading run state):
+                                 0 = automatic (off), 1 = on, 2 = off */
 } bp_options;
 
 /* Phase timings and launch counts of the last bp_run. The timings are filled
@@ -165,6 +170,7 @@ typedef struct {
                                   ran one launch per sub-step (always filled) */
     int32_t sweep_form;        /* RS sweep form of the run: 0 per-sub-step launches, 1 cluster
                                   kernel, 2 per-sub-step launches with paired entries */
+    int32_t overlap_launches;  /* 1 when the run used programmatic dependent launches */
 } bp_profile;
 
 /* Fills *opt with the defaults listed above. */

@@ -60,7 +60,7 @@ class bp_options(ctypes.Structure):
                 ("time_budget_ms", ctypes.c_double), ("graph_id_base", ctypes.c_uint32),
                 ("kernel_variant", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("potts_path", ctypes.c_int32), ("select_path", ctypes.c_int32),
-                ("splash_sweep", ctypes.c_int32)]
+                ("splash_sweep", ctypes.c_int32), ("overlap_launches", ctypes.c_int32)]
 
 
 class bp_profile(ctypes.Structure):
@@ -71,7 +71,7 @@ class bp_profile(ctypes.Structure):
                 ("select_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double),
                 ("sweep_launches", ctypes.c_int64), ("select_ctas", ctypes.c_int32 * 2),
                 ("kernel_variant", ctypes.c_int32), ("sweep_ctas", ctypes.c_int32),
-                ("sweep_form", ctypes.c_int32)]
+                ("sweep_form", ctypes.c_int32), ("overlap_launches", ctypes.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -541,10 +541,11 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
                 break;
             }
             auto step_launch = rp.sweep_form == SWEEP_PAIR ? launch_splash_list_pair : launch_splash_list_step;
-            step_launch(dtype, dg, dr, -1, level_of(0), s);
+            const bool pdl = rp.pdl != 0;
+            step_launch(dtype, dg, dr, -1, level_of(0), s, pdl);
             for (int step = 0; step < 2 * h; ++step)
-                step_launch(dtype, dg, dr, level_of(step), level_of(step + 1), s);
-            step_launch(dtype, dg, dr, level_of(2 * h), -1, s);
+                step_launch(dtype, dg, dr, level_of(step), level_of(step + 1), s, pdl);
+            step_launch(dtype, dg, dr, level_of(2 * h), -1, s, pdl);
             kernels += any ? 2 * h + 2 : 0;
             break;
         }
@@ -654,6 +655,7 @@ static int build_run_params(const bp_graph *g, int32_t schedule, double parallel
     rp.ratio_threshold = opt.ratio_threshold;
     rp.seed = opt.seed;
     rp.graph_id_base = opt.graph_id_base;
+    rp.pdl = opt.overlap_launches == 1 ? 1 : 0;
     rp.splash_depth = opt.splash_depth;
     rp.rs_roots_mode = opt.rs_roots_mode;
     rp.record_trace = (opt.record_trace && opt.trace_capacity > 0 && schedule != BP_LBP) ? 1 : 0;
@@ -860,6 +862,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "select_path must be 0..2");
     if (opt.splash_sweep < 0 || opt.splash_sweep > 3)
         return fail(BP_ERR_INVALID_ARG, "splash_sweep must be 0..3");
+    if (opt.overlap_launches < 0 || opt.overlap_launches > 2)
+        return fail(BP_ERR_INVALID_ARG, "overlap_launches must be 0..2");
     if (opt.kernel_variant < 0 || opt.kernel_variant > 5)
         return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 5]");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
@@ -1123,6 +1127,7 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     prof.kernel_variant = variant;
     prof.sweep_ctas = rp.sweep_form == SWEEP_CLUSTER ? dg.sweep_c : 0;
     prof.sweep_form = rp.sweep_form;
+    prof.overlap_launches = rp.pdl;
     g->last_profile = prof;
     g->has_result = true;
     g->res_dtype = dtype;

@@ -81,6 +81,8 @@ struct RunParams {
     int32_t tc_path;          // shared-table update: 0 per-vertex, 1 tiles/CUDA cores, 2 tiles/tensor
                               // cores, 3 tiles/tensor cores with residual products
     int32_t sel_grid;         // grid-wide selection: bit 0 RBP, bit 1 RS (keys the captured rounds)
+    int32_t pdl;              // 1: the update, decision, RnBP commit and sweep-step kernels are
+                              // launched with programmatic stream serialization
     int32_t sweep_form;       // RS sweeps (binary, level lists): SWEEP_LIST one launch per
                               // sub-step, SWEEP_CLUSTER one cluster kernel per round over
                               // per-graph level lists, SWEEP_PAIR one launch per sub-step
@@ -136,6 +138,18 @@ __device__ __forceinline__ double graph_low_p(const DevRun &dr, const RunParams 
 {
     return dr.graph_p ? dr.graph_p[gg] : rp.low_p;
 }
+
+// Programmatic dependent launch: a grid launched with programmatic stream
+// serialization may start while its predecessor on the stream finishes; this
+// waits until every prerequisite grid has completed and its memory is
+// visible. In a grid launched without that attribute it returns at once.
+// Every thread of such a grid calls it before its first access to data that
+// a kernel of the run writes.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next grid on the stream (when launched with that attribute) be
+// scheduled once every block of this grid has executed it; that grid still
+// waits for this one's completion in griddep_wait. A no-op otherwise.
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
 
 // Deepest splash whose sweeps run over per-level vertex lists (binary messages).
 constexpr int LVL_MAX = 3;

@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval_bin(DevGraph g, DevRun dr, RunPa
 template <typename S, int MODE, int CACHE, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_eval_bin_pf(DevGraph g, DevRun dr, RunParams rp)
 {
+    griddep_launch_dependents();
     using A = typename Store<S>::A;
     using RT = typename ResidT<S>::T;
     const int first = blockIdx.x * blockDim.x;
@@ -72,8 +73,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_eval_bin_pf(DevGraph g, DevRun 
     unsigned int cnt = 0;
     if (i < g.n) {
         gg = g.gid[i];
-        valid = eval_vertex_bin_pf<S, MODE == MODE_CAND, CACHE>(g, dr, (RT *)dr.resid, i, gg,
-                                                                 eps_in(rp, (A)0), maxa, cnt);
+        valid = eval_vertex_bin_pf<S, MODE == MODE_CAND, CACHE, true>(g, dr, (RT *)dr.resid, i, gg,
+                                                                       eps_in(rp, (A)0), maxa, cnt);
+    } else {
+        griddep_wait();
     }
     reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
 }
@@ -209,6 +212,8 @@ __global__ void __launch_bounds__(BLOCK) k_eval_gen(DevGraph g, DevRun dr, RunPa
 // Per-graph decision after an evaluation (one warp per graph).
 __global__ void k_decide(DevGraph g, DevRun dr, RunParams rp)
 {
+    griddep_launch_dependents();
+    griddep_wait();
     const int gg = blockIdx.x;
     const int lane = threadIdx.x;
     if (gg == 0 && lane <= LVL_MAX && dr.lvl_cnt)
@@ -540,6 +545,8 @@ __global__ void __launch_bounds__(TILE_V) k_eval_bin_tiled(DevGraph g, DevRun dr
 template <typename S>
 __global__ void __launch_bounds__(TILE_V) k_commit_rnbp_tiled(DevGraph g, DevRun dr, RunParams rp)
 {
+    griddep_launch_dependents();
+    griddep_wait();
     using RT = typename ResidT<S>::T;
     __shared__ uint8_t s_src[TILE_E];
     __shared__ int s_g[TILE_V];
@@ -777,6 +784,8 @@ __global__ void __launch_bounds__(BLOCK) k_bfs_level_lists(DevGraph g, DevRun dr
 template <typename S>
 __global__ void __launch_bounds__(BLOCK, 6) k_splash_list_step(DevGraph g, DevRun dr, int Lc, int Le)
 {
+    griddep_launch_dependents();
+    griddep_wait();
     const int nc = Lc >= 0 ? dr.lvl_cnt[Lc] : 0;
     const int ne = Le >= 0 ? dr.lvl_cnt[Le] : 0;
     const int2 *lc = dr.lvl_list + (size_t)(Lc >= 0 ? Lc : 0) * g.n;
@@ -935,6 +944,30 @@ __global__ void __launch_bounds__(BLOCK) k_messages_gen(DevGraph g, DevRun dr, d
 // Host-side launchers.
 static inline int blocks_for(int n, int per_block) { return (n + per_block - 1) / per_block; }
 
+// Launch of a kernel that calls griddep_wait before touching run state: with
+// pdl, programmatic stream serialization lets its grid be scheduled while the
+// previous kernel on the stream drains (in a captured graph the edge becomes
+// a programmatic one); without it, an ordinary launch.
+template <typename... KArgs, typename... Args>
+static void launch_k(bool pdl, void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args... args)
+{
+    if (!pdl) {
+        kernel<<<grid, block, 0, s>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)block, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Calls BODY with S bound to the storage type of dtype (Q16 only for the
 // binary Ising layout, which the runtime enforces).
 #define BPG_DISPATCH4(dtype, BODY)                                   \
@@ -963,11 +996,11 @@ static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams
     const bool tiled = rp.variant == 2;
     if (rp.variant >= 4) {
         if (mode == MODE_LBP) {
-            if (rp.variant == 4) k_eval_bin_pf<S, MODE_LBP, 4, 6><<<nb, BLOCK, 0, s>>>(g, dr, rp);
-            else k_eval_bin_pf<S, MODE_LBP, 8, 4><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+            if (rp.variant == 4) launch_k(rp.pdl, k_eval_bin_pf<S, MODE_LBP, 4, 6>, nb, BLOCK, s, g, dr, rp);
+            else launch_k(rp.pdl, k_eval_bin_pf<S, MODE_LBP, 8, 4>, nb, BLOCK, s, g, dr, rp);
         } else {
-            if (rp.variant == 4) k_eval_bin_pf<S, MODE_CAND, 4, 6><<<nb, BLOCK, 0, s>>>(g, dr, rp);
-            else k_eval_bin_pf<S, MODE_CAND, 8, 4><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+            if (rp.variant == 4) launch_k(rp.pdl, k_eval_bin_pf<S, MODE_CAND, 4, 6>, nb, BLOCK, s, g, dr, rp);
+            else launch_k(rp.pdl, k_eval_bin_pf<S, MODE_CAND, 8, 4>, nb, BLOCK, s, g, dr, rp);
         }
         return;
     }
@@ -1019,14 +1052,14 @@ void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams
 
 void launch_decide(const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
 {
-    k_decide<<<g.G, 32, 0, s>>>(g, dr, rp);
+    launch_k(rp.pdl, k_decide, g.G, 32, s, g, dr, rp);
 }
 
 void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
 {
     if (g.n == 0)
         return;
-    BPG_DISPATCH4(dtype, (k_commit_rnbp_tiled<S><<<blocks_for(g.n, TILE_V), TILE_V, 0, s>>>(g, dr, rp)));
+    BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_tiled<S>, blocks_for(g.n, TILE_V), TILE_V, s, g, dr, rp)));
 }
 
 void launch_bfs_level(const DevGraph &g, const DevRun &dr, int d, cudaStream_t s)
@@ -1043,15 +1076,17 @@ void launch_bfs_level_lists(const DevGraph &g, const DevRun &dr, int d, int h, c
     k_bfs_level_lists<<<blocks_for(g.n, BLOCK), BLOCK, 0, s>>>(g, dr, d, h);
 }
 
-void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s)
+void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s,
+                             bool pdl)
 {
     if (g.n == 0)
         return;
     const int nb = std::min(blocks_for(g.n, BLOCK), 152 * 6);   // one wave at 6 blocks per SM
-    BPG_DISPATCH4(dtype, (k_splash_list_step<S><<<nb, BLOCK, 0, s>>>(g, dr, Lc, Le)));
+    BPG_DISPATCH4(dtype, (launch_k(pdl, k_splash_list_step<S>, nb, BLOCK, s, g, dr, Lc, Le)));
 }
 
-void launch_splash_list_pair(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s)
+void launch_splash_list_pair(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s,
+                             bool)
 {
     if (g.n == 0)
         return;

@@ -42,9 +42,13 @@ void launch_splash_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, 
 // the round's per-graph counts; the list steps pair commits and evaluations
 // as launch_splash_step does.
 void launch_bfs_level_lists(const DevGraph &g, const DevRun &dr, int d, int h, cudaStream_t s);
-void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s);
-// The same sub-step with a commit entry and an evaluation entry per thread.
-void launch_splash_list_pair(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s);
+// pdl: launch with programmatic stream serialization (RunParams::pdl).
+void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s,
+                             bool pdl = false);
+// The same sub-step with a commit entry and an evaluation entry per thread
+// (always launched without programmatic serialization).
+void launch_splash_list_pair(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s,
+                             bool pdl = false);
 // Residual Splash with one thread-block cluster per graph (binary messages,
 // depth <= LVL_MAX, cluster selection): every sub-step of a round's sweeps in
 // one launch over the per-graph level lists of k_select_rs. plan_sweep fills

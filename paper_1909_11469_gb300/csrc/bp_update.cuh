@@ -63,7 +63,9 @@ __device__ __forceinline__ void eval_vertex_bin(const DevGraph &g, const S *cur,
 // rev, q) are read before the graph's run status is known, so the message
 // gathers wait on one level of loads instead of three. gg = graph of vertex i.
 // Returns false (and touches nothing) when the graph is not running.
-template <typename S, bool STORE_R, int CACHE>
+// WAIT: call griddep_wait between the graph arrays (constant during a run)
+// and the first read of run state.
+template <typename S, bool STORE_R, int CACHE, bool WAIT = false>
 __device__ __forceinline__ bool eval_vertex_bin_pf(const DevGraph &g, const DevRun &dr,
                                                    typename ResidT<S>::T *R, int i, int gg,
                                                    typename Store<S>::A eps_a,
@@ -91,6 +93,8 @@ __device__ __forceinline__ bool eval_vertex_bin_pf(const DevGraph &g, const DevR
             qv[c] = q[beg + c];
         }
     }
+    if constexpr (WAIT)
+        griddep_wait();
     const int status = dr.gs[gg].status;
     const int cb = dr.gs[gg].cur;
     if (status != ST_RUNNING)

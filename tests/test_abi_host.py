@@ -48,7 +48,7 @@ int main(void) {
          offsetof(bp_run_stats, device_ms), offsetof(bp_run_stats, status),
          sizeof(bp_profile), offsetof(bp_profile, kernel_variant),
          sizeof(bp_tune_result), offsetof(bp_tune_result, ms_per_round_select),
-         offsetof(bp_options, splash_sweep), offsetof(bp_profile, sweep_form));
+         offsetof(bp_options, overlap_launches), offsetof(bp_profile, overlap_launches));
   return 0;
 }
 """)
@@ -60,7 +60,7 @@ int main(void) {
                     bp.bp_run_stats.device_ms.offset, bp.bp_run_stats.status.offset,
                     ctypes.sizeof(bp.bp_profile), bp.bp_profile.kernel_variant.offset,
                     ctypes.sizeof(bp.bp_tune_result), bp.bp_tune_result.ms_per_round_select.offset,
-                    bp.bp_options.splash_sweep.offset, bp.bp_profile.sweep_form.offset]
+                    bp.bp_options.overlap_launches.offset, bp.bp_profile.overlap_launches.offset]
 
 
 def test_status_strings(L):
