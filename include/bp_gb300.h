@@ -136,10 +136,11 @@ typedef struct {
                                  runs as 1), 3 = one launch per sub-step, a commit
                                  entry and an evaluation entry per thread */
     int32_t overlap_launches; /* programmatic dependent launches of the per-round update,
-                                 decision, RnBP commit and sweep-step kernels (each
-                                 grid may be scheduled while the previous kernel
-                                 drains; it waits for it before reading run state):
-                                 0 = automatic (off), 1 = on, 2 = off */
+                                 decision and RnBP commit kernels (each grid may be
+                                 scheduled while the previous kernel drains; it waits
+                                 for it before reading run state; the sweep steps
+                                 always launch without it): 0 = automatic (on), 1 =
+                                 on, 2 = off */
 } bp_options;
 
 /* Phase timings and launch counts of the last bp_run. The timings are filled

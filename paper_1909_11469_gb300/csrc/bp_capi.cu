@@ -541,11 +541,13 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
                 break;
             }
             auto step_launch = rp.sweep_form == SWEEP_PAIR ? launch_splash_list_pair : launch_splash_list_step;
-            const bool pdl = rp.pdl != 0;
-            step_launch(dtype, dg, dr, -1, level_of(0), s, pdl);
+            // sweep steps launch without programmatic serialization (measured
+            // slower between sweep steps); the next round's update still
+            // overlaps the last one, which lets its dependents launch early
+            step_launch(dtype, dg, dr, -1, level_of(0), s, false);
             for (int step = 0; step < 2 * h; ++step)
-                step_launch(dtype, dg, dr, level_of(step), level_of(step + 1), s, pdl);
-            step_launch(dtype, dg, dr, level_of(2 * h), -1, s, pdl);
+                step_launch(dtype, dg, dr, level_of(step), level_of(step + 1), s, false);
+            step_launch(dtype, dg, dr, level_of(2 * h), -1, s, false);
             kernels += any ? 2 * h + 2 : 0;
             break;
         }
@@ -655,7 +657,7 @@ static int build_run_params(const bp_graph *g, int32_t schedule, double parallel
     rp.ratio_threshold = opt.ratio_threshold;
     rp.seed = opt.seed;
     rp.graph_id_base = opt.graph_id_base;
-    rp.pdl = opt.overlap_launches == 1 ? 1 : 0;
+    rp.pdl = opt.overlap_launches == 2 ? 0 : 1;
     rp.splash_depth = opt.splash_depth;
     rp.rs_roots_mode = opt.rs_roots_mode;
     rp.record_trace = (opt.record_trace && opt.trace_capacity > 0 && schedule != BP_LBP) ? 1 : 0;

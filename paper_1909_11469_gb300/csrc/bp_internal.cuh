@@ -81,8 +81,8 @@ struct RunParams {
     int32_t tc_path;          // shared-table update: 0 per-vertex, 1 tiles/CUDA cores, 2 tiles/tensor
                               // cores, 3 tiles/tensor cores with residual products
     int32_t sel_grid;         // grid-wide selection: bit 0 RBP, bit 1 RS (keys the captured rounds)
-    int32_t pdl;              // 1: the update, decision, RnBP commit and sweep-step kernels are
-                              // launched with programmatic stream serialization
+    int32_t pdl;              // 1: the update, decision and RnBP commit kernels are launched
+                              // with programmatic stream serialization
     int32_t sweep_form;       // RS sweeps (binary, level lists): SWEEP_LIST one launch per
                               // sub-step, SWEEP_CLUSTER one cluster kernel per round over
                               // per-graph level lists, SWEEP_PAIR one launch per sub-step

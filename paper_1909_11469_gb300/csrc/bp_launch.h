@@ -42,7 +42,7 @@ void launch_splash_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, 
 // the round's per-graph counts; the list steps pair commits and evaluations
 // as launch_splash_step does.
 void launch_bfs_level_lists(const DevGraph &g, const DevRun &dr, int d, int h, cudaStream_t s);
-// pdl: launch with programmatic stream serialization (RunParams::pdl).
+// pdl: launch with programmatic stream serialization.
 void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s,
                              bool pdl = false);
 // The same sub-step with a commit entry and an evaluation entry per thread

@@ -260,17 +260,15 @@ __device__ __forceinline__ void splash_eval_vertex_b(const DevGraph &g, const De
     }
     const int end = g.row_ptr[i + 1];
     const int deg = end - beg;
+    // the source's level picks the buffer, so each incoming message is one
+    // load (reading both buffers next to the level measured slower: the
+    // sweep is bound by its scattered requests more than by their latency)
     A uin[CACHE];
 #pragma unroll
     for (int k = 0; k < CACHE; ++k) {
         if (k < deg) {
-            const A u0 = Store<S>::ld(b0 + rf[k], g.qscale);
-            if (Lc >= 0) {
-                const A u1 = Store<S>::ld((const S *)b1 + rf[k], g.qscale);
-                uin[k] = dr.level[rc[k]] == Lc ? u1 : u0;
-            } else {
-                uin[k] = u0;
-            }
+            const bool fresh = Lc >= 0 && dr.level[rc[k]] == Lc;
+            uin[k] = Store<S>::ld((fresh ? (const S *)b1 : b0) + rf[k], g.qscale);
         }
     }
     auto incoming = [&](int e) -> A {

@@ -1,8 +1,9 @@
-"""Programmatic dependent launches (bp_options.overlap_launches = 1): the
-per-round update, decision, RnBP commit and sweep-step grids may be scheduled
-while the previous kernel drains and wait for it before reading run state, so
-every result is bit-identical to ordinary launches, in captured rounds and in
-directly launched (profiled) rounds, and FP64 runs still replay the oracle."""
+"""Programmatic dependent launches (bp_options.overlap_launches, on by
+default): the per-round update, decision and RnBP commit grids may be
+scheduled while the previous kernel drains and wait for it before reading run
+state, so every result is bit-identical to ordinary launches (2 = off), in
+captured rounds and in directly launched (profiled) rounds, and FP64 runs
+still replay the oracle."""
 import numpy as np
 import pytest
 
@@ -34,8 +35,8 @@ def test_overlap_bit_identical(name, dtype, sched, par):
     prob = synth.ising_grid_batch(37, 2.5, range(5)) if name == "grids" else synth.er_batch(40, 3, n_max=800)
     a = run(prob, sched, par, dtype, 2)
     assert a[4]["overlap_launches"] == 0
-    for variant, profile in ((0, 0), (1, 0), (0, 1)):
-        b = run(prob, sched, par, dtype, 1, variant=variant, profile=profile)
+    for overlap, variant, profile in ((1, 0, 0), (1, 1, 0), (1, 0, 1), (0, 0, 0)):
+        b = run(prob, sched, par, dtype, overlap, variant=variant, profile=profile)
         assert b[4]["overlap_launches"] == 1
         keys = ("rounds", "committed_updates", "candidate_evals", "converged")
         assert [a[0][k] for k in keys] == [b[0][k] for k in keys], (variant, profile)
