@@ -73,19 +73,18 @@ L2_FLUSH_BYTES = 512 << 20          # > 126 MB of L2
 # message (s), + residual (4) in the frontier modes; per processed vertex
 # row_ptr, unary log-odds and graph id (12). s = 4 (FP32) or 2 (BF16, Q16).
 MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# message-update kernel from one ncu capture on the workload, with the kernel as
-# it is now (the summaries and commands are in profiles/). Captures are cold
-# (ncu flushes the caches), so they bound the warm traffic from above.
-# k_splash_list_step on the default workload: mean DRAM bytes of three captured
-# launches (26.8, 43.1 and 45.0 MB: the sub-steps move different level sizes).
-NCU_SWEEP_TRAFFIC = {("ising100x100_b2.5_50seeds", "f32", "per_sub_step"): (26.758e6 + 43.094e6 + 45.042e6) / 3}
-NCU_UPDATE_TRAFFIC = {
-    # k_eval_bin_pf<float, CAND, 4 edges, 6 blocks/SM>: 29.81 MB + 2.8 KB
-    ("ising100x100_b2.5_50seeds", "f32"): 29.806e6 + 2.8e3,
-    # k_eval_bin_pf<float, LBP, 4 edges, 6 blocks/SM>: 59.97 MB + 1.45 MB
-    ("ising1000x1000_b3", "f32"): 59.973e6 + 1.454e6,
-}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# roofline kernel from one ncu capture on the workload, valid only while the
+# kernel is unchanged since the capture (the summaries and commands are in
+# profiles/). Captures are cold (ncu flushes the caches), so they bound the warm
+# traffic from above. The captures of k_splash_list_step (mean of three
+# launches: 38.3 MB) and k_eval_bin_pf (default workload 29.8 MB, 1000x1000
+# LBP 61.4 MB) predate the current kernels -- the sweep evaluation now loads
+# one buffer per incoming message, and the update waits for its predecessor in
+# griddepcontrol.wait -- so both tables are empty and the traffic is null
+# until the kernels are captured again.
+NCU_SWEEP_TRAFFIC = {}
+NCU_UPDATE_TRAFFIC = {}
 BYTES_PER_VERTEX = 12
 
 
