@@ -127,8 +127,7 @@ struct bp_graph {
     int32_t max_graph_edges = 0;
     int32_t sel_plan[4][6];          // per message dtype: RBP CTAs, bytes, grid flag; RS the same
     bool sel_planned[4] = {false, false, false, false};
-    int32_t sweep_plan[4][2];        // per message dtype: cluster-sweep CTAs per graph, 1 = the
-                                     // estimate prefers the cluster sweep
+    int32_t sweep_c[4];              // per message dtype: CTAs per graph of the cluster sweep
     bool sweep_planned[4] = {false, false, false, false};
     // grid-wide selection buffers (allocated when a plan picks the grid kernels)
     GSelState *d_gsel = nullptr;
@@ -293,7 +292,7 @@ void apply_select_plan(const bp_graph *g, int dtype, int sel_grid_bits, DevGraph
         dg.sel_dyn[1] = g->sel_plan[dtype][4];
     }
     if (g->sweep_planned[dtype])
-        dg.sweep_c = g->sweep_plan[dtype][0];
+        dg.sweep_c = g->sweep_c[dtype];
     dg.sel_grid[0] = sel_grid_bits & 1;
     dg.sel_grid[1] = (sel_grid_bits >> 1) & 1;
 }
@@ -946,19 +945,18 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         // lists, or the cluster sweep over the per-graph lists that only the
         // cluster selection writes
         const bool cluster_ok = !(rp.sel_grid & 2);
-        if (cluster_ok && !g->sweep_planned[dtype]) {
-            plan_sweep(dtype, g->G, g->n, g->max_graph_vertices, g->sweep_plan[dtype]);
-            g->sweep_planned[dtype] = true;
-        }
         static const int32_t form_of[4] = {SWEEP_LIST, SWEEP_LIST, SWEEP_CLUSTER, SWEEP_PAIR};
         int32_t form = form_of[opt.splash_sweep];
-        if (opt.splash_sweep == 0 && cluster_ok && g->sweep_plan[dtype][1])
-            form = SWEEP_CLUSTER;
         if (form == SWEEP_CLUSTER && !cluster_ok)
             form = SWEEP_LIST;
+        if (form == SWEEP_CLUSTER) {
+            if (!g->sweep_planned[dtype]) {
+                g->sweep_c[dtype] = plan_sweep(dtype, g->G, g->n, g->max_graph_vertices);
+                g->sweep_planned[dtype] = true;
+            }
+            dg.sweep_c = g->sweep_c[dtype];
+        }
         rp.sweep_form = form;
-        if (form == SWEEP_CLUSTER)
-            dg.sweep_c = g->sweep_plan[dtype][0];
     }
     DevRun dr = dev_run(g);
     g->has_result = false;

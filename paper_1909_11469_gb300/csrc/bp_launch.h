@@ -51,10 +51,9 @@ void launch_splash_list_pair(int dtype, const DevGraph &g, const DevRun &dr, int
                              bool pdl = false);
 // Residual Splash with one thread-block cluster per graph (binary messages,
 // depth <= LVL_MAX, cluster selection): every sub-step of a round's sweeps in
-// one launch over the per-graph level lists of k_select_rs. plan_sweep fills
-// out[0] = CTAs per graph and out[1] = 1 when the automatic choice takes this
-// form (host occupancy queries; outside stream capture).
-void plan_sweep(int dtype, int G, int n, int max_gv, int32_t out[2]);
+// one launch over the per-graph level lists of k_select_rs. plan_sweep
+// returns its CTAs per graph (host occupancy queries; outside stream capture).
+int plan_sweep(int dtype, int G, int n, int max_gv);
 void launch_splash_sweep_cluster(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp,
                                  cudaStream_t s);
 void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int level_L, cudaStream_t s);

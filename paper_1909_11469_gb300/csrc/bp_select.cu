@@ -392,19 +392,17 @@ static int sweep_clusters(K kernel, int c, int G)
 // Cluster size of the sweep kernel: the c (1, 2, 4, 8) with the least
 // estimated time per sub-step -- per wave of resident clusters ~1 us (barrier)
 // plus ~1.2 us per pass of the cluster's c * SWEEP_THREADS threads over a
-// level of an average graph, plus the passes the largest graph adds. The
-// automatic choice between the two sweep forms stays with the per-sub-step
-// launches (out[1] = 0): on 50 graphs of 10,000 vertices they measured faster
-// (1035 vs 1146 ms per RS batch run of 10,000 rounds), since a sub-step of
-// either form is bound by the latency of its dependent loads rather than by
-// the launch, and a cluster's CTAs make more passes over a level than the
-// whole grid does.
+// level of an average graph, plus the passes the largest graph adds. (The
+// cluster sweep is taken on request only: on 50 graphs of 10,000 vertices the
+// per-sub-step launches measured faster, 1035 vs 1146 ms per RS batch run of
+// 10,000 rounds, since a sub-step of either form is bound by its dependent
+// loads rather than by the launch.)
 template <typename K>
-static void plan_sweep_kernel(K kernel, int G, int n, int max_gv, int32_t out[2])
+static int plan_sweep_kernel(K kernel, int G, int n, int max_gv)
 {
     const double avg = G > 0 ? (double)n / (double)G : 0.0;
     double best = 1e300;
-    out[0] = 1;
+    int best_c = 1;
     for (int c = 1; c <= 8; c *= 2) {
         const int ncl = sweep_clusters(kernel, c, G);
         if (ncl < 1)
@@ -416,19 +414,19 @@ static void plan_sweep_kernel(K kernel, int G, int n, int max_gv, int32_t out[2]
         const double t = waves * (1.0 + 1.2 * pass_avg) + 1.2 * (pass_max - pass_avg);
         if (t < best) {
             best = t;
-            out[0] = c;
+            best_c = c;
         }
     }
-    out[1] = 0;
+    return best_c;
 }
 
-void plan_sweep(int dtype, int G, int n, int max_gv, int32_t out[2])
+int plan_sweep(int dtype, int G, int n, int max_gv)
 {
     switch (dtype) {
-    case DT_F64: plan_sweep_kernel(k_splash_sweep_cluster<double>, G, n, max_gv, out); break;
-    case DT_F32: plan_sweep_kernel(k_splash_sweep_cluster<float>, G, n, max_gv, out); break;
-    case DT_BF16: plan_sweep_kernel(k_splash_sweep_cluster<__nv_bfloat16>, G, n, max_gv, out); break;
-    default: plan_sweep_kernel(k_splash_sweep_cluster<int16_t>, G, n, max_gv, out); break;
+    case DT_F64: return plan_sweep_kernel(k_splash_sweep_cluster<double>, G, n, max_gv);
+    case DT_F32: return plan_sweep_kernel(k_splash_sweep_cluster<float>, G, n, max_gv);
+    case DT_BF16: return plan_sweep_kernel(k_splash_sweep_cluster<__nv_bfloat16>, G, n, max_gv);
+    default: return plan_sweep_kernel(k_splash_sweep_cluster<int16_t>, G, n, max_gv);
     }
 }
 
