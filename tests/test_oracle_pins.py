@@ -84,6 +84,31 @@ def test_tree_exact_brute_force(orc, schedule, par):
     assert np.abs(res["beliefs"] - exact).max() < 1e-12
 
 
+@pytest.mark.parametrize("kind", ["ising_tree", "chain", "table_tree"])
+def test_rs_one_deep_splash_is_exact_on_a_tree(orc, kind):
+    """Residual Splash with a single root and a splash as deep as the tree
+    sweeps the levels from the leaves to the root and back out (Section III-A),
+    which on a tree is one exact collect-distribute pass: after ONE round every
+    belief equals the exact marginal. A sweep in the wrong order, a sub-step
+    that reads stale messages or a missing commit leaves it inexact, and so
+    does a splash too shallow to reach the leaves (checked as the control)."""
+    if kind == "ising_tree":
+        prob, exact = synth.ising_tree(12, 2.0, seed=11), None
+    elif kind == "chain":
+        prob = synth.paper_ising(1, 40, C=6.0, seed=3)
+        exact = _exact.chain_marginals(prob)
+    else:
+        prob, exact = synth.random_table_graph(9, 3, extra_edges=0, seed=4), None
+    if exact is None:
+        exact = _exact.brute_force_marginals(prob)
+    p_one_root = 1e-9   # k_v = clamp(ceil(p M), 1, n) = 1
+    deep = orc.run(prob, "rs", parallelism=p_one_root, eps=1e-300, max_rounds=1, splash_depth=prob.n - 1)
+    assert deep["rounds"] == 1
+    assert np.abs(deep["beliefs"] - exact).max() < 1e-12
+    shallow = orc.run(prob, "rs", parallelism=p_one_root, eps=1e-300, max_rounds=1, splash_depth=1)
+    assert np.abs(shallow["beliefs"] - exact).max() > 1e-6
+
+
 def test_tree_exact_tables_k3(orc):
     prob = synth.random_table_graph(9, 3, extra_edges=0, seed=4)
     res = orc.run(prob, "lbp", eps=1e-14, max_rounds=100)

@@ -208,6 +208,21 @@ def test_table_loopy_fp64_replay(k):
     assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F64
 
 
+@pytest.mark.parametrize("k", [3, 8])
+@pytest.mark.parametrize("sched,par", [("rbp", 0.1), ("rs", 0.1)])
+def test_table_frontier_schedules_fp64_replay(k, sched, par):
+    """k-state tables under RBP (k values copied per committed message) and
+    Residual Splash (k-state splash evaluation and commit per level)."""
+    prob = synth.random_table_graph(40, k, extra_edges=25, seed=k, pair_std=0.5)
+    ref = oracle.run(prob, sched, parallelism=par, eps=1e-6, max_rounds=30, trace_cap=30)
+    res = gpu_run(prob, sched, par, 1e-6, 30, "f64", trace=30)
+    assert res["stats"]["rounds"] == ref["rounds"]
+    assert np.array_equal(res["trace"], ref["trace"][:ref["rounds"]])
+    assert res["stats"]["committed_updates"] == ref["committed_updates"]
+    assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F64
+    assert np.abs(res["messages"] - ref["messages"]).max() < TOL_F64
+
+
 @pytest.mark.parametrize("dtype,tol", [("f32", TOL_F32), ("bf16", TOL_BF16)])
 @pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5)])
 def test_potts_trace_follow(dtype, tol, sched, par):

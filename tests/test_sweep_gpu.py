@@ -6,6 +6,8 @@ lists (bp_options.splash_sweep = 1 / 3 / 2). All perform the same reads and
 writes in every sub-step (the splash of Section III-C with the level order h,
 ..., 0, ..., h), so FP64 runs replay the oracle exactly and every storage
 format gives bit-identical results in every form."""
+import math
+
 import numpy as np
 import pytest
 
@@ -62,6 +64,69 @@ def test_fp64_batch_replays_oracle(sweep, depth):
         assert gst[gi][2] == ref["committed_updates"], gi
         v0, v1 = batch.graph_var_offsets[gi], batch.graph_var_offsets[gi + 1]
         assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < 1e-9, gi
+
+
+def selection_safe_rounds(m, depth, p, T, gid):
+    """Rounds of the oracle's RS run (at most T) before the first root
+    selection that rounding decides: the k-th largest vertex residual is below
+    1e-12 or within 1e-9 (relative) of the next. On trees a deep splash makes
+    messages exact, so many vertex residuals fall to rounding level (exact 0
+    in one FP64 implementation, 1e-16 in the other) while k roots are still
+    chosen among them; from that round on the two runs may splash other
+    vertices."""
+    kv = min(max(math.ceil(p * len(m.col)), 1), m.n)
+    row_ptr, rev = np.asarray(m.row_ptr), np.asarray(m.rev)
+    for r in range(T):
+        o = oracle.run(m, "rs", parallelism=p, eps=1e-5, max_rounds=r, splash_depth=depth, graph_id=gid)
+        if o["converged"]:
+            return T
+        _, res = oracle.evaluate(m, o["messages"])
+        vres = np.array([res[rev[row_ptr[v]:row_ptr[v + 1]]].max() if row_ptr[v + 1] > row_ptr[v] else 0.0
+                         for v in range(m.n)])
+        s = np.sort(vres)[::-1]
+        kth, nxt = s[kv - 1], (s[kv] if kv < m.n else -1.0)
+        if kth < 1e-12 or kth - nxt <= 1e-9 * kth:
+            return r
+    return T
+
+
+@pytest.mark.parametrize("depth", [4, 7, 16])
+def test_deep_splash_fp64_replays_oracle(depth):
+    """Splashes deeper than the level lists hold (h > 3) sweep by scanning the
+    level array: the uneven batch matches the oracle graph by graph for as many
+    rounds (at most 40) as every graph's root selection stays clear of rounding
+    (the 300-vertex chain: 9 rounds at h = 7, 6 at h = 16; at h = 7 and 16 its
+    run over 40 rounds did differ from the oracle's after that point)."""
+    members, batch = uneven_batch()
+    T = min(selection_safe_rounds(m, depth, 0.05, 40, gi) for gi, m in enumerate(members))
+    assert T >= 5
+    st, bel, msg, gst, prof = run(batch, "f64", 0, depth=depth, par=0.05, rounds=T)
+    assert prof["sweep_ctas"] == 0
+    for gi, m in enumerate(members):
+        ref = oracle.run(m, "rs", parallelism=0.05, eps=1e-5, max_rounds=T, splash_depth=depth,
+                         graph_id=gi)
+        assert gst[gi][1] == ref["rounds"], gi
+        assert bool(gst[gi][0]) == ref["converged"], gi
+        assert gst[gi][2] == ref["committed_updates"], gi
+        v0, v1 = batch.graph_var_offsets[gi], batch.graph_var_offsets[gi + 1]
+        assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < 1e-9, gi
+
+
+@pytest.mark.parametrize("kind", ["tree", "chain"])
+def test_one_deep_splash_is_exact_on_a_tree(kind):
+    """One root (p tiny) and a splash as deep as the tree: one round is a
+    collect-distribute pass, so the beliefs are the exact marginals."""
+    from tests import _exact
+    if kind == "tree":
+        prob = synth.ising_tree(12, 2.0, seed=11)
+        exact = _exact.brute_force_marginals(prob)
+    else:
+        prob = synth.paper_ising(1, 17, C=6.0, seed=3)
+        exact = _exact.chain_marginals(prob)
+    with bp.Graph(prob) as g:
+        st = g.run("rs", 1e-9, eps=1e-300, max_rounds=1, msg_dtype="f64", splash_depth=prob.n - 1)
+        assert st["rounds"] == 1
+        assert np.abs(g.beliefs() - exact).max() < 1e-12
 
 
 @pytest.mark.parametrize("sweep", [1, 2, 3])
