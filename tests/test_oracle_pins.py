@@ -247,6 +247,56 @@ def test_rnbp_full_p_commits_exactly_unconverged(orc):
         msg[r >= eps] = cand[r >= eps]
 
 
+def _residuals_eq2_eq4(prob, msg):
+    cand = np.array([_exact.message_eq2(prob, msg, e) for e in range(prob.m)])
+    return cand, np.abs(cand - msg).max(axis=1)
+
+
+def _top_k_ids(key, k):
+    """Ids of the k largest keys, ties to the smaller id (numpy lexsort)."""
+    order = np.lexsort((np.arange(key.shape[0]), -key))
+    top, rest = key[order[k - 1]], (key[order[k]] if k < key.shape[0] else -1.0)
+    assert top - rest > 1e-12 * max(top, 1e-300)   # the pin needs a clear k-th key
+    return np.sort(order[:k])
+
+
+def test_rbp_frontier_is_top_k_of_eq4_residuals(orc):
+    """RBP (Section III-A, reading R4): every round commits exactly the
+    k = ceil(p M) messages of largest Eq. 4 residual, ties to the smaller id;
+    residuals re-derived here from a direct Eq. 2 transcription."""
+    prob = synth.ising_grid(6, 2.0, seed=12)
+    p, T = 0.13, 4   # p M = 15.6: ceil and floor differ
+    k = int(np.ceil(p * prob.m))
+    res = orc.run(prob, "rbp", parallelism=p, eps=1e-9, max_rounds=T, trace_cap=T)
+    assert res["rounds"] == T and res["committed_updates"] == k * T
+    msg = np.full((prob.m, 2), 0.5)
+    for t in range(T):
+        cand, r = _residuals_eq2_eq4(prob, msg)
+        bits = np.unpackbits(res["trace"][t].view(np.uint8), bitorder="little")[:prob.m]
+        assert np.array_equal(np.flatnonzero(bits), _top_k_ids(r, k)), t
+        msg[bits.astype(bool)] = cand[bits.astype(bool)]
+    assert np.abs(res["messages"] - msg).max() < 1e-12
+
+
+def test_rs_roots_are_top_k_vertex_residuals(orc):
+    """Residual Splash (Section III-A, reading R5): the roots of round t + 1 are
+    the k_v = clamp(ceil(p M), 1, n) vertices of largest vertex residual (the
+    largest Eq. 4 residual of an incoming message) in the state after t
+    rounds, ties to the smaller id."""
+    prob = synth.ising_grid(7, 2.0, seed=13)
+    p, T = 0.05, 4
+    kv = min(max(int(np.ceil(p * prob.m)), 1), prob.n)
+    res = orc.run(prob, "rs", parallelism=p, eps=1e-9, max_rounds=T, trace_cap=T)
+    assert res["rounds"] == T
+    rev = np.asarray(prob.rev)
+    for t in range(T):
+        state = orc.run(prob, "rs", parallelism=p, eps=1e-9, max_rounds=t)["messages"]
+        _, r = _residuals_eq2_eq4(prob, state)
+        vres = np.array([r[rev[prob.row_ptr[v]:prob.row_ptr[v + 1]]].max() for v in range(prob.n)])
+        bits = np.unpackbits(res["trace"][t].view(np.uint8), bitorder="little")[:prob.n]
+        assert np.array_equal(np.flatnonzero(bits), _top_k_ids(vres, kv)), t
+
+
 def test_rnbp_edge_ratio_switch(orc):
     """p follows EdgeRatio: replay the frontier sizes from the trace with the
     Philox stream and check LowP is used exactly when N_t / N_{t-1} > 0.9."""
