@@ -675,7 +675,8 @@ def main():
             "config": {"workload": args.workload, "graphs_per_gpu": G, "autotune": tune,
                        "rounds_scale": args.rounds_scale, "direct_launch": bool(args.direct_launch),
                        "vertices": int(prob.n), "directed_messages": int(prob.m), "states": int(prob.k),
-                       "potts_path": args.potts_path,
+                       "potts_path": args.potts_path, "splash_sweep": args.splash_sweep,
+                       "overlap_launches": args.overlap_launches,
                        "eps": wl["eps"], "schedules": [f"{s}:{p}" for s, p in wl["schedules"]],
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"dp{world}" if world > 1 else "single"},
