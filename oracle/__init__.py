@@ -85,6 +85,8 @@ def lib():
             L.orc_top_k.restype = ctypes.c_int
             L.orc_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             L.orc_philox4x32_10.restype = None
+            L.orc_stored_logodds.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double]
+            L.orc_stored_logodds.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -192,6 +194,12 @@ def philox4x32_10(ctr, key):
     out = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_ptr(c), _ptr(kk), _ptr(out))
     return out
+
+
+def stored_logodds(storage: str, u: float, q16_scale: float = 0.0) -> float:
+    """The value an Ising log-odds u is stored as under the given storage mode."""
+    return float(lib().orc_stored_logodds({"f64": 0, "bf16": 1, "q16": 2}[storage], float(u),
+                                          float(q16_scale)))
 
 
 def run_batch(prob, **kw):

@@ -234,23 +234,31 @@ static double round_bf16(double v)
     return (double)f;
 }
 
+/* The value an Ising log-odds u is stored as: storage 0 keeps it, 1 rounds it
+ * to bfloat16, 2 to the nearest multiple of q16_scale (ties to even) clamped to
+ * +-32767 multiples. Exported so that tests can pin the rounding itself. */
+double orc_stored_logodds(int32_t storage, double u, double q16_scale)
+{
+    if (storage == 1)
+        return round_bf16(u);
+    if (storage == 2) {
+        double q = nearbyint(u / q16_scale);
+        if (q > 32767.0)
+            q = 32767.0;
+        if (q < -32767.0)
+            q = -32767.0;
+        return q * q16_scale;
+    }
+    return u;
+}
+
 static void store_round(const orc_problem *pb, const orc_params *pr, double *c)
 {
     int32_t k = pb->k;
     if (pr->storage == 0)
         return;
     if (pb->pair_kind == ORC_PAIR_ISING) {
-        double u = log(c[1]) - log(c[0]);
-        if (pr->storage == 1) {
-            u = round_bf16(u);
-        } else {
-            double q = nearbyint(u / pr->q16_scale);
-            if (q > 32767.0)
-                q = 32767.0;
-            if (q < -32767.0)
-                q = -32767.0;
-            u = q * pr->q16_scale;
-        }
+        double u = orc_stored_logodds(pr->storage, log(c[1]) - log(c[0]), pr->q16_scale);
         c[1] = 1.0 / (1.0 + exp(-u));
         c[0] = 1.0 / (1.0 + exp(u));
     } else {

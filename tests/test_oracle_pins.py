@@ -401,3 +401,107 @@ def test_rounded_storage_residual_zero_when_unchanged(orc):
     prob = synth.ising_tree(12, 1.0, seed=2)
     res = orc.run(prob, "lbp", eps=1e-12, max_rounds=200, storage="bf16")
     assert res["converged"] and res["final_max_residual"] == 0.0
+
+
+# --------------------------------------------------------------------------- storage rounding pins
+# Known answers derived by hand from the formats' definitions (not from the
+# oracle). bfloat16 keeps 8 significant bits: in the binade [2^e, 2^(e+1)) the
+# spacing is 2^(e-7), and a value halfway between two neighbours goes to the one
+# whose last kept mantissa bit is 0 (round to nearest, ties to even).
+#   1 + 2^-8          halfway between 1 (mantissa 0, even) and 1 + 2^-7 (1, odd)  -> 1
+#   1 + 3*2^-8        halfway between 1 + 2^-7 (1, odd) and 1 + 2^-6 (2, even)    -> 1 + 2^-6
+#   1 + 2^-8 + 2^-20  just above the first tie                                    -> 1 + 2^-7
+#   2 - 2^-8          halfway between 1 + 127/128 (127, odd) and 2 (carry into
+#                     the exponent, mantissa 0)                                   -> 2
+#   3 + 2^-7          in [2, 4) the spacing is 2^-6; halfway between 3 (mantissa
+#                     64, even) and 3 + 2^-6 (65, odd)                            -> 3
+#   0.3               float32(0.3) = 0.300000011920929; in [0.25, 0.5) the
+#                     spacing is 2^-9, 0.3 / 2^-9 = 153.6 -> 154 * 2^-9           -> 0.30078125
+# Negative values mirror. A truncating rounding fails the 2nd, 3rd, 4th and 6th
+# rows; rounding ties away from zero fails the 1st and 5th.
+BF16_KNOWN = [
+    (1 + 2.0 ** -8, 1.0),
+    (1 + 3 * 2.0 ** -8, 1 + 2.0 ** -6),
+    (1 + 2.0 ** -8 + 2.0 ** -20, 1 + 2.0 ** -7),
+    (2 - 2.0 ** -8, 2.0),
+    (3 + 2.0 ** -7, 3.0),
+    (float(np.float32(0.3)), 154 * 2.0 ** -9),
+]
+# Q16 with step s = 2^-12: the stored value is s * (nearest integer to u / s,
+# ties to even), clamped to +-32767 steps.
+#   2.5 s -> 2 s (tie, even)      3.5 s -> 4 s (tie, even)     2.75 s -> 3 s
+#   2.25 s -> 2 s                 40000 s -> 32767 s (clamp)
+# A truncating quantiser fails 3.5 s and 2.75 s; ties away from zero fails 2.5 s.
+Q16_STEP = 2.0 ** -12
+Q16_KNOWN = [(2.5, 2), (3.5, 4), (2.75, 3), (2.25, 2), (40000.0, 32767)]
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_bf16_rounding_known_answers(orc, sign):
+    for u, want in BF16_KNOWN:
+        assert orc.stored_logodds("bf16", sign * u) == sign * want, (u, want)
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_q16_rounding_known_answers(orc, sign):
+    for steps, want in Q16_KNOWN:
+        got = orc.stored_logodds("q16", sign * steps * Q16_STEP, Q16_STEP)
+        assert got == sign * want * Q16_STEP, (steps, want, got / Q16_STEP)
+
+
+def _copy_edge(t0: float, t1: float):
+    """Two vertices joined by one edge whose coupling beta = 30 makes each
+    message copy its source's field: with unary log-potentials (0, t) the
+    message's log-odds is log[(e^{-b} + e^{b+t}) / (e^{b} + e^{t-b})]
+    = t + O(e^{-2b + |t|}), i.e. t to far below FP64 resolution for |t| <= 10."""
+    row_ptr, col, rev = synth.csr_from_undirected(2, np.array([0]), np.array([1]))
+    return synth.Problem(2, 2, row_ptr, col, rev, np.array([0.0, t0, 0.0, t1], np.float32),
+                         synth.PAIR_ISING_BETA, np.array([30.0, 30.0], np.float32),
+                         np.array([0, 2], np.int64))
+
+
+def _stored_u(res):
+    m = res["messages"]
+    return np.log(m[:, 1]) - np.log(m[:, 0])
+
+
+def test_bf16_storage_rounding_through_a_run(orc):
+    """The rounding pinned above is the one a run stores: message 0 -> 1 carries
+    t = vertex 0's field, message 1 -> 0 carries vertex 1's. Round 1 commits the
+    rounded values, round 2 finds them unchanged (residual 0)."""
+    for u, want in BF16_KNOWN:
+        assert float(np.float32(u)) == u
+        res = orc.run(_copy_edge(u, -u), "lbp", eps=1e-15, max_rounds=5, storage="bf16")
+        assert res["converged"] and res["rounds"] == 1
+        got = _stored_u(res)
+        # edge 0 is 0 -> 1 (CSR row 0), edge 1 is 1 -> 0
+        assert abs(got[0] - want) < 1e-12 and abs(got[1] + want) < 1e-12, (u, want, got)
+
+
+def test_q16_storage_rounding_through_a_run(orc):
+    """Q16 through a run, on values clear of ties (a tie through a run is decided
+    by the FP64 rounding of the computed log-odds): 2.75 s -> 3 s, 2.25 s -> 2 s,
+    the clamp at 32767 s, and the mirrored negatives."""
+    for steps, want in [(2.75, 3), (2.25, 2), (3.6, 4), (40000.0, 32767)]:
+        t = steps * Q16_STEP
+        res = orc.run(_copy_edge(t, -t), "lbp", eps=1e-15, max_rounds=5, storage="q16",
+                      q16_scale=Q16_STEP)
+        assert res["converged"] and res["rounds"] == 1
+        got = _stored_u(res) / Q16_STEP
+        assert abs(got[0] - want) < 1e-6 and abs(got[1] + want) < 1e-6, (steps, want, got)
+
+
+def test_bf16_storage_of_k_state_logs(orc):
+    """k-state layout: each normalised log m(x) is rounded on its own (no
+    renormalisation). With a copying 3x3 table (log-potential 0 on the diagonal,
+    -200 elsewhere) and equal unaries the message is uniform, log m(x) = -ln 3 =
+    -1.0986...; in [1, 2) the bfloat16 spacing is 2^-7 and 1.0986 / 2^-7 = 140.6,
+    so the stored log is -141 / 128 (truncation would give -140 / 128)."""
+    k = 3
+    row_ptr, col, rev = synth.csr_from_undirected(2, np.array([0]), np.array([1]))
+    tab = np.full((2, k, k), -200.0, np.float32)
+    tab[:, np.arange(k), np.arange(k)] = 0.0
+    prob = synth.Problem(2, k, row_ptr, col, rev, np.full(2 * k, 0.25, np.float32),
+                         synth.PAIR_TABLE, tab.reshape(-1), np.array([0, 2], np.int64))
+    res = orc.run(prob, "lbp", eps=1e-15, max_rounds=5, storage="bf16")
+    assert np.abs(np.log(res["messages"]) + 141.0 / 128.0).max() < 1e-12
