@@ -47,7 +47,9 @@ typedef enum {
     BP_ERR_TIMEOUT = -6,       /* the wall-clock budget of bp_run ran out */
     BP_ERR_OOM = -7,           /* device or host allocation failed */
     BP_ERR_UNSUPPORTED = -8,   /* combination not implemented (e.g. k > 32) */
-    BP_ERR_NO_RESULT = -9      /* results requested before any bp_run */
+    BP_ERR_NO_RESULT = -9,     /* results requested before any bp_run */
+    BP_ERR_INTERNAL = -10      /* an internal consistency check failed (a library bug;
+                                  see bp_last_error) */
 } bp_status;
 
 /* Frontier generators (Algorithm 1, GenerateFrontier). */
@@ -192,7 +194,10 @@ typedef struct {
 } bp_tune_result;
 
 /*
- * Creates a handle for one graph. n_states = k (uniform over vertices,
+ * Creates a handle for one graph: the structure of the pairwise MRF of Eq. 1
+ * (Section II-A), one variable per vertex and one pairwise factor per
+ * undirected edge, stored as the adjacency list with edge and vertex ids that
+ * Section III-B describes. n_states = k (uniform over vertices,
  * 2 <= k <= 32). row_ptr has n_vars + 1 entries (row_ptr[0] = 0,
  * row_ptr[n_vars] = n_dir_edges), col and rev have n_dir_edges entries.
  * The CSR is validated (BP_ERR_BAD_GRAPH) and copied to the device.
@@ -234,11 +239,16 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind,
 int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_t max_rounds,
            const bp_options *opt, bp_run_stats *stats);
 
-/* Copies the beliefs of the last bp_run, [n_vars * k] float64, rows summing to 1. */
+/* Copies the beliefs of the last bp_run (Eq. 3: b_i(x) proportional to
+ * psi_i(x) times the product of the incoming messages, normalised in FP64),
+ * [n_vars * k] float64 (row = vertex), rows summing to 1. The caller owns out. */
 int bp_get_beliefs(const bp_graph *g, double *out);
 
-/* Copies the final messages of the last bp_run in the probability domain,
- * [n_dir_edges * k] float64 (row e = message on directed edge e). */
+/* Copies the final messages of the last bp_run (the committed state of the
+ * Eq. 2 updates, each normalised to sum 1 as Section II-A requires) in the
+ * probability domain, [n_dir_edges * k] float64 (row e = message on directed
+ * edge e); a 16-bit stored value is decoded exactly as the kernels decode it.
+ * The caller owns out. */
 int bp_get_messages(const bp_graph *g, double *out);
 
 /* Copies the residuals (Eq. 4: max-norm of the probability-domain change) of
@@ -275,19 +285,28 @@ int bp_get_trace(const bp_graph *g, uint32_t *out, int64_t capacity_words, int32
  * pointer owned by the caller: row_ptr [n_vars + 1] (int32), col and rev
  * [n_dir_edges], unary_log [n_vars * 2], beta [n_dir_edges] (layouts as for
  * bp_create_graph / BP_PAIR_ISING_BETA), beliefs [n_vars * 2] float64 output.
- * rounds_out / converged_out are optional HOST outputs. The run uses the same
- * kernels, rounds and convergence test as bp_run(BP_LBP) with msg_dtype BP_F32
- * and writes the same beliefs.
+ * rounds_out / converged_out are optional HOST outputs. The run evaluates with
+ * the thread-per-vertex update mapping (bp_options.kernel_variant = 1) in
+ * direct launches, with the same arithmetic, rounds and convergence test as
+ * bp_run(BP_LBP) with msg_dtype BP_F32 and that mapping, and writes the same
+ * beliefs bit for bit.
  *
- * Scratch: one static device array of about 5.0 MiB in the library, reserved
- * on every GPU that loads the library and held until the process exits. It
- * bounds the graph to at most 131072 vertices and 262144 directed edges
- * (larger graphs fail with BP_ERR_UNSUPPORTED). The first call on a device
- * looks up the array's device address with that device current (make that
- * first call before any stream capture). Each call resets the scratch it reads
- * and runs on cuda_stream (NULL = legacy default stream), synchronising it;
- * calls whose work overlaps on the GPU share the one array and race.
- * Inputs are validated on the device (BP_ERR_BAD_GRAPH, BP_ERR_NONFINITE).
+ * Scratch: one static device array of about 5.0 MiB in the library, held on
+ * every GPU where it has been set up until the process exits. It bounds the
+ * graph to at most 131072 vertices and 262144 directed edges (larger graphs
+ * fail with BP_ERR_UNSUPPORTED before anything is launched). The CUDA runtime
+ * loads the library's device code lazily, so the FIRST call on each device does
+ * the set-up: it loads this entry point's module, which places the array (and
+ * the module's code) in device memory, and looks up the array's device address
+ * with that device current. Make that first call (a small graph will do) before
+ * a framework reserves the GPU's memory and before any stream capture; later
+ * calls on that device allocate nothing. Each call clears the scratch it reads
+ * and runs on cuda_stream (NULL = legacy default stream), synchronising it.
+ * Every call on a device shares the one array: calls whose work overlaps on
+ * the GPU race on it, so callers must serialise them. Inputs are validated on
+ * the device (BP_ERR_BAD_GRAPH, BP_ERR_NONFINITE). A launch error is reported
+ * as BP_ERR_CUDA with the failing step; an error that earlier CUDA work of the
+ * calling thread left pending is consumed at entry and not reported.
  */
 int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_ptr, const int32_t *col,
                        const int32_t *rev, const float *unary_log, const float *beta, double eps,
@@ -358,6 +377,17 @@ int bp_autotune_parallelism(bp_graph *g, int32_t schedule, const double *candida
  */
 int bp_time_update(bp_graph *g, int32_t schedule, double parallelism, const bp_options *opt, int32_t launches,
                    double *ms_per_launch);
+
+/*
+ * bp_q16_scale - the Q16 storage step of the handle's potentials: the log-odds
+ * per integer unit that BP_Q16 messages use, s = (float)(2 max_e |beta_e| /
+ * 32767), or (float)(1 / 32767) when every beta is 0. *out (host) receives it.
+ * Binary Ising potentials only (BP_ERR_UNSUPPORTED otherwise);
+ * BP_ERR_NO_POTENTIALS before bp_set_potentials. The paper has no counterpart
+ * (Q16 is this library's storage format; the step is exported so that checkers
+ * emulate the same grid).
+ */
+int bp_q16_scale(const bp_graph *g, float *out);
 
 /* Copies the phase profile of the last bp_run (see bp_profile). */
 int bp_get_profile(const bp_graph *g, bp_profile *out);

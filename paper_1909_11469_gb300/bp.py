@@ -26,17 +26,13 @@ BP_ERR_TIMEOUT = -6
 BP_ERR_OOM = -7
 BP_ERR_UNSUPPORTED = -8
 BP_ERR_NO_RESULT = -9
+BP_ERR_INTERNAL = -10
 
 BP_LBP, BP_RBP, BP_RS, BP_RNBP = 0, 1, 2, 3
 SCHEDULES = {"lbp": BP_LBP, "rbp": BP_RBP, "rs": BP_RS, "rnbp": BP_RNBP}
 BP_F64, BP_F32, BP_BF16, BP_Q16 = 0, 1, 2, 3
 DTYPES = {"f64": BP_F64, "f32": BP_F32, "bf16": BP_BF16, "q16": BP_Q16}
 
-
-def q16_scale(pair_log) -> float:
-    """The Q16 log-odds step the library uses for Ising potentials pair_log."""
-    bmax = float(np.abs(np.asarray(pair_log, dtype=np.float64)).max()) if len(pair_log) else 0.0
-    return float(np.float32(2.0 * bmax / 32767.0)) if bmax > 0 else float(np.float32(1.0 / 32767.0))
 BP_PAIR_ISING_BETA, BP_PAIR_TABLE, BP_PAIR_SHARED = 0, 1, 2
 
 
@@ -111,6 +107,7 @@ _SIGNATURES = {
                                                ctypes.c_int32, _P, _P]),
     "bp_lbp_run_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
                                           ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P]),
+    "bp_q16_scale": (ctypes.c_int, [_P, _P]),
     "bp_graph_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "bp_destroy_graph": (None, [_P]),
     "bp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -333,6 +330,13 @@ def bp_lbp_run_noalloc(n_vars, n_dir_edges, row_ptr, col, rev, unary_log, beta, 
     return rounds.value, bool(conv.value)
 
 
+def bp_q16_scale(handle) -> float:
+    """The Q16 log-odds step of the handle's (binary Ising) potentials."""
+    out = ctypes.c_float()
+    _check(lib().bp_q16_scale(handle, ctypes.byref(out)), "bp_q16_scale")
+    return float(out.value)
+
+
 def bp_destroy_graph(handle) -> None:
     if handle:
         lib().bp_destroy_graph(handle)
@@ -363,6 +367,9 @@ class Graph:
 
     def graph_stats(self):
         return bp_get_graph_stats(self.handle)
+
+    def q16_scale(self):
+        return bp_q16_scale(self.handle)
 
     def profile(self):
         return bp_get_profile(self.handle)

@@ -1427,6 +1427,18 @@ int bp_time_update(bp_graph *g, int32_t schedule, double parallelism, const bp_o
     return BP_OK;
 }
 
+int bp_q16_scale(const bp_graph *g, float *out)
+{
+    if (!g || !out)
+        return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (!g->has_pot)
+        return fail(BP_ERR_NO_POTENTIALS, "bp_q16_scale before bp_set_potentials");
+    if (!(g->k == 2 && g->pair_kind == BP_PAIR_ISING_BETA))
+        return fail(BP_ERR_UNSUPPORTED, "Q16 storage needs binary Ising potentials");
+    *out = g->qscale;
+    return BP_OK;
+}
+
 int bp_get_profile(const bp_graph *g, bp_profile *out)
 {
     if (!g || !out)
@@ -1519,6 +1531,7 @@ const char *bp_status_string(int status)
     case BP_ERR_OOM: return "out of memory";
     case BP_ERR_UNSUPPORTED: return "unsupported configuration";
     case BP_ERR_NO_RESULT: return "no result available";
+    case BP_ERR_INTERNAL: return "internal consistency check failed";
     default: return "unknown status";
     }
 }

@@ -1050,6 +1050,17 @@ void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams
         BPG_DISPATCH3(dtype, (launch_eval_gen<S, 32>(g, dr, rp, mode, level_L, s)))
 }
 
+cudaError_t preload_lbp_f32_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_eval_bin<float, MODE_LBP>);
+    if (e == cudaSuccess)
+        e = cudaFuncGetAttributes(&fa, k_decide);
+    if (e == cudaSuccess)
+        e = cudaFuncGetAttributes(&fa, k_beliefs_bin<float>);
+    return e;
+}
+
 void launch_decide(const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
 {
     launch_k(rp.pdl, k_decide, g.G, 32, s, g, dr, rp);

@@ -15,6 +15,10 @@ void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s)
 void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
                  int kp, cudaStream_t s);
 void launch_decide(const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
+// Loads the kernels of an FP32 thread-per-vertex LBP run (update, decision,
+// beliefs) on the current device now rather than at their first launch (the
+// runtime loads device code lazily, and a load can allocate device memory).
+cudaError_t preload_lbp_f32_kernels();
 void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
 // One-time attribute set-up of the selection kernels (dynamic shared memory).
 void prepare_select_kernels();

@@ -8,9 +8,11 @@
 // They pass their inputs and outputs in device memory they own; the scratch
 // this run needs (two message buffers, exp(-2 beta), unary log-odds, the
 // per-run state and the convergence reductions) lives in one file-scope
-// static device array below, reserved by the CUDA runtime when the library's
-// module loads and held by every GPU that loads the library until the process
-// exits.
+// static device array below. The CUDA runtime loads device code lazily, so
+// the first call made on a device loads it (scratch_for_current_device loads
+// every kernel the call launches and looks up the array); from then on the
+// device holds the array until the process exits, and no call allocates
+// anything.
 #include "bp_gb300.h"
 #include "bp_internal.cuh"
 #include "bp_launch.h"
@@ -59,6 +61,10 @@ enum : unsigned { NA_BAD_GRAPH = 1u, NA_NONFINITE = 2u };
 
 // Checks the CSR and the potentials; every index is range-checked before it
 // is used, and a violation sets a bit in *err instead of touching memory.
+// Thread 0 also checks row_ptr[0] == 0 and row_ptr[n] == M; the other threads
+// do not wait for that check, which is safe because each thread checks its
+// own row range against [0, M] before reading col or rev, so a wrong first or
+// last entry is reported without any read outside the arrays.
 __global__ void k_na_validate(int32_t n, int32_t M, const int32_t *row_ptr, const int32_t *col,
                               const int32_t *rev, const float *unary, const float *beta, unsigned *err)
 {
@@ -155,6 +161,17 @@ int scratch_for_current_device(unsigned char **out)
         return na_fail(BP_ERR_UNSUPPORTED, "device ordinal beyond the scratch table");
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
+        // set-up: load the kernels this entry point launches (so that later
+        // calls load nothing) and look up the array, which loads its module
+        e = preload_lbp_f32_kernels();
+        if (e != cudaSuccess)
+            return na_fail(BP_ERR_CUDA, std::string("kernel load: ") + cudaGetErrorString(e));
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k_na_validate);
+        if (e == cudaSuccess)
+            e = cudaFuncGetAttributes(&fa, k_na_prepare);
+        if (e != cudaSuccess)
+            return na_fail(BP_ERR_CUDA, std::string("kernel load: ") + cudaGetErrorString(e));
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
@@ -184,6 +201,9 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
                            " directed edges)");
     if (!(eps > 0.0) || !std::isfinite(eps) || max_rounds < 0)
         return na_fail(BP_ERR_INVALID_ARG, "bp_lbp_run_noalloc: eps must be positive, max_rounds >= 0");
+    // An error that earlier CUDA work of this thread left pending belongs to
+    // that work: consume it so that the launch checks below see only ours.
+    (void)cudaGetLastError();
     unsigned char *sc = nullptr;
     int rc = scratch_for_current_device(&sc);
     if (rc != BP_OK)
@@ -195,6 +215,8 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
     if (e != cudaSuccess)
         return na_fail(BP_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     k_na_validate<<<(n + 255) / 256, 256, 0, s>>>(n, M, row_ptr, col, rev, unary_log, beta, d_err);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return na_fail(BP_ERR_CUDA, std::string("validation launch: ") + cudaGetErrorString(e));
     unsigned h_err = 0;
     e = cudaMemcpyAsync(&h_err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
@@ -208,6 +230,8 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
 
     const int pb = std::min((std::max(n, M) + 255) / 256, 152 * 8);
     k_na_prepare<<<pb, 256, 0, s>>>(n, M, unary_log, beta, sc);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return na_fail(BP_ERR_CUDA, std::string("set-up launch: ") + cudaGetErrorString(e));
 
     DevGraph g;
     memset(&g, 0, sizeof(g));
@@ -265,18 +289,25 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
             launch_decide(g, dr, rp, s);
         }
         launched += chunk;
+        // a failed launch stops here, before its zeroed reductions could be
+        // read as convergence by the next poll
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return na_fail(BP_ERR_CUDA, std::string("round launch: ") + cudaGetErrorString(e));
         e = cudaMemcpyAsync(&running, dr.n_running, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(s);
         if (e != cudaSuccess)
             return na_fail(BP_ERR_CUDA, std::string("round loop: ") + cudaGetErrorString(e));
+        // every graph stops after at most max_rounds + 1 evaluations, so a
+        // running graph past that point is a broken invariant, not a CUDA error
         if (running > 0 && launched > (int64_t)max_rounds + 1)
-            return na_fail(BP_ERR_CUDA, "bp_lbp_run_noalloc: round loop did not terminate");
+            return na_fail(BP_ERR_INTERNAL, "bp_lbp_run_noalloc: round loop did not terminate");
         chunk = std::min(chunk * 2, 64);
     }
     launch_beliefs(DT_F32, g, dr, 4, s);
     GState st;
-    e = cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return na_fail(BP_ERR_CUDA, std::string("beliefs launch: ") + cudaGetErrorString(e));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&st, dr.gs, sizeof(GState), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)

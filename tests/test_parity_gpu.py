@@ -35,6 +35,8 @@ def gpu_run(prob, sched, par=1.0, eps=1e-4, max_rounds=1000, dtype="f32", trace=
                    record_trace=1 if trace else 0, trace_capacity=trace, **opts)
         out = {"stats": st, "beliefs": g.beliefs(), "messages": g.messages(),
                "graph_stats": g.graph_stats()}
+        if dtype == "q16":
+            out["q16_scale"] = g.q16_scale()
         if trace:
             out["trace"] = g.trace(sched)
     return out
@@ -53,7 +55,7 @@ def follow(prob, sched, res, eps, storage="f64"):
     """Oracle run that commits the GPU's recorded frontiers."""
     rounds = res["stats"]["rounds"]
     kw = dict(eps=eps, storage=storage,
-              q16_scale=bp.q16_scale(prob.pair_log) if storage == "q16" else 0.0)
+              q16_scale=res["q16_scale"] if storage == "q16" else 0.0)
     if sched == "lbp":
         tr = all_ones_trace(prob.m, rounds)
         return oracle.run(prob, "lbp", trace_in=tr, trace_rounds=rounds, **kw)
