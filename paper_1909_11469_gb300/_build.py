@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbp_gb300.so")
 
 SOURCES = ["bp_capi.cu", "bp_kernels.cu", "bp_select.cu", "bp_select_grid.cu", "bp_persistent.cu",
-           "bp_potts_tc.cu", "bp_noalloc.cu"]
+           "bp_potts_tc.cu", "bp_noalloc.cu", "bp_stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

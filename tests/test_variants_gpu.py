@@ -1,7 +1,8 @@
 """The binary update mappings (thread per vertex, tiled edge quads, the
-persistent cluster kernel, the prefetching thread-per-vertex forms) compute
-the same arithmetic in the same order, so every schedule and storage format
-gives bit-identical beliefs, rounds and counters whichever mapping runs."""
+persistent cluster kernel, the prefetching thread-per-vertex forms, the
+streamed warp tiles) compute the same arithmetic in the same order, so every
+schedule and storage format gives bit-identical beliefs, rounds and counters
+whichever mapping runs."""
 import numpy as np
 import pytest
 
@@ -9,7 +10,7 @@ from paper_1909_11469_gb300 import bp, synth
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [1, 2, 3, 4, 5]
+VARIANTS = [1, 2, 3, 4, 5, 6]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -24,14 +25,69 @@ def built():
 def test_mappings_bit_identical(name, dtype, sched, par):
     prob = synth.ising_grid_batch(37, 2.5, range(5)) if name == "grid" else synth.er_batch(40, 3, n_max=800)
     results = {}
-    for v in VARIANTS:
+    variants = [v for v in VARIANTS if not (v == 6 and dtype == "f64")]   # 6: FP32 arithmetic only
+    for v in variants:
         with bp.Graph(prob) as g:
             st = g.run(sched, par, eps=1e-4, max_rounds=30, msg_dtype=dtype, seed=3, kernel_variant=v)
             results[v] = ((st["rounds"], st["committed_updates"], st["candidate_evals"]), g.beliefs(),
                           [(x["converged"], x["rounds"]) for x in g.graph_stats()])
-    key0, bel0, gs0 = results[VARIANTS[0]]
-    for v in VARIANTS[1:]:
+    key0, bel0, gs0 = results[variants[0]]
+    for v in variants[1:]:
         key, bel, gs = results[v]
         assert key == key0, (v, key, key0)
         assert gs == gs0, v
         assert np.array_equal(bel, bel0), (v, float(np.abs(bel - bel0).max()))
+
+
+def _star_batch(leaves_list, seed=0):
+    """Stars (one hub joined to `leaves` vertices) followed by isolated
+    vertices, as one batch: hubs at the tile edge limit, tiles cut by the
+    vertex limit, and runs of edgeless vertices between tiles."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for leaves in leaves_list:
+        n = leaves + 1 + 40
+        ei = np.zeros(leaves, np.int64)
+        ej = np.arange(1, leaves + 1, dtype=np.int64)
+        row_ptr, col, rev = synth.csr_from_undirected(n, ei, ej)
+        un = rng.uniform(-1, 1, n).astype(np.float32)
+        unary = np.stack([-un, un], 1).reshape(-1).astype(np.float32)
+        beta = np.zeros(col.shape[0], np.float32)
+        pos = synth._undirected_positions(row_ptr, col)
+        b = rng.uniform(-1.5, 1.5, pos.shape[0]).astype(np.float32)
+        beta[pos] = b
+        beta[rev[pos]] = b
+        probs.append(synth.Problem(n, 2, row_ptr, col, rev, unary, synth.PAIR_ISING_BETA, beta,
+                                   np.array([0, n], np.int64)))
+    return synth.concat_batch(probs)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "q16"])
+def test_streamed_tiles_edge_cases(dtype):
+    """The streamed warp tiles at their limits (a vertex with 128 out-edges
+    fills a tile; 127 and 1 edges share none), with edgeless vertices between
+    tiles and graphs without edges, give mapping 1's bits."""
+    prob = synth.concat_batch([_star_batch([128, 127, 1, 64]), synth.ising_grid(9, 1.0, seed=2),
+                               _star_batch([0, 3], seed=1)])
+    out = {}
+    for v in (1, 6):
+        with bp.Graph(prob) as g:
+            st = g.run("rnbp", 0.5, eps=1e-6, max_rounds=50, msg_dtype=dtype, seed=1, kernel_variant=v)
+            out[v] = (st["rounds"], st["committed_updates"], g.beliefs())
+    assert out[1][:2] == out[6][:2]
+    assert np.array_equal(out[1][2], out[6][2])
+
+
+def test_streamed_tiles_reject_high_degree():
+    """A vertex with more than 128 out-edges does not fit a warp tile: the
+    streamed mapping is refused, the automatic choice still runs."""
+    prob = _star_batch([129])
+    with bp.Graph(prob) as g:
+        with pytest.raises(bp.BPError) as ei:
+            g.run("lbp", 1.0, eps=1e-4, max_rounds=5, kernel_variant=6)
+        assert ei.value.code == bp.BP_ERR_UNSUPPORTED
+        g.run("lbp", 1.0, eps=1e-4, max_rounds=5)
+    with bp.Graph(synth.ising_grid(6, 1.0, seed=0)) as g:
+        with pytest.raises(bp.BPError) as ei:
+            g.run("lbp", 1.0, eps=1e-4, max_rounds=5, kernel_variant=6, msg_dtype="f64")
+        assert ei.value.code == bp.BP_ERR_UNSUPPORTED
