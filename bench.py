@@ -66,7 +66,7 @@ WORKLOADS = {
         kind="er_batch", n_graphs=4096, beta_max=3.0, lam_max=1.0, eps=1e-4, dtype="f32",
         schedules=[("rnbp", 0.5), ("lbp", 1.0)], autotune="mapping+p"),
 }
-DEFAULT_WORKLOAD = "ising100x100_b2.5_50seeds"
+DEFAULT_WORKLOAD = "er4096_b3"
 L2_FLUSH_BYTES = 512 << 20          # > 126 MB of L2
 # Algorithmic bytes of the full-evaluation kernel (binary Ising): per evaluated
 # message rev (4), incoming message (s), exp(-2 beta) (4), old message (s), new
@@ -143,7 +143,7 @@ def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kern
     achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
     mappings = sorted({pr.get("kernel_variant", 1) for _, _, _, pr, _ in step})
     names = {1: "k_eval_bin", 2: "k_eval_bin_tiled", 3: "k_eval_bin", 4: "k_eval_bin_pf<4 edges>",
-             5: "k_eval_bin_pf<8 edges>"}
+             5: "k_eval_bin_pf<8 edges>", 6: "k_eval_bin_stream"}
     kname = " / ".join(dict.fromkeys(names.get(v, "k_eval_bin") for v in mappings))
     in_step = {"achieved": achieved, "frac": (achieved / peak) if achieved else None,
                "avg_launch_us": 1e3 * eval_ms / max(eval_launches, 1)}
@@ -246,16 +246,26 @@ def round_cap(sched: str, p: float) -> int:
 
 
 def make_batch(wl, rank: int, world: int = 1):
+    """This rank's share of the workload and the Philox id of its first graph.
+    ER: one batch of n_graphs x world graphs (seed 0) split into contiguous
+    ranges balanced by directed edges (about n_graphs per rank: weak scaling),
+    each rank keeping the batch-wide graph ids. Grid batches: a disjoint seed
+    range per rank."""
     from paper_1909_11469_gb300 import shard, synth
     if wl["kind"] == "er_batch":
-        return synth.er_batch(wl["n_graphs"], seed=rank, beta_max=wl["beta_max"],
-                              lam_max=wl["lam_max"])
+        full = synth.er_batch(wl["n_graphs"] * world, seed=0, beta_max=wl["beta_max"], lam_max=wl["lam_max"])
+        if world == 1:
+            return full, 0
+        edges = np.diff(full.row_ptr[full.graph_var_offsets])
+        r = shard.balanced_ranges(edges, world)[rank]
+        return full.graphs(r.start, r.stop), r.start
     if wl["kind"] == "potts":
-        return synth.potts_grid(wl["side"], wl["k"], seed=rank)
+        return synth.potts_grid(wl["side"], wl["k"], seed=rank), 0
     seeds = shard.shard_seeds(rank, world, wl["n_seeds"])
     if wl["n_seeds"] == 1:
-        return synth.ising_grid(wl["side"], wl["beta_max"], rank, wl["lam_max"])
-    return synth.ising_grid_batch(wl["side"], wl["beta_max"], seeds, wl["lam_max"])
+        return synth.ising_grid(wl["side"], wl["beta_max"], rank, wl["lam_max"]), 0
+    batch = synth.ising_grid_batch(wl["side"], wl["beta_max"], seeds, wl["lam_max"])
+    return batch, shard.graph_id_base(rank, batch.n_graphs)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -308,42 +318,58 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(wl, budget_rounds: int, seed: int = 0):
-    """The FP64 oracle on one seed of the workload, each schedule capped at
-    budget_rounds rounds. Returns (committed updates, seconds)."""
+def oracle_sample(wl, budget_rounds: int, seconds: float, prob=None):
+    """The FP64 oracle, single thread, on a bounded sample of the workload,
+    each schedule capped at budget_rounds rounds. ER batch: every 16th graph
+    of the batch from graph 0 (its batch-wide Philox id), until `seconds` of
+    oracle time; grid workloads: seed 0. Returns (committed updates, seconds,
+    description)."""
     import oracle
     from paper_1909_11469_gb300 import synth
+
+    def one_graph(g, gid):
+        c, t = 0, 0.0
+        for sched, p in wl["schedules"]:
+            t0 = time.perf_counter()
+            r = oracle.run(g, sched, parallelism=p, eps=wl["eps"],
+                           max_rounds=min(budget_rounds, round_cap(sched, p)), seed=0, graph_id=gid)
+            t += time.perf_counter() - t0
+            c += r["committed_updates"]
+        return c, t
+
     if wl["kind"] == "er_batch":
-        prob = synth.er_batch(1, seed=seed, beta_max=wl["beta_max"], lam_max=wl["lam_max"])
-    elif wl["kind"] == "potts":
-        prob = synth.potts_grid(wl["side"], wl["k"], seed=seed)
+        batch = prob if prob is not None else make_batch(wl, 0, 1)[0]
+        committed, t, used = 0, 0.0, 0
+        for q in range(0, batch.n_graphs, 16):
+            c, dt = one_graph(batch.graph(q), q)
+            committed, t, used = committed + c, t + dt, used + 1
+            if t >= seconds:
+                break
+        return committed, t, (f"{used} graphs of the batch (every 16th from graph 0), each schedule capped at "
+                              f"{budget_rounds} rounds")
+    if wl["kind"] == "potts":
+        g = synth.potts_grid(wl["side"], wl["k"], seed=0)
     else:
-        prob = synth.ising_grid(wl["side"], wl["beta_max"], seed, wl["lam_max"])
-    committed, t = 0, 0.0
-    for sched, p in wl["schedules"]:
-        t0 = time.perf_counter()
-        r = oracle.run(prob, sched, parallelism=p, eps=wl["eps"],
-                       max_rounds=min(budget_rounds, round_cap(sched, p)), seed=seed)
-        t += time.perf_counter() - t0
-        committed += r["committed_updates"]
-    return committed, t
+        g = synth.ising_grid(wl["side"], wl["beta_max"], 0, wl["lam_max"])
+    c, t = one_graph(g, 0)
+    return c, t, f"seed 0 of the workload, each schedule capped at {budget_rounds} rounds"
 
 
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    rounds = 60
+    rounds, seconds = 60, 8.0
+    prob = make_batch(wl, 0, 1)[0] if wl["kind"] == "er_batch" else None
     for _ in range(args.warmup):
-        oracle_sample(wl, rounds)
-    committed, secs = 0, 0.0
+        oracle_sample(wl, rounds, 1.0, prob)
+    committed, secs, desc = 0, 0.0, ""
     for _ in range(args.steps):
-        c, t = oracle_sample(wl, rounds)
+        c, t, desc = oracle_sample(wl, rounds, seconds, prob)
         committed += c
         secs += t
     value = committed / secs
-    sample = (f"one {wl['side']}x{wl['side']} seed per step, each schedule capped at "
-              f"{rounds} rounds, FP64 oracle, single thread")
+    sample = f"{desc}, FP64 oracle, single thread, per step"
     line = {
         "metric": "message updates/sec", "value": value, "unit": "message updates/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -380,7 +406,7 @@ def main():
     ap.add_argument("--direct-launch", action="store_true",
                     help="timed steps launch kernels directly instead of replaying CUDA graphs "
                          "(profiler passes only)")
-    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
+    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="binary update mapping (0 = library's choice)")
     ap.add_argument("--potts-path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="shared-table update: 0 automatic, 1 CUDA cores, 2 tensor cores BF16, "
@@ -423,7 +449,7 @@ def main():
     __graft_entry__.build()
     from paper_1909_11469_gb300 import bp
 
-    prob = make_batch(wl, rank, world)
+    prob, gid_base = make_batch(wl, rank, world)
     stream = torch.cuda.current_stream()
     g = bp.Graph(prob)
     G = prob.n_graphs
@@ -433,7 +459,7 @@ def main():
 
     def opts(**kw):
         return bp.bp_default_options(msg_dtype=wl["dtype"], cuda_stream=stream.cuda_stream,
-                                     graph_id_base=shard.graph_id_base(rank, G),
+                                     graph_id_base=gid_base,
                                      kernel_variant=args.kernel_variant,
                                      potts_path=args.potts_path, splash_sweep=args.splash_sweep,
                                      overlap_launches=args.overlap_launches, **kw)
@@ -544,8 +570,9 @@ def main():
                 pass
         update_roofline, phase = eval_roofline(prof_step, wl["dtype"], peak, peak_src, prob.k, kname,
                                                isolated=iso, n=prob.n, m=prob.m)
-        if prob.k == 2 and all(pr.get("kernel_variant") == 4 for _, _, _, pr, _ in prof_step):
-            update_roofline["traffic"] = NCU_UPDATE_TRAFFIC.get((args.workload, wl["dtype"]))
+        variants = {pr.get("kernel_variant") for _, _, _, pr, _ in prof_step}
+        if prob.k == 2 and len(variants) == 1:
+            update_roofline["traffic"] = NCU_UPDATE_TRAFFIC.get((args.workload, wl["dtype"], variants.pop()))
         phase["select_ms"] = sum(pr["select_ms"] for _, _, _, pr, _ in prof_step)
         phase["sweep_ms"] = sum(pr["sweep_ms"] for _, _, _, pr, _ in prof_step)
         # the dominant kernel class of the step gets the roofline
@@ -661,10 +688,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        c, t = oracle_sample(wl, 300)
+        c, t, desc = oracle_sample(wl, 300, 12.0, prob)
         cpu = {"value": c / t, "unit": "message updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"seed 0 of the workload, each schedule capped at 300 rounds "
-                         f"({t:.1f} s of FP64 oracle, single thread)"}
+               "sample": f"{desc} ({t:.1f} s of FP64 oracle, single thread)"}
 
     if rank == 0:
         line = {

@@ -63,11 +63,19 @@ typedef enum {
 /* Storage type of the log-domain messages (arithmetic is FP32, or FP64 for BP_F64).
  * Binary Ising messages (k = 2, BP_PAIR_ISING_BETA) are stored as one log-odds
  * value u = log m(1) - log m(0); other messages as k values log m(x).
+ * BP_BF16: k-state logs are rounded to bfloat16. A binary Ising log-odds is
+ * stored in the exponent of a bfloat16 word: the word nearest to
+ * w = 2^(|u| / b - 125) with the sign of u, b = the smallest power of two
+ * >= 2 max_e |beta_e| / 250.
+ * An Ising message satisfies |u| <= 2 |beta|, so w stays in [2^-125, 2^125],
+ * and the word's exponent and mantissa bits form a logarithmic code of |u|
+ * whose step is at most b / 128 (a plain bfloat16 log-odds would have a
+ * relative step of 2^-7 |u|, too coarse for beliefs within 2e-3).
  * BP_Q16 (binary Ising only) stores u as a signed 16-bit integer q with
- * u = q * s, s = (float)(2 max_e |beta_e| / 32767): an Ising message satisfies
- * |u| <= 2 |beta|, so the range is never exceeded and the step is uniform.
- * With BF16 and Q16 a residual compares rounded candidates with the stored
- * messages, so an unchanged stored value has residual 0. */
+ * u = q * s, s = (float)(2 max_e |beta_e| / 32767); the step is uniform.
+ * bp_storage_scale returns b and s. With BF16 and Q16 a residual compares
+ * rounded candidates with the stored messages, so an unchanged stored value
+ * has residual 0. */
 typedef enum { BP_F64 = 0, BP_F32 = 1, BP_BF16 = 2, BP_Q16 = 3 } bp_msg_dtype;
 
 /* Pairwise potential layouts, as natural logs theta = log psi (Eq. 1). */
@@ -117,7 +125,11 @@ typedef struct {
                                  kernel: one thread-block cluster per graph runs all of
                                  its rounds in a single launch, 4 = one thread per vertex
                                  with the graph arrays of 4 edges prefetched in parallel
-                                 with the graph's status, 5 = the same with 8 edges */
+                                 with the graph's status, 5 = the same with 8 edges,
+                                 6 = streamed tiles: warp tiles of <= 128 edges staged in
+                                 shared memory by bulk copies from a producer warp, one
+                                 lane per edge (FP32 / BF16 / Q16 messages, vertices with
+                                 <= 128 out-edges; BP_ERR_UNSUPPORTED otherwise) */
     int32_t profile;          /* 1: time every round's phases with CUDA events (default 0) */
     int32_t potts_path;       /* shared-table (BP_PAIR_SHARED) update, FP32/BF16 storage,
                                  tiles of <= 128 edges: 0 = automatic (3 for k >= 16,
@@ -181,12 +193,12 @@ void bp_default_options(bp_options *opt);
 
 /* Result of bp_autotune. */
 typedef struct {
-    int32_t kernel_variant;    /* the fastest mapping measured (1 to 5) */
+    int32_t kernel_variant;    /* the fastest mapping measured (1 to 6) */
     int32_t size_class;        /* the key it was recorded under: schedule (bits 0-1), msg_dtype
                                   (2-3), floor(log2(n_vars / n_graphs)) (4-8),
                                   floor(log2(n_graphs)) (9-13), largest vertex degree
                                   <= 4 / <= 8 / more (14-15) */
-    double ms_per_round[6];    /* measured device ms per round, index = mapping; 0 = not tried */
+    double ms_per_round[8];    /* measured device ms per round, index = mapping (1 to 6); 0 = not tried */
     int32_t select_path;       /* RBP / RS: the faster selection path measured (1 cluster, 2
                                   grid-wide; bp_options.select_path), 0 for other schedules */
     double ms_per_round_select[3]; /* device ms per round with the chosen mapping, index =
@@ -319,8 +331,8 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
  * (it runs one kernel design); the batch configuration of arbitrary graph
  * sizes calls for a tuned choice per size class.
  *
- * For each mapping (1, 2, 4, 5, and 3 when the handle holds more than one
- * graph) it runs bp_run(schedule, parallelism, eps, trial_rounds, opt) twice
+ * For each mapping (1, 2, 4, 5, 6 where the streamed tiles apply, and 3 when
+ * the handle holds more than one graph) it runs bp_run(schedule, parallelism, eps, trial_rounds, opt) twice
  * (the first run captures the rounds; the second is timed by its device_ms)
  * and records the mapping with the least device time per round in a
  * process-wide table under the size class (see bp_tune_result); for RBP and
@@ -379,15 +391,17 @@ int bp_time_update(bp_graph *g, int32_t schedule, double parallelism, const bp_o
                    double *ms_per_launch);
 
 /*
- * bp_q16_scale - the Q16 storage step of the handle's potentials: the log-odds
- * per integer unit that BP_Q16 messages use, s = (float)(2 max_e |beta_e| /
- * 32767), or (float)(1 / 32767) when every beta is 0. *out (host) receives it.
- * Binary Ising potentials only (BP_ERR_UNSUPPORTED otherwise);
- * BP_ERR_NO_POTENTIALS before bp_set_potentials. The paper has no counterpart
- * (Q16 is this library's storage format; the step is exported so that checkers
- * emulate the same grid).
+ * bp_storage_scale - the scale of a 16-bit message format on the handle's
+ * binary Ising potentials (see bp_msg_dtype), with B = max_e |beta_e|:
+ * BP_Q16: the log-odds per integer unit, s = (float)(2 B / 32767);
+ * BP_BF16: the log-odds per unit of log2 of the stored word, b = the
+ * smallest power of two >= 2 B / 250. When every beta is 0, B = 1/2 is used. *out (host)
+ * receives it. BP_ERR_INVALID_ARG for other formats, BP_ERR_UNSUPPORTED for
+ * other potential layouts, BP_ERR_NO_POTENTIALS before bp_set_potentials. The
+ * paper has no counterpart (the formats are this library's message storage;
+ * the scale is exported so that checkers emulate the same grid).
  */
-int bp_q16_scale(const bp_graph *g, float *out);
+int bp_storage_scale(const bp_graph *g, int32_t msg_dtype, float *out);
 
 /* Copies the phase profile of the last bp_run (see bp_profile). */
 int bp_get_profile(const bp_graph *g, bp_profile *out);

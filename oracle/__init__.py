@@ -24,6 +24,7 @@ _LIB_PATH = os.path.join(_HERE, "libbporacle.so")
 
 LBP, RBP, RS, RNBP = 0, 1, 2, 3
 SCHEDULES = {"lbp": LBP, "rbp": RBP, "rs": RS, "rnbp": RNBP}
+STORAGE = {"f64": 0, "bf16": 1, "q16": 2, "bf16_plain": 3}
 
 
 class OrcProblem(ctypes.Structure):
@@ -41,7 +42,7 @@ class OrcParams(ctypes.Structure):
                 ("splash_depth", ctypes.c_int32), ("rs_roots_mode", ctypes.c_int32),
                 ("trace_in", ctypes.c_void_p), ("trace_rounds", ctypes.c_int32),
                 ("trace_out", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("q16_scale", ctypes.c_double)]
+                ("storage", ctypes.c_int32), ("storage_scale", ctypes.c_double)]
 
 
 class OrcStats(ctypes.Structure):
@@ -111,10 +112,11 @@ class _Bound:
 
 def run(prob, schedule="lbp", parallelism=1.0, eps=1e-4, max_rounds=1000, seed=0,
         graph_id=0, high_p=1.0, ratio_threshold=0.9, splash_depth=2, rs_roots_mode=0,
-        trace_in=None, trace_rounds=0, trace_cap=0, storage="f64", q16_scale=0.0):
+        trace_in=None, trace_rounds=0, trace_cap=0, storage="f64", storage_scale=0.0):
     """Run one graph (prob must hold a single graph). Returns a dict with beliefs
     [n, k], messages [M, k] (probability domain), stats and the selected trace.
-    storage: "f64" (exact), "bf16" or "q16" (emulated 16-bit message storage)."""
+    storage: "f64" (exact), "bf16", "q16" or "bf16_plain" (emulated 16-bit message
+    storage; storage_scale is the library's scale of that format, bp_storage_scale)."""
     sched = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     b = _Bound(prob)
     n, k, m = int(prob.n), int(prob.k), int(b.col.shape[0])
@@ -129,7 +131,7 @@ def run(prob, schedule="lbp", parallelism=1.0, eps=1e-4, max_rounds=1000, seed=0
                        int(graph_id), float(high_p), float(ratio_threshold), int(splash_depth),
                        int(rs_roots_mode), _ptr(tin) if tin is not None else None,
                        int(trace_rounds), _ptr(tout) if trace_cap > 0 else None, int(trace_cap),
-                       {"f64": 0, "bf16": 1, "q16": 2}[storage], float(q16_scale))
+                       STORAGE[storage], float(storage_scale))
     beliefs = np.zeros(n * k + 1, dtype=np.float64)
     msgs = np.zeros(m * k + 1, dtype=np.float64)
     st = OrcStats()
@@ -196,10 +198,9 @@ def philox4x32_10(ctr, key):
     return out
 
 
-def stored_logodds(storage: str, u: float, q16_scale: float = 0.0) -> float:
+def stored_logodds(storage: str, u: float, scale: float = 0.0) -> float:
     """The value an Ising log-odds u is stored as under the given storage mode."""
-    return float(lib().orc_stored_logodds({"f64": 0, "bf16": 1, "q16": 2}[storage], float(u),
-                                          float(q16_scale)))
+    return float(lib().orc_stored_logodds(STORAGE[storage], float(u), float(scale)))
 
 
 def run_batch(prob, **kw):

@@ -74,9 +74,12 @@ typedef struct {
     int32_t trace_rounds;
     uint32_t *trace_out;     /* optional: frontier bitmask per round, as selected */
     int32_t trace_cap;
-    int32_t storage;         /* 0: exact FP64; 1: BF16 rounding of the stored log value;
-                                2: 16-bit fixed-point log-odds (Ising only) */
-    double q16_scale;        /* storage 2: log-odds step of one integer unit */
+    int32_t storage;         /* 0: exact FP64; 1: BF16 (Ising: the log-odds in the exponent
+                                code below; other layouts: each log m(x) rounded);
+                                2: 16-bit fixed-point log-odds (Ising only);
+                                3: BF16 rounding of the plain Ising log-odds */
+    double storage_scale;    /* storage 1 (Ising): log-odds per unit of log2 of the stored
+                                word; storage 2: log-odds step of one integer unit */
 } orc_params;
 
 typedef struct {
@@ -218,12 +221,22 @@ static void message_update(const orc_model *md, const double *msg, int64_t e, do
  * is committed then goes through the same rounding as the stored word, and
  * residuals compare rounded candidates with rounded current messages, so a
  * message whose stored value does not change has residual 0.
- *   BF16: the stored quantity is rounded to float, then to bfloat16 (round to
- *   nearest, ties to even). For the Ising layout (k = 2, beta potentials) the
- *   stored quantity is the log-odds u = log m(1) - log m(0); otherwise it is
- *   log m(x) of each state (not renormalised after rounding).
- *   Q16: Ising log-odds rounded to the nearest multiple of q16_scale, clamped
- *   to +-32767 multiples. */
+ *   BF16, Ising layout (k = 2, beta potentials): the stored word is the
+ *   bfloat16 value nearest to w = 2^(|u| / b - 125), with the sign of the
+ *   log-odds u = log m(1) - log m(0) and b = storage_scale. With b >= 2
+ *   max|beta| / 250 every |u| <= 2 max|beta| maps into [2^-125, 2^125], so the
+ *   word's 8 exponent bits and 7 mantissa bits form a logarithmic code of |u|
+ *   whose step is at most b / 128 (a step of log2 w is at most 2^-7). The value is
+ *   rounded to float, then to bfloat16, and read back as |u| = (log2 |w| +
+ *   125) b.
+ *   BF16 plain (storage 3, Ising layout): the log-odds itself rounded to float,
+ *   then to bfloat16; its step is 2^-7 |u| (relative), which the exponent code
+ *   above replaces by a uniform one.
+ *   BF16, other layouts: log m(x) of each state rounded to bfloat16 (not
+ *   renormalised after rounding).
+ *   Q16: Ising log-odds rounded to the nearest multiple of storage_scale,
+ *   clamped to +-32767 multiples.
+ * Rounding to bfloat16 keeps 8 significant bits, to nearest, ties to even. */
 static double round_bf16(double v)
 {
     float f = (float)v;
@@ -234,21 +247,27 @@ static double round_bf16(double v)
     return (double)f;
 }
 
-/* The value an Ising log-odds u is stored as: storage 0 keeps it, 1 rounds it
- * to bfloat16, 2 to the nearest multiple of q16_scale (ties to even) clamped to
- * +-32767 multiples. Exported so that tests can pin the rounding itself. */
-double orc_stored_logodds(int32_t storage, double u, double q16_scale)
+/* The value an Ising log-odds u is stored as: storage 0 keeps it, 1 codes it
+ * in the exponent of a bfloat16 word, 2 rounds it to the nearest multiple of
+ * the scale (ties to even) clamped to +-32767 multiples, 3 rounds it to
+ * bfloat16. Exported so that tests can pin the rounding itself. */
+double orc_stored_logodds(int32_t storage, double u, double scale)
 {
-    if (storage == 1)
-        return round_bf16(u);
+    if (storage == 1) {
+        double w = round_bf16(exp2(fabs(u) / scale - 125.0));
+        double a = (log2(w) + 125.0) * scale;
+        return u < 0.0 ? -a : a;
+    }
     if (storage == 2) {
-        double q = nearbyint(u / q16_scale);
+        double q = nearbyint(u / scale);
         if (q > 32767.0)
             q = 32767.0;
         if (q < -32767.0)
             q = -32767.0;
-        return q * q16_scale;
+        return q * scale;
     }
+    if (storage == 3)
+        return round_bf16(u);
     return u;
 }
 
@@ -258,7 +277,7 @@ static void store_round(const orc_problem *pb, const orc_params *pr, double *c)
     if (pr->storage == 0)
         return;
     if (pb->pair_kind == ORC_PAIR_ISING) {
-        double u = orc_stored_logodds(pr->storage, log(c[1]) - log(c[0]), pr->q16_scale);
+        double u = orc_stored_logodds(pr->storage, log(c[1]) - log(c[0]), pr->storage_scale);
         c[1] = 1.0 / (1.0 + exp(-u));
         c[0] = 1.0 / (1.0 + exp(u));
     } else {

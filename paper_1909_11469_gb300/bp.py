@@ -77,7 +77,7 @@ class bp_profile(ctypes.Structure):
 
 class bp_tune_result(ctypes.Structure):
     _fields_ = [("kernel_variant", ctypes.c_int32), ("size_class", ctypes.c_int32),
-                ("ms_per_round", ctypes.c_double * 6), ("select_path", ctypes.c_int32),
+                ("ms_per_round", ctypes.c_double * 8), ("select_path", ctypes.c_int32),
                 ("ms_per_round_select", ctypes.c_double * 3)]
 
     def as_dict(self):
@@ -107,7 +107,7 @@ _SIGNATURES = {
                                                ctypes.c_int32, _P, _P]),
     "bp_lbp_run_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
                                           ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P]),
-    "bp_q16_scale": (ctypes.c_int, [_P, _P]),
+    "bp_storage_scale": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "bp_graph_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "bp_destroy_graph": (None, [_P]),
     "bp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -330,10 +330,12 @@ def bp_lbp_run_noalloc(n_vars, n_dir_edges, row_ptr, col, rev, unary_log, beta, 
     return rounds.value, bool(conv.value)
 
 
-def bp_q16_scale(handle) -> float:
-    """The Q16 log-odds step of the handle's (binary Ising) potentials."""
+def bp_storage_scale(handle, msg_dtype) -> float:
+    """The scale of a 16-bit format ("q16" or "bf16") on the handle's binary
+    Ising potentials."""
+    dt = DTYPES[msg_dtype] if isinstance(msg_dtype, str) else int(msg_dtype)
     out = ctypes.c_float()
-    _check(lib().bp_q16_scale(handle, ctypes.byref(out)), "bp_q16_scale")
+    _check(lib().bp_storage_scale(handle, dt, ctypes.byref(out)), "bp_storage_scale")
     return float(out.value)
 
 
@@ -368,8 +370,8 @@ class Graph:
     def graph_stats(self):
         return bp_get_graph_stats(self.handle)
 
-    def q16_scale(self):
-        return bp_q16_scale(self.handle)
+    def storage_scale(self, msg_dtype):
+        return bp_storage_scale(self.handle, msg_dtype)
 
     def profile(self):
         return bp_get_profile(self.handle)

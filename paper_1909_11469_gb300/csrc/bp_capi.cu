@@ -102,6 +102,7 @@ struct bp_graph {
     int pair_kind = -1;
     bool has_pot = false;
     float qscale = 1.0f;   // Q16 log-odds step: 2 max|beta| / 32767
+    float bscale = 1.0f;   // BF16 (binary Ising) log-odds per unit of log2 of the word: 2 max|beta| / 250
     int32_t sel_smem_bytes = 0;   // staged keys of the largest graph, capped
     float *d_unary = nullptr, *d_udiff32 = nullptr, *d_q32 = nullptr, *d_pair = nullptr,
           *d_psi_shared = nullptr;
@@ -139,6 +140,11 @@ struct bp_graph {
     int32_t n_tc_tiles = 0;
     bool tc_tiles_ok = false;
     int32_t *d_err = nullptr;
+    // warp tiles of the streamed update (mapping 6), n_wtiles + 1 records; 0
+    // tiles when a vertex has more than STREAM_WT out-edges
+    int4 *d_wtiles = nullptr;
+    int32_t n_wtiles = 0;
+    bool wtiles_ok = false;
     uint32_t *d_trace = nullptr;
     size_t trace_alloc_words = 0;
     double *d_beliefs = nullptr;
@@ -218,7 +224,27 @@ int32_t resolve_select_path(const bp_graph *g, int schedule, int dtype, int32_t 
     return it != g_tune_table.end() ? (it->second >> 8) & 0xff : 0;
 }
 
-DevGraph dev_graph(const bp_graph *g)
+// BF16 code scale of Ising potentials with max |beta| = bmax: the smallest
+// power of two >= 2 bmax / 250, so every |u| <= 2 bmax has |u| / b <= 250 and
+// the scaling by b and 1/b is exact.
+float bf16_scale(double bmax)
+{
+    int ex = 0;
+    const double m = std::frexp(2.0 * bmax / 250.0, &ex);   // 2 bmax / 250 = m 2^ex, m in [0.5, 1)
+    return (float)std::ldexp(1.0, m == 0.5 ? ex - 1 : ex);
+}
+
+// Scale of the run's 16-bit storage (DevGraph::qscale).
+float storage_scale(const bp_graph *g, int dtype)
+{
+    if (dtype == DT_Q16)
+        return g->qscale;
+    if (dtype == DT_BF16 && epm_of(g) == 1)
+        return g->bscale;
+    return 0.0f;
+}
+
+DevGraph dev_graph(const bp_graph *g, int dtype)
 {
     DevGraph d;
     d.n = g->n;
@@ -226,7 +252,7 @@ DevGraph dev_graph(const bp_graph *g)
     d.G = g->G;
     d.M = (int32_t)g->M;
     d.epm = epm_of(g);
-    d.qscale = g->qscale;
+    d.qscale = storage_scale(g, dtype);
     d.vec_ok = 1;   // every device array of a handle comes from cudaMalloc (256-byte aligned)
     d.sel_smem_bytes = g->sel_smem_bytes;
     d.max_ge = g->max_graph_edges;
@@ -249,6 +275,8 @@ DevGraph dev_graph(const bp_graph *g)
     d.q64 = g->d_q64;
     d.pair = g->d_pair;
     d.psi_shared = g->d_psi_shared;
+    d.wtiles = g->d_wtiles;
+    d.n_wtiles = g->n_wtiles;
     return d;
 }
 
@@ -271,6 +299,7 @@ DevRun dev_run(const bp_graph *g)
     r.lvl_cnt = g->d_lvl_cnt;
     r.lvl_gcnt = g->d_lvl_gcnt;
     r.graph_p = g->graph_p_set ? g->d_graph_p : nullptr;
+    r.err = g->d_err;
     r.gsel = g->d_gsel;
     r.gsel_hist = g->d_gsel_hist;
     r.gsel_tie = g->d_gsel_tie;
@@ -299,6 +328,12 @@ void apply_select_plan(const bp_graph *g, int dtype, int sel_grid_bits, DevGraph
 
 size_t dtype_size(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }   // BF16, Q16: 2
 
+// Elements appended to the arrays the streamed update reads with bulk copies
+// (rev, row_ptr, exp(-2 beta), unary log-odds, messages): a copy starts at the
+// 16-byte block of a tile's first element and ends at the block of its last,
+// so it may read up to 15 bytes past an array's last element.
+constexpr size_t PAD = 16;
+
 int ensure_msg_buffers(bp_graph *g, int dtype)
 {
     if (g->buf_dtype == dtype && g->buf_epm == epm_of(g))
@@ -310,7 +345,8 @@ int ensure_msg_buffers(bp_graph *g, int dtype)
     size_t rs = dtype == DT_F64 ? 8 : 4;
     int rc;
     for (int b = 0; b < 2; ++b) {
-        if ((rc = dalloc((char **)&g->d_msg[b], elems * es)) != BP_OK)
+        // (+ PAD elements: the streamed update copies whole 16-byte blocks)
+        if ((rc = dalloc((char **)&g->d_msg[b], (elems + PAD) * es)) != BP_OK)
             return rc;
     }
     if ((rc = dalloc((char **)&g->d_resid, (size_t)g->M * rs)) != BP_OK)
@@ -382,6 +418,7 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     cudaGetDevice(&g->dev);
     prepare_select_kernels();
     prepare_potts_tc();
+    prepare_stream_kernels();
     g->n = n;
     g->k = k;
     g->M = M;
@@ -405,8 +442,8 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     for (int32_t i = 0; i < n; ++i)
         g->max_deg = std::max<int32_t>(g->max_deg, (int32_t)(row_ptr[i + 1] - row_ptr[i]));
     int rc;
-    if ((rc = dalloc(&g->d_row_ptr, (size_t)n + 1)) || (rc = dalloc(&g->d_col, (size_t)M)) ||
-        (rc = dalloc(&g->d_rev, (size_t)M)) || (rc = dalloc(&g->d_gid, (size_t)std::max(n, 1))) ||
+    if ((rc = dalloc(&g->d_row_ptr, (size_t)n + 1 + PAD)) || (rc = dalloc(&g->d_col, (size_t)M)) ||
+        (rc = dalloc(&g->d_rev, (size_t)M + PAD)) || (rc = dalloc(&g->d_gid, (size_t)std::max(n, 1))) ||
         (rc = dalloc(&g->d_gv_off, (size_t)n_graphs + 1)) || (rc = dalloc(&g->d_ge_off, (size_t)n_graphs + 1)))
         return rc;
     BP_CK(cudaMemcpy(g->d_row_ptr, rp32.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice));
@@ -450,8 +487,39 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
         if ((rc = dalloc(&g->d_tc_tiles, tv.size())))
             return rc;
         BP_CK(cudaMemcpy(g->d_tc_tiles, tv.data(), sizeof(int32_t) * tv.size(), cudaMemcpyHostToDevice));
-        if ((rc = dalloc(&g->d_err, 1)))
+    }
+    if ((rc = dalloc(&g->d_err, 1)))
+        return rc;
+    BP_CK(cudaMemset(g->d_err, 0, sizeof(int32_t)));
+    {
+        // warp tiles of the streamed update: greedy runs of consecutive
+        // vertices of one graph, at most STREAM_WT out-edges and STREAM_WV
+        // vertices
+        std::vector<int4> rec;
+        bool ok = g->max_deg <= STREAM_WT;
+        for (int32_t q = 0; ok && q < n_graphs; ++q) {
+            int32_t v = gv[(size_t)q];
+            const int32_t vend = gv[(size_t)q + 1];
+            while (v < vend) {
+                const int32_t v0 = v;
+                int64_t ecount = 0;
+                while (v < vend && v - v0 < STREAM_WV && ecount + (row_ptr[v + 1] - row_ptr[v]) <= STREAM_WT) {
+                    ecount += row_ptr[v + 1] - row_ptr[v];
+                    ++v;
+                }
+                // {first vertex, first edge, graph, vertex count}: every
+                // vertex lies in one tile, so a tile ends where the next begins
+                rec.push_back(make_int4(v0, (int32_t)row_ptr[v0], q, v - v0));
+            }
+        }
+        if (!ok)
+            rec.clear();
+        g->wtiles_ok = ok;
+        g->n_wtiles = (int32_t)rec.size();
+        rec.push_back(make_int4(n, (int32_t)M, -1, 0));
+        if ((rc = dalloc(&g->d_wtiles, rec.size())))
             return rc;
+        BP_CK(cudaMemcpy(g->d_wtiles, rec.data(), sizeof(int4) * rec.size(), cudaMemcpyHostToDevice));
     }
     BP_CK(cudaMallocHost((void **)&g->h_running, sizeof(int32_t)));
     BP_CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
@@ -604,7 +672,7 @@ int get_graph_exec(bp_graph *g, int dtype, const RunParams &rp, int rounds, Cach
     c.kp = g->kp;
     c.epm = epm_of(g);
     c.kernels = 0;
-    DevGraph dg = dev_graph(g);
+    DevGraph dg = dev_graph(g, dtype);
     apply_select_plan(g, dtype, rp.sel_grid, dg);
     DevRun dr = dev_run(g);
     BP_CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -664,6 +732,9 @@ static int build_run_params(const bp_graph *g, int32_t schedule, double parallel
     const int64_t trace_count = schedule == BP_RS ? g->n : g->M;
     rp.trace_words = (int32_t)((trace_count + 31) / 32);
     variant = epm_of(g) == 1 ? resolve_variant(g, schedule, dtype, opt.kernel_variant) : 1;
+    if (variant == 6 && (dtype == DT_F64 || !g->wtiles_ok))
+        return fail(BP_ERR_UNSUPPORTED, "the streamed update (kernel_variant 6) needs FP32, BF16 or Q16 messages "
+                                        "and vertices with at most 128 out-edges");
     rp.variant = variant == 3 ? 1 : variant;
     rp.eps_f = float_at_least(eps);
     // shared-table update in vertex tiles: 0 = per-vertex k-state kernel,
@@ -783,19 +854,22 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
         ud[(size_t)i] = (double)unary_log[(size_t)i * k + 1] - (double)unary_log[(size_t)i * k];
         ud32[(size_t)i] = (float)ud[(size_t)i];
     }
-    if ((rc = dalloc(&g->d_udiff64, (size_t)n)) || (rc = dalloc(&g->d_udiff32, (size_t)n)))
+    if ((rc = dalloc(&g->d_udiff64, (size_t)n)) || (rc = dalloc(&g->d_udiff32, (size_t)n + PAD)))
         return rc;
     if (n) {
         BP_CK(cudaMemcpy(g->d_udiff64, ud.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
         BP_CK(cudaMemcpy(g->d_udiff32, ud32.data(), sizeof(float) * (size_t)n, cudaMemcpyHostToDevice));
     }
     g->qscale = 1.0f / 32767.0f;
+    g->bscale = bf16_scale(0.5);
     if (pair_kind == BP_PAIR_ISING_BETA) {
         double bmax = 0.0;
         for (int64_t e = 0; e < M; ++e)
             bmax = std::max(bmax, std::fabs((double)pair_log[e]));
-        if (bmax > 0.0)
+        if (bmax > 0.0) {
             g->qscale = (float)(2.0 * bmax / 32767.0);
+            g->bscale = bf16_scale(bmax);
+        }
         std::vector<double> q64((size_t)M);
         std::vector<float> q32((size_t)M);
         for (int64_t e = 0; e < M; ++e) {
@@ -803,7 +877,7 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
             q64[(size_t)e] = std::min(std::max(q, 1e-300), 1e300);
             q32[(size_t)e] = (float)std::min(std::max(q, 1e-30), 1e30);
         }
-        if ((rc = dalloc(&g->d_q64, (size_t)M)) || (rc = dalloc(&g->d_q32, (size_t)M)))
+        if ((rc = dalloc(&g->d_q64, (size_t)M)) || (rc = dalloc(&g->d_q32, (size_t)M + PAD)))
             return rc;
         if (M) {
             BP_CK(cudaMemcpy(g->d_q64, q64.data(), sizeof(double) * (size_t)M, cudaMemcpyHostToDevice));
@@ -865,8 +939,8 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "splash_sweep must be 0..3");
     if (opt.overlap_launches < 0 || opt.overlap_launches > 2)
         return fail(BP_ERR_INVALID_ARG, "overlap_launches must be 0..2");
-    if (opt.kernel_variant < 0 || opt.kernel_variant > 5)
-        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 5]");
+    if (opt.kernel_variant < 0 || opt.kernel_variant > 6)
+        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 6]");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
         return fail(BP_ERR_INVALID_ARG, "splash_depth must be in [0, 16]");
     if (opt.record_trace && opt.trace_capacity < 0)
@@ -929,7 +1003,7 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         g->sel_plan[dtype][5] = grid[1];
         g->sel_planned[dtype] = true;
     }
-    DevGraph dg = dev_graph(g);
+    DevGraph dg = dev_graph(g, dtype);
     {
         const int32_t sp = resolve_select_path(g, schedule, dtype, opt.select_path);
         int bits = g->sel_planned[dtype] ? (g->sel_plan[dtype][2] | (g->sel_plan[dtype][5] << 1)) : 0;
@@ -1063,7 +1137,7 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         int32_t h_err = 0;
         BP_CK(cudaMemcpy(&h_err, g->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
         if (h_err)
-            return fail(BP_ERR_CUDA, "a tensor-core completion wait expired; results are invalid");
+            return fail(BP_ERR_CUDA, "a bulk-copy or tensor-core completion wait expired; results are invalid");
     }
     if (persistent) {
         BP_CK(cudaEventElapsedTime(&batch_ms, g->ev_pt0, g->ev_pt1));
@@ -1166,7 +1240,7 @@ int bp_get_messages(const bp_graph *g, double *out)
     int rc = dalloc(&d, count);
     if (rc)
         return rc;
-    launch_messages(g->res_dtype, dev_graph(g), dev_run(g), g->kp, d, 0);
+    launch_messages(g->res_dtype, dev_graph(g, g->res_dtype), dev_run(g), g->kp, d, 0);
     cudaError_t e = cudaMemcpy(out, d, sizeof(double) * count, cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess)
@@ -1269,11 +1343,14 @@ int bp_autotune(bp_graph *g, int32_t schedule, double parallelism, double eps, c
     o.time_budget_ms = 0.0;
     o.record_trace = 0;
     memset(out, 0, sizeof(*out));
-    static const int32_t cand[] = {1, 2, 4, 5, 3};
-    const int n_cand = g->G > 1 ? 5 : 4;   // the persistent kernel runs one cluster per graph
+    static const int32_t cand[] = {1, 2, 4, 5, 6, 3};
     double best = std::numeric_limits<double>::infinity();
     int32_t best_v = 1;
-    for (int c = 0; c < n_cand; ++c) {
+    for (int c = 0; c < 6; ++c) {
+        if (cand[c] == 3 && g->G == 1)
+            continue;   // the persistent kernel runs one cluster per graph
+        if (cand[c] == 6 && (o.msg_dtype == BP_F64 || !g->wtiles_ok))
+            continue;   // the streamed tiles need FP32 arithmetic and <= 128 out-edges per vertex
         o.kernel_variant = cand[c];
         bp_run_stats st;
         int rc = bp_run(g, schedule, parallelism, eps, trial_rounds, &o, &st);   // warm-up: captures rounds
@@ -1406,7 +1483,7 @@ int bp_time_update(bp_graph *g, int32_t schedule, double parallelism, const bp_o
     if (epm_of(g) == 1 && variant == 3)
         return fail(BP_ERR_UNSUPPORTED, "the persistent batch kernel has no separate update launch");
     cudaStream_t s = (cudaStream_t)opt.cuda_stream;
-    const DevGraph dg = dev_graph(g);
+    const DevGraph dg = dev_graph(g, dtype);
     const DevRun dr = dev_run(g);
     const int emode = rp.schedule == SCHED_LBP ? MODE_LBP : MODE_CAND;
     launch_init(dtype, dg, dr, s);
@@ -1427,15 +1504,17 @@ int bp_time_update(bp_graph *g, int32_t schedule, double parallelism, const bp_o
     return BP_OK;
 }
 
-int bp_q16_scale(const bp_graph *g, float *out)
+int bp_storage_scale(const bp_graph *g, int32_t msg_dtype, float *out)
 {
     if (!g || !out)
         return fail(BP_ERR_INVALID_ARG, "NULL argument");
+    if (msg_dtype != BP_Q16 && msg_dtype != BP_BF16)
+        return fail(BP_ERR_INVALID_ARG, "msg_dtype must be BP_Q16 or BP_BF16");
     if (!g->has_pot)
-        return fail(BP_ERR_NO_POTENTIALS, "bp_q16_scale before bp_set_potentials");
+        return fail(BP_ERR_NO_POTENTIALS, "bp_storage_scale before bp_set_potentials");
     if (!(g->k == 2 && g->pair_kind == BP_PAIR_ISING_BETA))
-        return fail(BP_ERR_UNSUPPORTED, "Q16 storage needs binary Ising potentials");
-    *out = g->qscale;
+        return fail(BP_ERR_UNSUPPORTED, "the scaled 16-bit formats hold binary Ising log-odds");
+    *out = storage_scale(g, msg_dtype);
     return BP_OK;
 }
 
@@ -1499,6 +1578,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_queue);
     dfree(g->d_tc_tiles);
     dfree(g->d_err);
+    dfree(g->d_wtiles);
     dfree(g->d_trace);
     dfree(g->d_beliefs);
     if (g->h_running)

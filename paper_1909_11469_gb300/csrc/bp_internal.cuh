@@ -30,12 +30,19 @@ struct GState {
     unsigned long long final_cnt;
 };
 
+// Warp tiles of the streamed update (bp_stream.cu): at most STREAM_WT
+// out-edges and STREAM_WV consecutive vertices of one graph.
+constexpr int STREAM_WT = 128;
+constexpr int STREAM_WV = 32;
+
 // Read-only graph and potential arrays on the device.
 struct DevGraph {
     int32_t n, k, G;
     int32_t M;
     int32_t epm;              // stored elements per message: 1 (binary log-odds) or k
-    float qscale;             // Q16 storage: log-odds per integer step
+    float qscale;             // scale of the run's 16-bit storage: Q16 log-odds per integer
+                              // step; BF16 binary log-odds per unit of log2 of the stored
+                              // word; 0 for BF16 k-state logs (plain rounding)
     int32_t vec_ok;           // 1: rev, q and message buffers are 16-byte aligned
     int32_t sel_smem_bytes;   // dynamic shared memory of the selection kernels (set per launch)
     int32_t max_ge;           // largest directed-edge count of a graph
@@ -59,6 +66,11 @@ struct DevGraph {
     const double *q64;        // [M]
     const float *pair;        // table [M*k*k] (log) or shared [k*k] (log)
     const float *psi_shared;  // [k*k] exp(Theta - max Theta)     (shared)
+    // streamed update: warp tiles {first vertex, first edge, graph, vertex
+    // count}, every vertex in one tile, and a sentinel {n, M, -1, 0};
+    // n_wtiles = 0 when a vertex has > STREAM_WT edges
+    const int4 *wtiles;
+    int32_t n_wtiles;
 };
 
 // Per-run parameters (kernel arguments, baked into the captured graph).
@@ -125,6 +137,7 @@ struct DevRun {
                                   // the lists are per graph: graph gg's level L at
                                   // lvl_list[L * n + gv_off[gg] + j], j < lvl_gcnt[gg * (LVL_MAX+1) + L]
     const double *graph_p;        // [G] per-graph parallelism, or null: every graph uses rp.low_p
+    int32_t *err;                 // [1] set when a bounded device wait runs out
     // grid-wide selection (large graphs; null when unused)
     GSelState *gsel;              // [G]
     unsigned int *gsel_hist;      // [G * 2048]
@@ -176,15 +189,47 @@ template <> struct Store<float> {
     static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
     static __device__ __forceinline__ float quant(float v, float) { return v; }
 };
+// BF16. With sc > 0 (binary Ising log-odds; sc a power of two) the word is
+// the bfloat16 value nearest to w = 2^(|u| / sc - 125), carrying the sign of u:
+// for |u| <= 250 sc it lies in [2^-125, 2^125], and its exponent and mantissa
+// bits form a logarithmic code of |u| with a step of at most sc / 128; read
+// back as |u| = (log2 |w| + 125) sc. With sc = 0 (k-state logs) the word is the
+// value itself rounded to bfloat16. ex2 / lg2 are the hardware approximations,
+// the scaling by sc and 1/sc is exact, so every kernel codes and decodes the
+// same bits.
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 template <> struct Store<__nv_bfloat16> {
     using A = float;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float) { return __bfloat162float(*p); }
-    static __device__ __forceinline__ float val(__nv_bfloat16 x, float) { return __bfloat162float(x); }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float) { *p = __float2bfloat16_rn(v); }
-    static __device__ __forceinline__ float quant(float v, float)
+    static __device__ __forceinline__ __nv_bfloat16 code(float v, float sc)
     {
-        return __bfloat162float(__float2bfloat16_rn(v));
+        if (sc <= 0.0f)
+            return __float2bfloat16_rn(v);
+        const float inv = __int_as_float(0x7F000000 - __float_as_int(sc));   // 1 / sc, exact for a power of two
+        const float w = ex2_approx(__fsub_rn(__fmul_rn(fabsf(v), inv), 125.0f));
+        return __float2bfloat16_rn(v < 0.0f ? -w : w);
     }
+    static __device__ __forceinline__ float val(__nv_bfloat16 x, float sc)
+    {
+        const float w = __bfloat162float(x);
+        if (sc <= 0.0f)
+            return w;
+        const float a = __fmul_rn(__fadd_rn(lg2_approx(fabsf(w)), 125.0f), sc);
+        return w < 0.0f ? -a : a;
+    }
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float sc) { return val(*p, sc); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float sc) { *p = code(v, sc); }
+    static __device__ __forceinline__ float quant(float v, float sc) { return val(code(v, sc), sc); }
 };
 // Q16: binary log-odds as a signed 16-bit multiple of sc, |q| <= 32767. The
 // products q * sc are rounded explicitly (__fmul_rn), so no kernel fuses them

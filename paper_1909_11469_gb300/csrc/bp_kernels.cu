@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 namespace bpg {
 
@@ -822,12 +823,12 @@ __global__ void __launch_bounds__(BLOCK, 6) k_splash_list_pair(DevGraph g, DevRu
 // --------------------------------------------------------------------------
 // Set-up of a run.
 template <typename S>
-__global__ void k_init_msgs(S *a, S *b, size_t count, double value)
+__global__ void k_init_msgs(S *a, S *b, size_t count, double value, float sc)
 {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
          t += (size_t)gridDim.x * blockDim.x) {
-        Store<S>::st(a + t, (typename Store<S>::A)value, 1.0f);
-        Store<S>::st(b + t, (typename Store<S>::A)value, 1.0f);
+        Store<S>::st(a + t, (typename Store<S>::A)value, sc);
+        Store<S>::st(b + t, (typename Store<S>::A)value, sc);
     }
 }
 
@@ -984,6 +985,11 @@ static void launch_k(bool pdl, void (*kernel)(KArgs...), int grid, int block, cu
     default: { using S = __nv_bfloat16; BODY; } break;               \
     }
 
+template <typename S> constexpr int dtype_of()
+{
+    return sizeof(S) == 8 ? DT_F64 : (sizeof(S) == 4 ? DT_F32 : (std::is_same<S, int16_t>::value ? DT_Q16 : DT_BF16));
+}
+
 template <typename S>
 static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
                             cudaStream_t s)
@@ -994,6 +1000,10 @@ static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams
     // (variant 2), thread per vertex with prefetched graph arrays of 4 (variant
     // 4, 40 registers: 6 blocks per SM) or 8 edges (variant 5, 4 blocks per SM)
     const bool tiled = rp.variant == 2;
+    if (rp.variant == 6) {
+        launch_eval_stream(dtype_of<S>(), g, dr, rp, mode, s);
+        return;
+    }
     if (rp.variant >= 4) {
         if (mode == MODE_LBP) {
             if (rp.variant == 4) launch_k(rp.pdl, k_eval_bin_pf<S, MODE_LBP, 4, 6>, nb, BLOCK, s, g, dr, rp);
@@ -1127,7 +1137,7 @@ void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s)
     double v = (g.epm == 1) ? 0.0 : -log((double)g.k);
     if (count) {
         int nb = (int)std::min<size_t>((count + BLOCK - 1) / BLOCK, 152 * 16);
-        BPG_DISPATCH4(dtype, (k_init_msgs<S><<<nb, BLOCK, 0, s>>>((S *)dr.msg[0], (S *)dr.msg[1], count, v)));
+        BPG_DISPATCH4(dtype, (k_init_msgs<S><<<nb, BLOCK, 0, s>>>((S *)dr.msg[0], (S *)dr.msg[1], count, v, g.qscale)));
     }
     int nb2 = blocks_for(g.G * NSUB, BLOCK);
     k_init_state<<<nb2, BLOCK, 0, s>>>(dr, g.G);

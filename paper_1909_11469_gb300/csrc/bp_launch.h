@@ -14,6 +14,10 @@ enum { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2, DT_Q16 = 3 };
 void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s);
 void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
                  int kp, cudaStream_t s);
+// Streamed warp-tile update (bp_stream.cu, update mapping 6; FP32, BF16, Q16).
+void prepare_stream_kernels();
+void launch_eval_stream(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode,
+                        cudaStream_t s);
 void launch_decide(const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s);
 // Loads the kernels of an FP32 thread-per-vertex LBP run (update, decision,
 // beliefs) on the current device now rather than at their first launch (the

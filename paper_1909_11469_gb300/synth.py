@@ -56,6 +56,28 @@ class Problem:
     def n_graphs(self) -> int:
         return int(self.graph_var_offsets.shape[0] - 1)
 
+    def graphs(self, g0: int, g1: int) -> "Problem":
+        """Graphs [g0, g1) of a batch as a batch of their own, renumbered from
+        vertex 0 and edge 0."""
+        v0, v1 = int(self.graph_var_offsets[g0]), int(self.graph_var_offsets[g1])
+        e0, e1 = int(self.row_ptr[v0]), int(self.row_ptr[v1])
+        k = self.k
+        if self.pair_kind == PAIR_ISING_BETA:
+            pl = self.pair_log[e0:e1].copy()
+        elif self.pair_kind == PAIR_TABLE:
+            pl = self.pair_log[e0 * k * k:e1 * k * k].copy()
+        else:
+            pl = self.pair_log.copy()
+        return Problem(
+            n=v1 - v0, k=k,
+            row_ptr=(self.row_ptr[v0:v1 + 1] - e0).astype(np.int64),
+            col=(self.col[e0:e1] - v0).astype(np.int32),
+            rev=(self.rev[e0:e1] - e0).astype(np.int32),
+            unary_log=self.unary_log[v0 * k:v1 * k].copy(),
+            pair_kind=self.pair_kind, pair_log=pl,
+            graph_var_offsets=(self.graph_var_offsets[g0:g1 + 1] - v0).astype(np.int64),
+            name=f"{self.name}[{g0}:{g1}]")
+
     def graph(self, g: int) -> "Problem":
         """Graph g of a batch, renumbered from vertex 0 and edge 0."""
         v0, v1 = int(self.graph_var_offsets[g]), int(self.graph_var_offsets[g + 1])

@@ -74,7 +74,8 @@ def test_bench_batch_sampled_graphs(sched, par, variant):
 
 
 @pytest.mark.parametrize("sched,dtype,tol", [("lbp", "f32", 1e-5), ("rnbp", "f32", 1e-5),
-                                             ("rnbp", "q16", 2e-3)])
+                                             ("rnbp", "q16", 2e-3), ("lbp", "bf16", 2e-3),
+                                             ("rnbp", "bf16", 2e-3)])
 def test_ising1000_full_grid(sched, dtype, tol):
     """1000x1000 Ising, beta ~ U[-3, 3] (4M messages): 4 rounds, every belief
     against the oracle following the GPU frontiers."""

@@ -366,11 +366,23 @@ def _bf16_exact(x):
     return np.all(f.astype(np.float64) == np.asarray(x)) and np.all((f.view(np.uint32) & 0xFFFF) == 0)
 
 
+def _bf16_scale(prob):
+    """The library's BF16 code scale: the smallest power of two >= 2 max|beta| / 250."""
+    return float(2.0 ** np.ceil(np.log2(2 * float(np.abs(prob.pair_log).max()) / 250)))
+
+
 def test_bf16_storage_values_are_bf16(orc):
-    """Under BF16 storage every stored Ising log-odds is a bfloat16 value, and
-    every stored k-state log is one too."""
+    """Under BF16 storage every stored Ising word w = 2^(|u| / b - 125) is a
+    bfloat16 value, under plain BF16 every stored log-odds is one, and every
+    stored k-state log is one too."""
     prob = synth.ising_grid(6, 1.5, seed=1)
-    res = orc.run(prob, "rnbp", parallelism=0.5, eps=1e-4, max_rounds=30, storage="bf16")
+    b = _bf16_scale(prob)
+    res = orc.run(prob, "rnbp", parallelism=0.5, eps=1e-4, max_rounds=30, storage="bf16", storage_scale=b)
+    u = np.log(res["messages"][:, 1]) - np.log(res["messages"][:, 0])
+    w = np.exp2(np.abs(u) / b - 125.0)
+    wb = np.float32(w)
+    assert _bf16_exact(wb) and np.abs(wb / w - 1).max() < 1e-9
+    res = orc.run(prob, "rnbp", parallelism=0.5, eps=1e-4, max_rounds=30, storage="bf16_plain")
     u = np.log(res["messages"][:, 1]) - np.log(res["messages"][:, 0])
     assert _bf16_exact(np.float32(u)) and np.abs(np.float32(u) - u).max() < 1e-12
     prob = synth.potts_grid(4, 5, seed=1)
@@ -386,7 +398,7 @@ def test_q16_storage_grid_and_bound(orc):
     prob = synth.ising_grid(6, 1.5, seed=2)
     beta_max = float(np.abs(prob.pair_log).max())
     step = float(np.float32(2 * beta_max / 32767))
-    res = orc.run(prob, "lbp", eps=1e-6, max_rounds=40, storage="q16", q16_scale=step)
+    res = orc.run(prob, "lbp", eps=1e-6, max_rounds=40, storage="q16", storage_scale=step)
     u = np.log(res["messages"][:, 1]) - np.log(res["messages"][:, 0])
     q = u / step
     assert np.abs(q - np.round(q)).max() < 1e-6 and np.abs(q).max() <= 32767
@@ -399,8 +411,9 @@ def test_rounded_storage_residual_zero_when_unchanged(orc):
     candidate rounds back to the stored word, so the final residual is exactly 0
     or below eps (bf16 limit cycles aside, reported as not converged)."""
     prob = synth.ising_tree(12, 1.0, seed=2)
-    res = orc.run(prob, "lbp", eps=1e-12, max_rounds=200, storage="bf16")
-    assert res["converged"] and res["final_max_residual"] == 0.0
+    for storage, scale in (("bf16", _bf16_scale(prob)), ("bf16_plain", 0.0)):
+        res = orc.run(prob, "lbp", eps=1e-12, max_rounds=200, storage=storage, storage_scale=scale)
+        assert res["converged"] and res["final_max_residual"] == 0.0
 
 
 # --------------------------------------------------------------------------- storage rounding pins
@@ -439,7 +452,38 @@ Q16_KNOWN = [(2.5, 2), (3.5, 4), (2.75, 3), (2.25, 2), (40000.0, 32767)]
 @pytest.mark.parametrize("sign", [1.0, -1.0])
 def test_bf16_rounding_known_answers(orc, sign):
     for u, want in BF16_KNOWN:
-        assert orc.stored_logodds("bf16", sign * u) == sign * want, (u, want)
+        assert orc.stored_logodds("bf16_plain", sign * u) == sign * want, (u, want)
+
+
+# The BF16 exponent code of an Ising log-odds u with scale b: the word is the
+# bfloat16 value nearest to w = 2^(|u| / b - 125) (sign of u), read back as
+# |u| = (log2 |w| + 125) b. Hand-derived cases:
+#   b = 1, u = 0:     w = 2^-125 exactly                       -> 0
+#   b = 0.1, u = 3.3: |u| / b - 125 = -92, w = 2^-92 exactly    -> 3.3
+#   b = 1, u = 0.3:   w = 2^-125 * 2^0.3, 2^0.3 = 1.2311444...; the 8-bit
+#                     significand is 1.2311444 * 128 = 157.586 -> 158 / 128
+#                     -> log2(158 / 128) = 0.3037807...  (truncation: 157 / 128,
+#                     0.2946...)
+#   b = 2, u = 0.6:   the same word (|u| / b = 0.3)            -> 2 log2(158 / 128)
+#   b = 1, u = 0.5:   2^0.5 * 128 = 181.02 -> 181 / 128        -> log2(181 / 128)
+BF16X_KNOWN = [(1.0, 0.0, 0.0), (0.1, 3.3, 3.3), (1.0, 0.3, np.log2(158 / 128)),
+               (2.0, 0.6, 2 * np.log2(158 / 128)), (1.0, 0.5, np.log2(181 / 128))]
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_bf16_exponent_code_known_answers(orc, sign):
+    for b, u, want in BF16X_KNOWN:
+        got = orc.stored_logodds("bf16", sign * u, b)
+        assert abs(got - sign * want) < 1e-12, (b, u, want, got)
+
+
+def test_bf16_exponent_code_through_a_run(orc):
+    """The exponent code is what a run stores: the single copying edge carries
+    t = 0.3 and -0.5 (scale 1) as log2(158 / 128) and -log2(181 / 128)."""
+    res = orc.run(_copy_edge(0.3, -0.5), "lbp", eps=1e-15, max_rounds=5, storage="bf16", storage_scale=1.0)
+    assert res["converged"] and res["rounds"] == 1
+    got = _stored_u(res)
+    assert abs(got[0] - np.log2(158 / 128)) < 1e-12 and abs(got[1] + np.log2(181 / 128)) < 1e-12, got
 
 
 @pytest.mark.parametrize("sign", [1.0, -1.0])
@@ -465,13 +509,13 @@ def _stored_u(res):
     return np.log(m[:, 1]) - np.log(m[:, 0])
 
 
-def test_bf16_storage_rounding_through_a_run(orc):
+def test_bf16_plain_rounding_through_a_run(orc):
     """The rounding pinned above is the one a run stores: message 0 -> 1 carries
     t = vertex 0's field, message 1 -> 0 carries vertex 1's. Round 1 commits the
     rounded values, round 2 finds them unchanged (residual 0)."""
     for u, want in BF16_KNOWN:
         assert float(np.float32(u)) == u
-        res = orc.run(_copy_edge(u, -u), "lbp", eps=1e-15, max_rounds=5, storage="bf16")
+        res = orc.run(_copy_edge(u, -u), "lbp", eps=1e-15, max_rounds=5, storage="bf16_plain")
         assert res["converged"] and res["rounds"] == 1
         got = _stored_u(res)
         # edge 0 is 0 -> 1 (CSR row 0), edge 1 is 1 -> 0
@@ -485,7 +529,7 @@ def test_q16_storage_rounding_through_a_run(orc):
     for steps, want in [(2.75, 3), (2.25, 2), (3.6, 4), (40000.0, 32767)]:
         t = steps * Q16_STEP
         res = orc.run(_copy_edge(t, -t), "lbp", eps=1e-15, max_rounds=5, storage="q16",
-                      q16_scale=Q16_STEP)
+                      storage_scale=Q16_STEP)
         assert res["converged"] and res["rounds"] == 1
         got = _stored_u(res) / Q16_STEP
         assert abs(got[0] - want) < 1e-6 and abs(got[1] + want) < 1e-6, (steps, want, got)
@@ -505,3 +549,21 @@ def test_bf16_storage_of_k_state_logs(orc):
                          synth.PAIR_TABLE, tab.reshape(-1), np.array([0, 2], np.int64))
     res = orc.run(prob, "lbp", eps=1e-15, max_rounds=5, storage="bf16")
     assert np.abs(np.log(res["messages"]) + 141.0 / 128.0).max() < 1e-12
+
+
+def test_bf16_formats_against_the_exact_oracle(orc):
+    """The belief tolerance 2e-3 of BF16 storage, on a converging loopy grid
+    (37x29, beta ~ U[-1, 1], LBP, eps = 1e-4), three seeds. Plain bfloat16
+    log-odds have a relative step of 2^-7: one step of a log-odds near 2 is
+    2^-6, and such steps keep the stored messages cycling between neighbours
+    (never below eps) with belief errors above 2e-3. The exponent code's step is
+    at most b / 128 <= 2 max|beta| / 16000 in log-odds: those runs converge and
+    stay an order of magnitude inside the tolerance."""
+    for seed in (7, 1, 2):
+        prob = synth.ising_grid(37, 1.0, seed=seed, cols=29)
+        exact = orc.run(prob, "lbp", eps=1e-4, max_rounds=2000)
+        code = orc.run(prob, "lbp", eps=1e-4, max_rounds=2000, storage="bf16", storage_scale=_bf16_scale(prob))
+        plain = orc.run(prob, "lbp", eps=1e-4, max_rounds=2000, storage="bf16_plain")
+        assert exact["converged"] and code["converged"] and not plain["converged"]
+        assert np.abs(code["beliefs"] - exact["beliefs"]).max() < 2e-4
+        assert np.abs(plain["beliefs"] - exact["beliefs"]).max() > 2e-3
