@@ -77,14 +77,12 @@ MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
 # roofline kernel from one ncu capture on the workload, valid only while the
 # kernel is unchanged since the capture (the summaries and commands are in
 # profiles/). Captures are cold (ncu flushes the caches), so they bound the warm
-# traffic from above. The captures of k_splash_list_step (mean of three
-# launches: 38.3 MB) and k_eval_bin_pf (default workload 29.8 MB, 1000x1000
-# LBP 61.4 MB) predate the current kernels -- the sweep evaluation now loads
-# one buffer per incoming message, and the update waits for its predecessor in
-# griddepcontrol.wait -- so both tables are empty and the traffic is null
-# until the kernels are captured again.
+# traffic from above. Keys: (workload, storage, update mapping) and (workload,
+# storage, sweep form). The 4096-graph ER capture is of an RnBP launch (the
+# residual stored: 2/3 of the step's update launches); an LBP launch moves 4 B
+# per message less.
 NCU_SWEEP_TRAFFIC = {}
-NCU_UPDATE_TRAFFIC = {}
+NCU_UPDATE_TRAFFIC = {("er4096_b3", "f32", 6): 254.224896e6 + 106.186240e6}
 BYTES_PER_VERTEX = 12
 
 
@@ -597,10 +595,23 @@ def main():
             d["committed_updates"] += st["committed_updates"]
             d["converged_fraction"] = float(np.mean([x["converged"] for x in gst]))
             d["median_rounds"] = float(np.median([x["rounds"] for x in gst]))
+            d["conv_rounds"] = sorted(int(x["rounds"]) for x in gst if x["converged"])
+            d["max_rounds"] = int(st["rounds"])
     for d in per_sched.values():
         d["batch_ms"] = float(np.median(d.pop("ms")))
         d["committed_updates"] //= args.steps
         d["graphs_per_s"] = G / (d["batch_ms"] / 1e3)
+        # cumulative converged fraction against rounds (the paper's Figs. 2 and
+        # 4 plot it against time): [fraction of all graphs converged, rounds,
+        # ms at the batch's mean round time]
+        cr, rmax = d.pop("conv_rounds"), d.pop("max_rounds")
+        ms_round = d["batch_ms"] / max(rmax, 1)
+        curve = []
+        for q in (0.1, 0.25, 0.5, 0.75, 0.9, 1.0):
+            if cr:
+                r = cr[max(0, int(np.ceil(q * len(cr))) - 1)]
+                curve.append([round(q * len(cr) / G, 4), r, round(r * ms_round, 3)])
+        d["convergence_curve"] = curve
 
     # time-to-convergence on the converging companion batch (same sizes and
     # seeds, milder couplings): batch time until every graph converged or hit

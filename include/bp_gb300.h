@@ -117,9 +117,10 @@ typedef struct {
     uint32_t graph_id_base;   /* Philox graph id of graph 0 of the handle (default 0) */
     int32_t kernel_variant;   /* binary Ising update mapping (every mapping computes the
                                  same bits): 0 = automatic (the choice bp_autotune
-                                 recorded for the handle's size class, else 4 when no
-                                 vertex has more than 4 edges and messages are not FP64,
-                                 and 1 otherwise), 1 =
+                                 recorded for the handle's size class; else, for
+                                 messages that are not FP64, 4 when no vertex has more
+                                 than 4 edges and 6 when the streamed tiles apply; 1
+                                 otherwise), 1 =
                                  per-round kernels, one thread per vertex, 2 = per-round,
                                  256-vertex tiles with 4-edge quads, 3 = persistent batch
                                  kernel: one thread-block cluster per graph runs all of
@@ -155,6 +156,14 @@ typedef struct {
                                  for it before reading run state; the sweep steps
                                  always launch without it): 0 = automatic (on), 1 =
                                  on, 2 = off */
+    int32_t dynamic_p;        /* RBP and RS: 1 = switch the frontier fraction every round
+                                 by the EdgeRatio rule that RnBP uses (Section IV-A; the
+                                 paper tried the same for RBP / RS and dropped it for its
+                                 overhead): HighP = high_p in round 1, then
+                                 parallelism (LowP) when the count of messages with
+                                 residual >= eps grew by more than ratio_threshold
+                                 relative to the previous round, else high_p; 0 = the
+                                 fixed fraction parallelism (default) */
 } bp_options;
 
 /* Phase timings and launch counts of the last bp_run. The timings are filled
@@ -235,6 +244,14 @@ int bp_create_batch(int32_t n_graphs, const int64_t *graph_var_offsets, int32_t 
  * pair_log is laid out per bp_pair_kind (see above). Inputs are validated for
  * finiteness and for the symmetry the kind requires (BP_ERR_NONFINITE) and
  * copied to the device; any previous result of the handle is discarded.
+ * Variable state counts (the paper's protein-folding graphs, Section IV-E,
+ * have 2 to 81 states per vertex): a unary log-potential of -inf marks that
+ * state of that vertex absent, so vertex v has k_v <= k present states. A
+ * message into v is then a distribution over v's present states (uniform at
+ * the start of a run, no mass on the absent ones) and absent states get
+ * belief 0. Needs BP_PAIR_TABLE (BP_ERR_UNSUPPORTED otherwise; table entries
+ * may also be -inf) and at least one present state per vertex
+ * (BP_ERR_NONFINITE). NaN and +inf are rejected everywhere.
  */
 int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind,
                       const float *pair_log);

@@ -42,7 +42,8 @@ class OrcParams(ctypes.Structure):
                 ("splash_depth", ctypes.c_int32), ("rs_roots_mode", ctypes.c_int32),
                 ("trace_in", ctypes.c_void_p), ("trace_rounds", ctypes.c_int32),
                 ("trace_out", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("storage_scale", ctypes.c_double)]
+                ("storage", ctypes.c_int32), ("storage_scale", ctypes.c_double),
+                ("dynamic_p", ctypes.c_int32)]
 
 
 class OrcStats(ctypes.Structure):
@@ -112,7 +113,7 @@ class _Bound:
 
 def run(prob, schedule="lbp", parallelism=1.0, eps=1e-4, max_rounds=1000, seed=0,
         graph_id=0, high_p=1.0, ratio_threshold=0.9, splash_depth=2, rs_roots_mode=0,
-        trace_in=None, trace_rounds=0, trace_cap=0, storage="f64", storage_scale=0.0):
+        trace_in=None, trace_rounds=0, trace_cap=0, storage="f64", storage_scale=0.0, dynamic_p=0):
     """Run one graph (prob must hold a single graph). Returns a dict with beliefs
     [n, k], messages [M, k] (probability domain), stats and the selected trace.
     storage: "f64" (exact), "bf16", "q16" or "bf16_plain" (emulated 16-bit message
@@ -131,7 +132,7 @@ def run(prob, schedule="lbp", parallelism=1.0, eps=1e-4, max_rounds=1000, seed=0
                        int(graph_id), float(high_p), float(ratio_threshold), int(splash_depth),
                        int(rs_roots_mode), _ptr(tin) if tin is not None else None,
                        int(trace_rounds), _ptr(tout) if trace_cap > 0 else None, int(trace_cap),
-                       STORAGE[storage], float(storage_scale))
+                       STORAGE[storage], float(storage_scale), int(dynamic_p))
     beliefs = np.zeros(n * k + 1, dtype=np.float64)
     msgs = np.zeros(m * k + 1, dtype=np.float64)
     st = OrcStats()

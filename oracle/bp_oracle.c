@@ -21,6 +21,14 @@
  *           (BFS of depth h) swept leaves -> root -> leaves (Section II-B, III-A, III-D)
  *     RnBP  residual >= eps filter, then a random fraction p of the rest, with p
  *           switched between LowP and HighP by EdgeRatio (Section IV-A, IV-D)
+ *     RBP / RS with dynamic p: the same EdgeRatio switch sets their frontier
+ *           fraction each round (Section IV-A, last sentence: tried there)
+ *
+ * Variable state counts (the protein-folding graphs of Section IV-E have 2 to
+ * 81 states per vertex): a state whose unary log-potential is -inf is absent;
+ * a message into a vertex is a distribution over its present states (uniform
+ * at the start, no mass on absent states), which is Eq. 2 on the vertex's own
+ * state space.
  *
  * Readings where the paper is silent (each one a named choice, shared with the
  * CUDA side only through its written description):
@@ -30,7 +38,8 @@
  *   test, select, commit simultaneously (Jacobi); rounds = committing rounds;
  *   RBP/RS ties broken by smaller id; RBP k = clamp(ceil(p*M), 1, M); RS roots
  *   = clamp(ceil(p*M), 1, n) (or ceil(p*n) in the alternative mode); RnBP draws
- *   one Philox4x32-10 word per (seed; edge, round, graph) and selects iff the
+ *   one Philox4x32-10 word per message -- word e mod 4 of the block with key
+ *   seed and counter (floor(e / 4), round, graph, 0) -- and selects iff the
  *   word is below floor(p * 2^32); EdgeRatio uses this round's and last round's
  *   unconverged counts, round 1 uses HighP.
  */
@@ -80,6 +89,7 @@ typedef struct {
                                 3: BF16 rounding of the plain Ising log-odds */
     double storage_scale;    /* storage 1 (Ising): log-odds per unit of log2 of the stored
                                 word; storage 2: log-odds step of one integer unit */
+    int32_t dynamic_p;       /* RBP / RS: 1 = frontier fraction by the EdgeRatio switch */
 } orc_params;
 
 typedef struct {
@@ -119,14 +129,16 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
     out[3] = c3;
 }
 
-/* RnBP random filter draw for message e in round t of graph g. */
+/* RnBP random filter draw for message e in round t of graph g: one Philox
+ * block per four consecutive messages, counter (floor(e / 4), t, g, 0); message
+ * e takes word e mod 4. */
 static uint32_t rnbp_draw(uint64_t seed, uint32_t e, uint32_t t, uint32_t g)
 {
-    uint32_t ctr[4] = {e, t, g, 0u};
+    uint32_t ctr[4] = {e >> 2, t, g, 0u};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t out[4];
     orc_philox4x32_10(ctr, key, out);
-    return out[0];
+    return out[e & 3u];
 }
 
 /* ------------------------------------------------------------------------- */
@@ -135,6 +147,8 @@ typedef struct {
     const orc_problem *pb;
     int32_t *src;       /* [m] source vertex of each directed edge */
     double *psi_u;      /* [n*k] */
+    uint8_t *present;   /* [n*k] 0 where the unary log-potential is -inf: an absent state */
+    int32_t *k_present; /* [n] present states of each vertex */
     double *psi_p;      /* [m*k*k] (or [k*k] with stride 0 for the shared table) */
     int64_t pair_stride;
 } orc_model;
@@ -145,15 +159,28 @@ static int model_init(orc_model *md, const orc_problem *pb)
     int64_t m = pb->m;
     memset(md, 0, sizeof(*md));
     md->pb = pb;
+    md->psi_p = NULL;
+    md->present = NULL;
+    md->k_present = NULL;
+    md->psi_u = NULL;
     md->src = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
     md->psi_u = (double *)malloc(sizeof(double) * (size_t)n * (size_t)k + 8);
-    if (!md->src || !md->psi_u)
+    md->present = (uint8_t *)malloc((size_t)n * (size_t)k + 8);
+    md->k_present = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!md->src || !md->psi_u || !md->present || !md->k_present)
         return -1;
     for (int32_t i = 0; i < n; ++i)
         for (int64_t e = pb->row_ptr[i]; e < pb->row_ptr[i + 1]; ++e)
             md->src[e] = i;
-    for (int64_t q = 0; q < (int64_t)n * k; ++q)
+    for (int64_t q = 0; q < (int64_t)n * k; ++q) {
         md->psi_u[q] = exp((double)pb->unary_log[q]);
+        md->present[q] = !(isinf(pb->unary_log[q]) && pb->unary_log[q] < 0.0f);
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        md->k_present[i] = 0;
+        for (int32_t a = 0; a < k; ++a)
+            md->k_present[i] += md->present[(int64_t)i * k + a];
+    }
     if (pb->pair_kind == ORC_PAIR_SHARED) {
         md->pair_stride = 0;
         md->psi_p = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k);
@@ -188,6 +215,8 @@ static void model_free(orc_model *md)
 {
     free(md->src);
     free(md->psi_u);
+    free(md->present);
+    free(md->k_present);
     free(md->psi_p);
 }
 
@@ -210,6 +239,11 @@ static void message_update(const orc_model *md, const double *msg, int64_t e, do
         for (int32_t b = 0; b < k; ++b)
             c[b] += psi[(int64_t)a * k + b] * w;
     }
+    /* an absent state of j (unary log-potential -inf) carries no mass */
+    int32_t j = pb->col[e];
+    for (int32_t b = 0; b < k; ++b)
+        if (!md->present[(int64_t)j * k + b])
+            c[b] = 0.0;
     double z = 0.0;
     for (int32_t b = 0; b < k; ++b)
         z += c[b];
@@ -443,9 +477,13 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
         return -1;
     }
 
-    /* Section II-A: messages start uniform. */
-    for (size_t q = 0; q < (size_t)m * (size_t)k; ++q)
-        msg[q] = 1.0 / (double)k;
+    /* Section II-A: messages start uniform, over the present states of the
+     * destination vertex. */
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t j = pb->col[e];
+        for (int32_t x = 0; x < k; ++x)
+            msg[e * k + x] = md.present[(int64_t)j * k + x] ? 1.0 / (double)md.k_present[j] : 0.0;
+    }
     for (int64_t e = 0; e < m; ++e)
         store_round(pb, pr, msg + e * k);
 
@@ -487,6 +525,20 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
                 break;
         }
         t += 1;
+        /* Parallelism of this round (Section IV-A): RnBP, and RBP / RS with
+         * dynamic_p, switch between HighP (round 1, or EdgeRatio <= threshold)
+         * and LowP (EdgeRatio = this round's unconverged count over the
+         * previous round's > threshold); otherwise the fixed p. */
+        double p_round = pr->parallelism;
+        if (pr->schedule == ORC_RNBP || (pr->dynamic_p && pr->schedule != ORC_LBP)) {
+            if (t == 1) {
+                p_round = pr->high_p;
+            } else {
+                double ratio = (double)n_t / (double)n_prev;   /* EdgeRatio */
+                p_round = (ratio > pr->ratio_threshold) ? pr->parallelism : pr->high_p;
+            }
+        }
+        n_prev = n_t;
         const uint32_t *tin = follow ? pr->trace_in + (int64_t)(t - 1) * trace_words : NULL;
         uint32_t *tout = (pr->trace_out && t <= pr->trace_cap)
                              ? pr->trace_out + (int64_t)(t - 1) * trace_words : NULL;
@@ -504,8 +556,8 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
                 for (int32_t v = 0; v < n; ++v)
                     chosen[v] = (uint8_t)trace_get(tin, v);
             } else {
-                int64_t kv = pr->rs_roots_mode == 1 ? clamp_ceil(pr->parallelism, n, 1, n)
-                                                    : clamp_ceil(pr->parallelism, m, 1, n);
+                int64_t kv = pr->rs_roots_mode == 1 ? clamp_ceil(p_round, n, 1, n)
+                                                    : clamp_ceil(p_round, m, 1, n);
                 top_k(vres, n, kv, order, chosen);
             }
             if (tout)
@@ -547,15 +599,9 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
                 for (int64_t e = 0; e < m; ++e)
                     chosen[e] = 1;
             } else if (pr->schedule == ORC_RBP) {
-                top_k(r, m, clamp_ceil(pr->parallelism, m, 1, m), order, chosen);
+                top_k(r, m, clamp_ceil(p_round, m, 1, m), order, chosen);
             } else { /* RnBP */
-                double p;
-                if (t == 1) {
-                    p = pr->high_p;
-                } else {
-                    double ratio = (double)n_t / (double)n_prev;   /* EdgeRatio */
-                    p = (ratio > pr->ratio_threshold) ? pr->parallelism : pr->high_p;
-                }
+                double p = p_round;
                 int always = (p >= 1.0);
                 uint64_t thr = (p <= 0.0) ? 0u : (uint64_t)(p * 4294967296.0);
                 for (int64_t e = 0; e < m; ++e) {
@@ -567,7 +613,6 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
                     }
                 }
             }
-            n_prev = n_t;
             /* Update(frontier): simultaneous commit of the selected candidates. */
             for (int64_t e = 0; e < m; ++e) {
                 if (!chosen[e])

@@ -56,7 +56,8 @@ class bp_options(ctypes.Structure):
                 ("time_budget_ms", ctypes.c_double), ("graph_id_base", ctypes.c_uint32),
                 ("kernel_variant", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("potts_path", ctypes.c_int32), ("select_path", ctypes.c_int32),
-                ("splash_sweep", ctypes.c_int32), ("overlap_launches", ctypes.c_int32)]
+                ("splash_sweep", ctypes.c_int32), ("overlap_launches", ctypes.c_int32),
+                ("dynamic_p", ctypes.c_int32)]
 
 
 class bp_profile(ctypes.Structure):

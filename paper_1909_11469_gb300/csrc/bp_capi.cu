@@ -95,6 +95,7 @@ struct bp_graph {
     int dev = 0;
     int kp = 32;
     std::vector<int32_t> h_rev, h_gv_off, h_ge_off;
+    std::vector<int32_t> h_col, h_src;   // destination and source vertex of every directed edge
     // structure
     int32_t *d_row_ptr = nullptr, *d_col = nullptr, *d_rev = nullptr, *d_gid = nullptr;
     int32_t *d_gv_off = nullptr, *d_ge_off = nullptr;
@@ -106,6 +107,7 @@ struct bp_graph {
     int32_t sel_smem_bytes = 0;   // staged keys of the largest graph, capped
     float *d_unary = nullptr, *d_udiff32 = nullptr, *d_q32 = nullptr, *d_pair = nullptr,
           *d_psi_shared = nullptr;
+    int32_t *d_kpresent = nullptr;   // present states per vertex, when some state is absent
     double *d_udiff64 = nullptr, *d_q64 = nullptr;
     // run buffers
     int buf_dtype = -1;
@@ -210,7 +212,11 @@ int32_t resolve_variant(const bp_graph *g, int schedule, int dtype, int32_t requ
         if (it != g_tune_table.end())
             return it->second & 0xff;
     }
-    return (g->max_deg <= 4 && dtype != DT_F64) ? 4 : 1;
+    if (dtype == DT_F64)
+        return 1;
+    if (g->max_deg <= 4)
+        return 4;
+    return g->wtiles_ok ? 6 : 1;
 }
 
 // Selection path of a run: the requested one, else the tuned one of the
@@ -275,6 +281,7 @@ DevGraph dev_graph(const bp_graph *g, int dtype)
     d.q64 = g->d_q64;
     d.pair = g->d_pair;
     d.psi_shared = g->d_psi_shared;
+    d.kpresent = g->d_kpresent;
     d.wtiles = g->d_wtiles;
     d.n_wtiles = g->n_wtiles;
     return d;
@@ -425,6 +432,8 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     g->G = n_graphs;
     g->kp = k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32));
     g->h_rev.assign(rev, rev + M);
+    g->h_col.assign(col, col + M);
+    g->h_src = src;
     g->h_gv_off = gv;
     g->h_ge_off = ge;
     int64_t max_keys = 1;
@@ -708,6 +717,15 @@ bool all_finite(const float *p, size_t n)
     return true;
 }
 
+// Finite or -inf (an absent state, or an impossible state pair) everywhere.
+bool finite_or_neg_inf(const float *p, size_t n)
+{
+    for (size_t q = 0; q < n; ++q)
+        if (!std::isfinite(p[q]) && !(std::isinf(p[q]) && p[q] < 0.0f))
+            return false;
+    return true;
+}
+
 }  // namespace
 
 // Run parameters of (schedule, parallelism, eps, max_rounds, opt) on handle g
@@ -727,6 +745,7 @@ static int build_run_params(const bp_graph *g, int32_t schedule, double parallel
     rp.pdl = opt.overlap_launches == 2 ? 0 : 1;
     rp.splash_depth = opt.splash_depth;
     rp.rs_roots_mode = opt.rs_roots_mode;
+    rp.dynamic_p = (opt.dynamic_p && (schedule == BP_RBP || schedule == BP_RS)) ? 1 : 0;
     rp.record_trace = (opt.record_trace && opt.trace_capacity > 0 && schedule != BP_LBP) ? 1 : 0;
     rp.trace_capacity = rp.record_trace ? opt.trace_capacity : 0;
     const int64_t trace_count = schedule == BP_RS ? g->n : g->M;
@@ -807,13 +826,27 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
         return fail(BP_ERR_INVALID_ARG, "unknown pair kind");
     if (pair_kind == BP_PAIR_ISING_BETA && k != 2)
         return fail(BP_ERR_INVALID_ARG, "Ising beta potentials need n_states = 2");
-    if (!all_finite(unary_log, (size_t)n * k))
-        return fail(BP_ERR_NONFINITE, "non-finite unary log-potential");
+    if (!finite_or_neg_inf(unary_log, (size_t)n * k))
+        return fail(BP_ERR_NONFINITE, "NaN or +inf unary log-potential");
+    // a state with unary log-potential -inf is absent (variable state counts)
+    std::vector<int32_t> kpresent((size_t)n, k);
+    bool absent = false;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t x = 0; x < k; ++x)
+            if (std::isinf(unary_log[(size_t)i * k + x])) {
+                --kpresent[(size_t)i];
+                absent = true;
+            }
+        if (kpresent[(size_t)i] == 0)
+            return fail(BP_ERR_NONFINITE, "vertex " + std::to_string(i) + " has no present state");
+    }
+    if (absent && pair_kind != BP_PAIR_TABLE)
+        return fail(BP_ERR_UNSUPPORTED, "absent states (unary -inf) need per-edge tables (BP_PAIR_TABLE)");
     size_t plen = pair_kind == BP_PAIR_ISING_BETA ? (size_t)M
                   : pair_kind == BP_PAIR_TABLE    ? (size_t)M * k * k
                                                   : (size_t)k * k;
-    if (plen && !all_finite(pair_log, plen))
-        return fail(BP_ERR_NONFINITE, "non-finite pairwise log-potential");
+    if (plen && !(pair_kind == BP_PAIR_TABLE ? finite_or_neg_inf(pair_log, plen) : all_finite(pair_log, plen)))
+        return fail(BP_ERR_NONFINITE, "NaN, +inf or (outside tables) -inf pairwise log-potential");
     if (pair_kind == BP_PAIR_ISING_BETA) {
         for (int64_t e = 0; e < M; ++e)
             if (pair_log[e] != pair_log[g->h_rev[(size_t)e]])
@@ -843,8 +876,14 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
     dfree(g->d_q64);
     dfree(g->d_pair);
     dfree(g->d_psi_shared);
+    dfree(g->d_kpresent);
     clear_cache(g);
     int rc;
+    if (absent) {
+        if ((rc = dalloc(&g->d_kpresent, (size_t)n)))
+            return rc;
+        BP_CK(cudaMemcpy(g->d_kpresent, kpresent.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
+    }
     if ((rc = dalloc(&g->d_unary, (size_t)n * k)))
         return rc;
     BP_CK(cudaMemcpy(g->d_unary, unary_log, sizeof(float) * (size_t)n * k, cudaMemcpyHostToDevice));
@@ -886,8 +925,26 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
     } else if (pair_kind == BP_PAIR_TABLE) {
         if ((rc = dalloc(&g->d_pair, plen)))
             return rc;
-        if (plen)
+        if (plen && absent) {
+            // no mass on an absent state: a pair involving one is impossible
+            // (log-potential -inf), so a message into vertex j is a
+            // distribution over j's present states; table(rev e) stays the
+            // transpose of table(e)
+            std::vector<float> tab(pair_log, pair_log + plen);
+            const float ninf = -std::numeric_limits<float>::infinity();
+            for (int64_t e = 0; e < M; ++e) {
+                const float *ui = unary_log + (size_t)g->h_src[(size_t)e] * k;
+                const float *uj = unary_log + (size_t)g->h_col[(size_t)e] * k;
+                float *t = tab.data() + (size_t)e * k * k;
+                for (int32_t x = 0; x < k; ++x)
+                    for (int32_t y = 0; y < k; ++y)
+                        if (std::isinf(ui[x]) || std::isinf(uj[y]))
+                            t[x * k + y] = ninf;
+            }
+            BP_CK(cudaMemcpy(g->d_pair, tab.data(), sizeof(float) * plen, cudaMemcpyHostToDevice));
+        } else if (plen) {
             BP_CK(cudaMemcpy(g->d_pair, pair_log, sizeof(float) * plen, cudaMemcpyHostToDevice));
+        }
     } else {
         if ((rc = dalloc(&g->d_pair, plen)) || (rc = dalloc(&g->d_psi_shared, plen)))
             return rc;
@@ -939,6 +996,10 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "splash_sweep must be 0..3");
     if (opt.overlap_launches < 0 || opt.overlap_launches > 2)
         return fail(BP_ERR_INVALID_ARG, "overlap_launches must be 0..2");
+    if (opt.dynamic_p < 0 || opt.dynamic_p > 1)
+        return fail(BP_ERR_INVALID_ARG, "dynamic_p must be 0 or 1");
+    if (opt.dynamic_p && (schedule == BP_RBP || schedule == BP_RS) && !(opt.high_p > 0.0))
+        return fail(BP_ERR_INVALID_ARG, "dynamic_p needs high_p > 0 (the RBP / RS HighP fraction)");
     if (opt.kernel_variant < 0 || opt.kernel_variant > 6)
         return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 6]");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
@@ -1562,6 +1623,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_q64);
     dfree(g->d_pair);
     dfree(g->d_psi_shared);
+    dfree(g->d_kpresent);
     dfree(g->d_level);
     dfree(g->d_lvl_list);
     dfree(g->d_lvl_cnt);

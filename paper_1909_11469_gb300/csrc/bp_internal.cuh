@@ -66,6 +66,7 @@ struct DevGraph {
     const double *q64;        // [M]
     const float *pair;        // table [M*k*k] (log) or shared [k*k] (log)
     const float *psi_shared;  // [k*k] exp(Theta - max Theta)     (shared)
+    const int32_t *kpresent;  // [n] present states per vertex (unary > -inf), or null when all k are
     // streamed update: warp tiles {first vertex, first edge, graph, vertex
     // count}, every vertex in one tile, and a sentinel {n, M, -1, 0};
     // n_wtiles = 0 when a vertex has > STREAM_WT edges
@@ -95,6 +96,7 @@ struct RunParams {
     int32_t sel_grid;         // grid-wide selection: bit 0 RBP, bit 1 RS (keys the captured rounds)
     int32_t pdl;              // 1: the update, decision and RnBP commit kernels are launched
                               // with programmatic stream serialization
+    int32_t dynamic_p;        // 1: RBP / RS frontier fraction switched per round by EdgeRatio
     int32_t sweep_form;       // RS sweeps (binary, level lists): SWEEP_LIST one launch per
                               // sub-step, SWEEP_CLUSTER one cluster kernel per round over
                               // per-graph level lists, SWEEP_PAIR one launch per sub-step
@@ -150,6 +152,19 @@ struct DevRun {
 __device__ __forceinline__ double graph_low_p(const DevRun &dr, const RunParams &rp, int gg)
 {
     return dr.graph_p ? dr.graph_p[gg] : rp.low_p;
+}
+
+// EdgeRatio switch of Section IV-A for committing round `rounds` (1-based)
+// with n_now messages of residual >= eps now and n_prev at the previous
+// evaluation: HighP in round 1, then LowP when n_now / n_prev > the threshold
+// (bad convergence), else HighP. RnBP uses it every round; RBP and RS use it
+// with dynamic_p for their frontier fraction.
+__device__ __forceinline__ double edge_ratio_p(const RunParams &rp, double low_p, int rounds,
+                                               unsigned long long n_now, unsigned long long n_prev)
+{
+    if (rounds == 1)
+        return rp.high_p;
+    return ((double)n_now / (double)n_prev > rp.ratio_threshold) ? low_p : rp.high_p;
 }
 
 // Programmatic dependent launch: a grid launched with programmatic stream
@@ -284,8 +299,8 @@ __device__ __forceinline__ double ising_logodds(double q, double h)
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11), one block of four words.
-__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                                 uint32_t k0, uint32_t k1)
+__device__ __forceinline__ uint4 philox4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                         uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -302,17 +317,28 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
         c2 = n2;
         c3 = lo0;
     }
-    return c0;
+    return make_uint4(c0, c1, c2, c3);
 }
 
+// RnBP random filter (Section IV-A): the Philox block of key seed and counter
+// (local_edge / 4, round, graph id, 0) serves four consecutive messages of a
+// graph; message local_edge draws word local_edge mod 4 and is selected when
+// it is below the round's threshold floor(p 2^32).
+__device__ __forceinline__ uint4 rnbp_block(const RunParams &rp, uint32_t quad, uint32_t round, uint32_t graph)
+{
+    return philox4(quad, round, rp.graph_id_base + graph, 0u, (uint32_t)(rp.seed & 0xffffffffu),
+                   (uint32_t)(rp.seed >> 32));
+}
+__device__ __forceinline__ uint32_t rnbp_word(const uint4 &b, uint32_t j)
+{
+    return j == 0 ? b.x : (j == 1 ? b.y : (j == 2 ? b.z : b.w));
+}
 __device__ __forceinline__ bool rnbp_pick(const RunParams &rp, uint32_t local_edge, uint32_t round,
                                           uint32_t graph, const GState &st)
 {
     if (st.always)
         return true;
-    uint32_t w = philox_word0(local_edge, round, rp.graph_id_base + graph, 0u,
-                              (uint32_t)(rp.seed & 0xffffffffu), (uint32_t)(rp.seed >> 32));
-    return w < st.thr;
+    return rnbp_word(rnbp_block(rp, local_edge >> 2, round, graph), local_edge & 3u) < st.thr;
 }
 
 // ---------------------------------------------------------------------------

@@ -249,17 +249,15 @@ __global__ void k_decide(DevGraph g, DevRun dr, RunParams rp)
             st.cur ^= 1;
             st.committed += (unsigned long long)Mg;
         } else if (rp.schedule == SCHED_RNBP) {
-            double p;
-            if (st.rounds == 1)
-                p = rp.high_p;
-            else
-                p = ((double)c / (double)st.n_prev > rp.ratio_threshold) ? graph_low_p(dr, rp, gg) : rp.high_p;
+            const double p = edge_ratio_p(rp, graph_low_p(dr, rp, gg), st.rounds, c, st.n_prev);
             st.always = (p >= 1.0) ? 1 : 0;
             st.thr = (p <= 0.0 || p >= 1.0) ? 0u : (uint32_t)(uint64_t)(p * 4294967296.0);
         } else {
             const int64_t base = (rp.schedule == SCHED_RS && rp.rs_roots_mode == 1) ? ng : Mg;
             const int64_t hi = (rp.schedule == SCHED_RS) ? ng : Mg;
-            double v = ceil(graph_low_p(dr, rp, gg) * (double)base);
+            const double p = rp.dynamic_p ? edge_ratio_p(rp, graph_low_p(dr, rp, gg), st.rounds, c, st.n_prev)
+                                          : graph_low_p(dr, rp, gg);
+            double v = ceil(p * (double)base);
             int64_t kk = (v > (double)hi) ? hi : (int64_t)v;
             kk = kk < 1 ? 1 : kk;
             kk = kk > hi ? hi : kk;
@@ -543,6 +541,110 @@ __global__ void __launch_bounds__(TILE_V) k_eval_bin_tiled(DevGraph g, DevRun dr
 // edge and its graph's round state; an edge pass reads the residuals
 // contiguously, draws Philox for the messages with residual >= eps and copies
 // the selected candidates.
+// RnBP commit over the warp tiles of the streamed update (single-graph runs
+// of consecutive vertices, <= 128 out-edges). A warp takes TPW consecutive
+// tiles and issues the loads of all of them before it uses any: the tile
+// records, then the graphs' round states and the residuals of the tiles'
+// messages. Each lane takes aligned quads of four consecutive messages of a
+// graph, which share one Philox block (one block per quad instead of one
+// per message), applies the eps filter and copies the selected candidates.
+// The kernel is bound by the latency of that short dependent chain (record
+// -> residual and state -> candidate -> store), so it keeps TPW chains in
+// flight per warp and many warps per SM; the commits of a tile are added
+// with one atomic.
+constexpr int COMMIT_TPW = 2;
+
+template <typename S>
+__global__ void __launch_bounds__(BLOCK, 3) k_commit_rnbp_wt(DevGraph g, DevRun dr, RunParams rp)
+{
+    griddep_launch_dependents();
+    using RT = typename ResidT<S>::T;
+    constexpr int QPL = 2;   // quads per lane: a tile of <= 128 edges meets <= 34 quads
+    const int lane = threadIdx.x & 31;
+    const int w = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int e0[COMMIT_TPW], e1[COMMIT_TPW], gg[COMMIT_TPW], ge0[COMMIT_TPW];
+#pragma unroll
+    for (int i = 0; i < COMMIT_TPW; ++i) {
+        const int t = w * COMMIT_TPW + i;
+        e0[i] = e1[i] = 0;
+        gg[i] = 0;
+        ge0[i] = 0;
+        if (t < g.n_wtiles) {
+            const int4 rec = g.wtiles[t];
+            e0[i] = rec.y;
+            e1[i] = g.wtiles[t + 1].y;
+            gg[i] = rec.z;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < COMMIT_TPW; ++i)
+        if (e1[i] > e0[i])
+            ge0[i] = g.ge_off[gg[i]];
+    griddep_wait();   // residuals, candidates and round state come from the previous kernels
+    const RT *R = (const RT *)dr.resid;
+    RT r[COMMIT_TPW][QPL][4];
+    // the graph's round state: status, rounds, RnBP threshold / always-flag
+    int st_status[COMMIT_TPW], st_rounds[COMMIT_TPW], st_always[COMMIT_TPW];
+    uint32_t st_thr[COMMIT_TPW];
+#pragma unroll
+    for (int i = 0; i < COMMIT_TPW; ++i) {
+        const int q0 = (e0[i] - ge0[i]) >> 2, q1 = (e1[i] - 1 - ge0[i]) >> 2;
+#pragma unroll
+        for (int k = 0; k < QPL; ++k) {
+            const int q = q0 + lane + 32 * k;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int e = ge0[i] + 4 * q + j;
+                r[i][k][j] = (q <= q1 && e >= e0[i] && e < e1[i]) ? R[e] : (RT)0;
+            }
+        }
+        const GState *sp = dr.gs + gg[i];
+        st_status[i] = sp->status;
+        st_rounds[i] = sp->rounds;
+        st_always[i] = sp->always;
+        st_thr[i] = sp->thr;
+    }
+    S *dst = (S *)dr.msg[0];
+    const S *src = (const S *)dr.msg[1];
+    const int epm = g.epm;
+    const RT eps = eps_in(rp, (RT)0);
+#pragma unroll
+    for (int i = 0; i < COMMIT_TPW; ++i) {
+        if (e1[i] == e0[i] || st_status[i] != ST_RUNNING)
+            continue;
+        const bool tr = rp.record_trace && st_rounds[i] <= rp.trace_capacity;
+        const int q0 = (e0[i] - ge0[i]) >> 2, q1 = (e1[i] - 1 - ge0[i]) >> 2;
+        unsigned int c = 0;
+#pragma unroll
+        for (int k = 0; k < QPL; ++k) {
+            const int q = q0 + lane + 32 * k;
+            if (q > q1)
+                continue;
+            const bool any = r[i][k][0] >= eps || r[i][k][1] >= eps || r[i][k][2] >= eps || r[i][k][3] >= eps;
+            if (!any)
+                continue;
+            uint4 wd = make_uint4(0u, 0u, 0u, 0u);
+            if (!st_always[i])
+                wd = rnbp_block(rp, (uint32_t)q, (uint32_t)st_rounds[i], (uint32_t)gg[i]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int e = ge0[i] + 4 * q + j;
+                if (e < e0[i] || e >= e1[i] || r[i][k][j] < eps ||
+                    !(st_always[i] || rnbp_word(wd, (uint32_t)j) < st_thr[i]))
+                    continue;
+                for (int x = 0; x < epm; ++x)
+                    dst[(size_t)e * epm + x] = src[(size_t)e * epm + x];
+                ++c;
+                if (tr)
+                    atomicOr(&dr.trace[(size_t)(st_rounds[i] - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
+            }
+        }
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0 && c)
+            atomicAdd(&dr.gs[gg[i]].committed, (unsigned long long)c);
+    }
+}
+
 template <typename S>
 __global__ void __launch_bounds__(TILE_V) k_commit_rnbp_tiled(DevGraph g, DevRun dr, RunParams rp)
 {
@@ -832,6 +934,24 @@ __global__ void k_init_msgs(S *a, S *b, size_t count, double value, float sc)
     }
 }
 
+// Start messages of a k-state layout with absent states: a message into
+// vertex j is uniform over j's present states and carries no mass (the log
+// floor) on the absent ones.
+template <typename S>
+__global__ void k_init_msgs_var(DevGraph g, S *a, S *b)
+{
+    using A = typename Store<S>::A;
+    const size_t count = (size_t)g.M * (size_t)g.k;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(t / (size_t)g.k), x = (int)(t % (size_t)g.k);
+        const int j = g.col[e];
+        const bool present = !isinf(g.unary[(size_t)j * g.k + x]);
+        const A v = present ? (A)(-log((double)g.kpresent[j])) : log_floor<A>();
+        Store<S>::st(a + t, v, g.qscale);
+        Store<S>::st(b + t, v, g.qscale);
+    }
+}
+
 __global__ void k_init_state(DevRun dr, int G)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G * NSUB; t += gridDim.x * blockDim.x) {
@@ -885,8 +1005,17 @@ __global__ void __launch_bounds__(BLOCK) k_beliefs_bin(DevGraph g, DevRun dr)
     double h = g.udiff64[i];
     for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
         h += (double)Store<S>::ld(cur + g.rev[e], g.qscale);
-    dr.beliefs[2 * (size_t)i + 1] = 1.0 / (1.0 + exp(-h));
-    dr.beliefs[2 * (size_t)i] = 1.0 / (1.0 + exp(h));
+    if constexpr (sizeof(typename Store<S>::A) == 8) {
+        dr.beliefs[2 * (size_t)i + 1] = 1.0 / (1.0 + exp(-h));
+        dr.beliefs[2 * (size_t)i] = 1.0 / (1.0 + exp(h));
+    } else {
+        // FP32 messages: exp in FP32 (relative error ~1e-7, below the
+        // messages' own), the normalisation in FP64; e = exp(-|h|) <= 1
+        const double e = (double)__expf(-(float)fabs(h));
+        const double hi = 1.0 / (1.0 + e), lo = e / (1.0 + e);
+        dr.beliefs[2 * (size_t)i + 1] = h >= 0.0 ? hi : lo;
+        dr.beliefs[2 * (size_t)i] = h >= 0.0 ? lo : hi;
+    }
 }
 
 template <typename S, int KP>
@@ -1080,6 +1209,12 @@ void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const Ru
 {
     if (g.n == 0)
         return;
+    if (g.n_wtiles > 0) {
+        // COMMIT_TPW warp tiles per warp
+        BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_wt<S>,
+                                       blocks_for(g.n_wtiles, COMMIT_TPW * (BLOCK / 32)), BLOCK, s, g, dr, rp)));
+        return;
+    }
     BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_tiled<S>, blocks_for(g.n, TILE_V), TILE_V, s, g, dr, rp)));
 }
 
@@ -1137,7 +1272,11 @@ void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s)
     double v = (g.epm == 1) ? 0.0 : -log((double)g.k);
     if (count) {
         int nb = (int)std::min<size_t>((count + BLOCK - 1) / BLOCK, 152 * 16);
-        BPG_DISPATCH4(dtype, (k_init_msgs<S><<<nb, BLOCK, 0, s>>>((S *)dr.msg[0], (S *)dr.msg[1], count, v, g.qscale)));
+        if (g.epm > 1 && g.kpresent)
+            BPG_DISPATCH3(dtype, (k_init_msgs_var<S><<<nb, BLOCK, 0, s>>>(g, (S *)dr.msg[0], (S *)dr.msg[1])))
+        else
+            BPG_DISPATCH4(dtype, (k_init_msgs<S><<<nb, BLOCK, 0, s>>>((S *)dr.msg[0], (S *)dr.msg[1], count, v,
+                                                                      g.qscale)));
     }
     int nb2 = blocks_for(g.G * NSUB, BLOCK);
     k_init_state<<<nb2, BLOCK, 0, s>>>(dr, g.G);

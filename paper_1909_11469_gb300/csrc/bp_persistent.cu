@@ -158,11 +158,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_persistent(DevGraph g, DevRun dr
             if (SCHED == SCHED_LBP) {
                 cur ^= 1;
             } else if (SCHED == SCHED_RNBP) {
-                double p;
-                if (rounds == 1)
-                    p = rp.high_p;
-                else
-                    p = ((double)ntot / (double)n_prev > rp.ratio_threshold) ? graph_low_p(dr, rp, gg) : rp.high_p;
+                const double p = edge_ratio_p(rp, graph_low_p(dr, rp, gg), rounds, ntot, n_prev);
                 GState sel;
                 sel.always = (p >= 1.0) ? 1 : 0;
                 sel.thr = (p <= 0.0 || p >= 1.0) ? 0u : (uint32_t)(uint64_t)(p * 4294967296.0);
@@ -178,9 +174,10 @@ __global__ void __launch_bounds__(PT_THREADS) k_persistent(DevGraph g, DevRun dr
                             atomicOr(&dr.trace[(size_t)(rounds - 1) * rp.trace_words + (ge >> 5)], 1u << (ge & 31));
                     }
                 }
-                n_prev = ntot;
             } else if (SCHED == SCHED_RBP) {
-                double v = ceil(graph_low_p(dr, rp, gg) * (double)Mg);
+                const double p = rp.dynamic_p ? edge_ratio_p(rp, graph_low_p(dr, rp, gg), rounds, ntot, n_prev)
+                                              : graph_low_p(dr, rp, gg);
+                double v = ceil(p * (double)Mg);
                 long long kk = (v > (double)Mg) ? Mg : (long long)v;
                 kk = kk < 1 ? 1 : (kk > Mg ? Mg : kk);
                 rbp_committed += (unsigned long long)kk;
@@ -206,7 +203,9 @@ __global__ void __launch_bounds__(PT_THREADS) k_persistent(DevGraph g, DevRun dr
                 });
             } else {   // SCHED_RS
                 const int64_t base = (rp.rs_roots_mode == 1) ? nv : Mg;
-                double v = ceil(graph_low_p(dr, rp, gg) * (double)base);
+                const double p = rp.dynamic_p ? edge_ratio_p(rp, graph_low_p(dr, rp, gg), rounds, ntot, n_prev)
+                                              : graph_low_p(dr, rp, gg);
+                double v = ceil(p * (double)base);
                 long long kk = (v > (double)nv) ? nv : (long long)v;
                 kk = kk < 1 ? 1 : (kk > nv ? nv : kk);
                 const int nl = vhi - vlo;
@@ -254,6 +253,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_persistent(DevGraph g, DevRun dr
                     cl.sync();
                 }
             }
+            n_prev = ntot;
             cl.sync();   // frontier writes are visible before the next evaluation
         }
 

@@ -110,16 +110,16 @@ __device__ __forceinline__ void bulk_load(unsigned dst, const void *src, unsigne
 }
 
 // (max residual, count) of one graph from every lane of a warp into a
-// reduction sub-slot.
-template <typename A>
-__device__ __forceinline__ void sw_flush(const DevRun &dr, int gg, A maxa, unsigned cnt, int slot)
+// reduction sub-slot. The residuals are non-negative floats, whose bit
+// patterns order like the values, so the warp max is one integer reduction.
+__device__ __forceinline__ void sw_flush(const DevRun &dr, int gg, float maxa, unsigned cnt, int slot)
 {
-    unsigned long long mb = (unsigned long long)__double_as_longlong((double)maxa);
-    mb = warp_max_u64(mb);
-    cnt = warp_sum_u32(cnt);
+    const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(maxa));
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
     if ((threadIdx.x & 31) == 0 && gg >= 0) {
         if (mb)
-            atomicMax(&dr.red_max[(size_t)gg * NSUB + slot], mb);
+            atomicMax(&dr.red_max[(size_t)gg * NSUB + slot],
+                      (unsigned long long)__double_as_longlong((double)__uint_as_float(mb)));
         if (cnt)
             atomicAdd(&dr.red_cnt[(size_t)gg * NSUB + slot], cnt);
     }

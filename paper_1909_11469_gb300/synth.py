@@ -230,6 +230,49 @@ def potts_grid(side: int, k: int, seed: int, noise_std: float = 0.3,
                    name=f"potts{side}x{cols}_k{k}_s{seed}")
 
 
+def protein_like(n: int, seed: int, k_min: int = 2, k_max: int = 32, attach: int = 2,
+                 pair_std: float = 1.0, tree: bool = False) -> Problem:
+    """Synthetic stand-in with the shape of the paper's protein-folding graphs
+    (Section IV-E: 2 to 81 settings per vertex, highly irregular structure; the
+    dataset itself is not available): vertices join by preferential attachment,
+    each new vertex linking to `attach` earlier ones (1 when tree=True) with
+    probability proportional to degree + 1; vertex v has k_v states, k_v drawn
+    log-uniform in [k_min, k_max] (an integer); the layout has k_max states and
+    the absent ones carry unary log-potential -inf; present unaries ~ N(0, 1);
+    one pairwise log-table ~ N(0, pair_std^2) per undirected edge, stored per
+    directed edge with table[rev e] = table[e] transposed.
+    Draw order: k_v, edges, unaries, tables."""
+    rng = _rng(seed)
+    kv = np.floor(np.exp(rng.uniform(np.log(k_min), np.log(k_max + 1), size=n))).astype(np.int64)
+    kv = np.clip(kv, k_min, k_max)
+    deg = np.zeros(n, dtype=np.float64)
+    ei, ej = [], []
+    links = 1 if tree else attach
+    for v in range(1, n):
+        cnt = min(links, v)
+        w = deg[:v] + 1.0
+        targets = rng.choice(v, size=cnt, replace=False, p=w / w.sum())
+        for t in targets:
+            ei.append(int(t))
+            ej.append(v)
+            deg[t] += 1
+            deg[v] += 1
+    row_ptr, col, rev = csr_from_undirected(n, np.array(ei, np.int64), np.array(ej, np.int64))
+    unary = rng.standard_normal(size=(n, k_max))
+    unary[np.arange(k_max)[None, :] >= kv[:, None]] = -np.inf
+    und = _undirected_positions(row_ptr, col)
+    tables = np.zeros((col.shape[0], k_max, k_max))
+    for e in und:
+        t = rng.normal(0.0, pair_std, size=(k_max, k_max))
+        tables[e] = t
+        tables[rev[e]] = t.T
+    return Problem(n=n, k=k_max, row_ptr=row_ptr, col=col, rev=rev,
+                   unary_log=unary.astype(np.float32).ravel(), pair_kind=PAIR_TABLE,
+                   pair_log=tables.astype(np.float32).ravel(),
+                   graph_var_offsets=np.array([0, n], dtype=np.int64),
+                   name=f"protein_like{n}_k{k_min}-{k_max}_s{seed}")
+
+
 def random_table_graph(n: int, k: int, extra_edges: int, seed: int,
                        unary_std: float = 1.0, pair_std: float = 1.0) -> Problem:
     """Random connected graph (a random tree plus extra random edges) with a

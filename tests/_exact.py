@@ -148,3 +148,72 @@ def serial_rbp(prob, eps: float, max_updates: int):
             version[f] += 1
             heapq.heappush(heap, (-res[f], f, int(version[f])))
         assert int(src[e]) >= 0
+
+
+def grid_marginals(prob, rows: int, cols: int) -> np.ndarray:
+    """Exact marginals of a binary rows x cols grid MRF (vertex r * cols + c)
+    by row transfer matrices: a row's 2^cols joint states carry the row's
+    unary and horizontal factors; the vertical factors between rows r and r+1
+    form a 2^cols x 2^cols matrix; a forward and a backward pass over the rows
+    (each step renormalised) give every row's joint distribution, summed to
+    vertex marginals. Exact for any coupling; cols <= 12."""
+    assert prob.k == 2 and prob.n == rows * cols and cols <= 12
+    S = 1 << cols
+    bits = ((np.arange(S)[:, None] >> np.arange(cols)[None, :]) & 1).astype(np.int64)   # [S, cols]
+    unary = prob.unary_log.astype(np.float64).reshape(prob.n, 2)
+    src = src_of(prob)
+    horiz = {}
+    vert = {}
+    for e in range(prob.m):
+        i, j = int(src[e]), int(prob.col[e])
+        if i >= j:
+            continue
+        th = pair_table(prob, e)
+        if j == i + 1 and i // cols == j // cols:
+            horiz[i] = th
+        elif j == i + cols:
+            vert[i] = th
+        else:
+            raise ValueError("not a 4-neighbour grid")
+    row_log = np.zeros((rows, S))
+    for r in range(rows):
+        for c in range(cols):
+            v = r * cols + c
+            row_log[r] += unary[v][bits[:, c]]
+            if c + 1 < cols:
+                row_log[r] += horiz[v][bits[:, c], bits[:, c + 1]]
+    trans = []
+    for r in range(rows - 1):
+        lt = np.zeros((S, S))
+        for c in range(cols):
+            v = r * cols + c
+            lt += vert[v][bits[:, c][:, None], bits[:, c][None, :]]
+        trans.append(np.exp(lt - lt.max()))
+    row_pot = np.exp(row_log - row_log.max(axis=1, keepdims=True))
+    fwd = np.zeros((rows, S))
+    bwd = np.ones((rows, S))
+    a = row_pot[0]
+    fwd[0] = a / a.sum()
+    for r in range(1, rows):
+        a = (fwd[r - 1] @ trans[r - 1]) * row_pot[r]
+        fwd[r] = a / a.sum()
+    for r in range(rows - 2, -1, -1):
+        b = trans[r] @ (row_pot[r + 1] * bwd[r + 1])
+        bwd[r] = b / b.sum()
+    out = np.zeros((prob.n, 2))
+    for r in range(rows):
+        joint = fwd[r] * bwd[r]
+        joint /= joint.sum()
+        for c in range(cols):
+            p1 = joint[bits[:, c] == 1].sum()
+            out[r * cols + c] = (1.0 - p1, p1)
+    return out
+
+
+def kl_divergence(p: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """KL(p || q) of each row of two [n, k] distribution arrays."""
+    p = np.asarray(p, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where(p > 0, p * (np.log(p) - np.log(q)), 0.0)
+    return t.sum(axis=1)

@@ -115,6 +115,32 @@ def test_er_batch_4096_sampled(variant):
         assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < 1e-9, gi
 
 
+@pytest.mark.parametrize("dtype,tol,T", [("f32", 1e-5, 20), ("bf16", 2e-3, 6)])
+@pytest.mark.parametrize("variant", [0, 6])
+def test_er_batch_4096_trace_follow(dtype, tol, T, variant):
+    """The benchmark's workload (4096 Erdos-Renyi graphs, 17.9M messages,
+    beta ~ U[-3, 3]): T RnBP rounds (LowP 0.5) with the automatic and the
+    streamed update mapping; on sampled graphs the exact FP64 oracle commits
+    the GPU's recorded frontiers of that graph. (beta up to 3 is far from
+    contracting, so BF16's rounding is followed for a shorter horizon.)"""
+    batch = synth.er_batch(4096, seed=0)
+    with bp.Graph(batch) as g:
+        g.run("rnbp", 0.5, eps=1e-4, max_rounds=T, msg_dtype=dtype, record_trace=1, trace_capacity=T,
+              seed=3, kernel_variant=variant, **_stream_opts())
+        bel = g.beliefs()
+        gst = g.graph_stats()
+        tr = g.trace("rnbp")
+    rng = np.random.default_rng(1)
+    for gi in rng.choice(4096, 8, replace=False):
+        gi = int(gi)
+        one = batch.graph(gi)
+        v0, v1 = batch.graph_var_offsets[gi], batch.graph_var_offsets[gi + 1]
+        e0, e1 = batch.row_ptr[v0], batch.row_ptr[v1]
+        rounds = gst[gi]["rounds"]
+        ref = oracle.run(one, "rnbp", eps=1e-4, trace_in=_bits(tr[:rounds], e0, e1), trace_rounds=rounds)
+        assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < tol, gi
+
+
 def test_potts256_k32():
     """Potts 256x256, k = 32, shared table: 3 RnBP rounds (LowP 0.5), every
     belief against the oracle following the GPU frontiers."""

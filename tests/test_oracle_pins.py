@@ -314,7 +314,7 @@ def test_rnbp_edge_ratio_switch(orc):
         p = 1.0 if t == 1 else (low if n_t / n_prev > 0.9 else 1.0)
         sel = np.zeros(prob.m, bool)
         for e in np.nonzero(r >= eps)[0]:
-            u = int(orc.philox4x32_10([e, t, 0, 0], [99, 0])[0])
+            u = int(orc.philox4x32_10([e // 4, t, 0, 0], [99, 0])[e % 4])
             sel[e] = p >= 1.0 or u < int(p * 2 ** 32)
         bits = np.unpackbits(res["trace"][t - 1].view(np.uint8), bitorder="little")[:prob.m]
         assert np.array_equal(bits.astype(bool), sel), t
@@ -567,3 +567,130 @@ def test_bf16_formats_against_the_exact_oracle(orc):
         assert exact["converged"] and code["converged"] and not plain["converged"]
         assert np.abs(code["beliefs"] - exact["beliefs"]).max() < 2e-4
         assert np.abs(plain["beliefs"] - exact["beliefs"]).max() > 2e-3
+
+
+# --------------------------------------------------------------------------- dynamic p for RBP / RS
+def _frontier_sizes(res):
+    return [int(np.unpackbits(row.view(np.uint8)).sum()) for row in res["trace"][:res["rounds"]]]
+
+
+@pytest.mark.parametrize("sched", ["rbp", "rs"])
+def test_dynamic_p_with_equal_fractions_is_the_fixed_schedule(orc, sched):
+    """LowP = HighP = p: the EdgeRatio switch picks p either way, so the run is
+    the fixed-p run, frontier for frontier."""
+    prob = synth.ising_grid(9, 2.0, seed=4)
+    a = orc.run(prob, sched, parallelism=0.05, eps=1e-6, max_rounds=60, trace_cap=60)
+    b = orc.run(prob, sched, parallelism=0.05, high_p=0.05, eps=1e-6, max_rounds=60, trace_cap=60, dynamic_p=1)
+    assert a["rounds"] == b["rounds"] and np.array_equal(a["trace"], b["trace"])
+    assert np.array_equal(a["beliefs"], b["beliefs"])
+
+
+def test_dynamic_p_never_low_is_lbp(orc):
+    """A threshold no EdgeRatio exceeds keeps HighP = 1: every round commits the
+    whole frontier, which is LBP's trajectory (RBP with p = 1 is LBP)."""
+    prob = synth.ising_grid(9, 1.5, seed=2)
+    lbp = orc.run(prob, "lbp", eps=1e-6, max_rounds=500)
+    dyn = orc.run(prob, "rbp", parallelism=0.01, high_p=1.0, ratio_threshold=1e300, eps=1e-6,
+                  max_rounds=500, dynamic_p=1)
+    assert lbp["converged"] and dyn["rounds"] == lbp["rounds"]
+    assert np.abs(dyn["beliefs"] - lbp["beliefs"]).max() < 1e-15
+
+
+@pytest.mark.parametrize("sched", ["rbp", "rs"])
+def test_dynamic_p_frontier_sizes_follow_edge_ratio(orc, sched):
+    """Round 1 uses HighP; round t > 1 uses LowP exactly when N_t / N_{t-1} > 0.9,
+    N_t = messages with residual >= eps at the evaluation before round t (read
+    from runs stopped after t - 1 rounds). RBP commits ceil(p M) messages, RS
+    picks ceil(p M) roots (clamped to n)."""
+    prob = synth.ising_grid(8, 2.5, seed=6)
+    lo, hi, T = 0.02, 0.3, 25
+    res = orc.run(prob, sched, parallelism=lo, high_p=hi, eps=1e-5, max_rounds=T, trace_cap=T, dynamic_p=1)
+    n_t = [orc.run(prob, sched, parallelism=lo, high_p=hi, eps=1e-5, max_rounds=t, dynamic_p=1)["final_unconverged"]
+           for t in range(T + 1)]
+    sizes = _frontier_sizes(res)
+    m, n = prob.m, prob.n
+    switched = 0
+    for t in range(1, res["rounds"] + 1):
+        p = hi if t == 1 else (lo if n_t[t - 1] / n_t[t - 2] > 0.9 else hi)
+        switched += p == lo
+        want = min(int(np.ceil(p * m)), m if sched == "rbp" else n)
+        if sched == "rbp":
+            assert sizes[t - 1] == want, (t, sizes[t - 1], want)
+        else:
+            assert sizes[t - 1] == want, (t, sizes[t - 1], want)
+    assert 0 < switched < res["rounds"] - 1
+
+
+# --------------------------------------------------------------------------- exact grid marginals, KL (Fig. 5)
+@pytest.mark.parametrize("rows,cols,seed", [(4, 4, 0), (3, 5, 1), (5, 3, 2), (4, 5, 3)])
+def test_grid_transfer_matrix_equals_brute_force(rows, cols, seed):
+    """The row transfer-matrix elimination used for 10x10 grids equals
+    enumeration of all 2^n assignments on grids small enough to enumerate."""
+    prob = synth.ising_grid(rows, 2.0, seed=seed, cols=cols)
+    assert np.abs(_exact.grid_marginals(prob, rows, cols) - _exact.brute_force_marginals(prob)).max() < 1e-13
+
+
+def test_kl_vs_exact_10x10_rnbp_matches_serial_rbp(orc):
+    """Section IV-E / Fig. 5: on the paper's 10x10 Ising set at C = 2, exact
+    marginals by elimination, KL(exact || beliefs) per graph for RnBP (LowP
+    0.7) and serial residual BP (RBP with one message per round). The paper
+    reports the same quality for both; here each KL is within 2% of the other
+    on every seed (observed at most 0.7%), and both are fixed points within
+    4 * 10 eps of each other (R18)."""
+    for seed in range(10):
+        prob = synth.paper_ising(10, 10, 2.0, seed=seed)
+        exact = _exact.grid_marginals(prob, 10, 10)
+        rn = orc.run(prob, "rnbp", parallelism=0.7, eps=1e-4, max_rounds=10000, seed=seed)
+        sr = orc.run(prob, "rbp", parallelism=1e-9, eps=1e-4, max_rounds=200000)
+        assert rn["converged"] and sr["converged"]
+        k_rn = _exact.kl_divergence(exact, rn["beliefs"]).sum()
+        k_sr = _exact.kl_divergence(exact, sr["beliefs"]).sum()
+        assert 0 < k_rn < 0.5 and abs(k_rn - k_sr) <= 0.02 * k_sr, (seed, k_rn, k_sr)
+        assert np.abs(rn["beliefs"] - sr["beliefs"]).max() < 4 * 10 * 1e-4
+
+
+# --------------------------------------------------------------------------- variable state counts
+def _pad_states(prob, k_to, seed=0):
+    """The same MRF with k_to states per vertex: the added states get unary
+    log-potential -inf (absent) and arbitrary pairwise entries."""
+    rng = np.random.default_rng(seed)
+    k = prob.k
+    un = np.full((prob.n, k_to), -np.inf, np.float32)
+    un[:, :k] = prob.unary_log.reshape(prob.n, k)
+    tab = rng.normal(0.0, 3.0, size=(prob.m, k_to, k_to)).astype(np.float32)
+    for e in range(prob.m):
+        r = prob.rev[e]
+        if r < e:
+            tab[e] = tab[r].T
+    tab[:, :k, :k] = prob.pair_log.reshape(prob.m, k, k)
+    return synth.Problem(prob.n, k_to, prob.row_ptr, prob.col, prob.rev, un.ravel(), synth.PAIR_TABLE,
+                         tab.ravel(), prob.graph_var_offsets)
+
+
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.4), ("rbp", 0.1), ("rs", 0.1)])
+def test_absent_states_equal_the_smaller_state_space(orc, sched, par):
+    """A 3-state MRF laid out with 5 states, the 2 extra ones absent (unary
+    -inf, arbitrary pairwise entries): every schedule takes the same frontiers
+    and rounds, and the present states' beliefs and messages equal the 3-state
+    run (absent states carry no mass)."""
+    prob = synth.random_table_graph(30, 3, extra_edges=15, seed=5, pair_std=0.6)
+    big = _pad_states(prob, 5)
+    a = orc.run(prob, sched, parallelism=par, high_p=0.9, eps=1e-6, max_rounds=300, seed=2, trace_cap=300)
+    b = orc.run(big, sched, parallelism=par, high_p=0.9, eps=1e-6, max_rounds=300, seed=2, trace_cap=300)
+    assert a["rounds"] == b["rounds"] and a["converged"] == b["converged"]
+    assert np.array_equal(a["trace"], b["trace"])
+    assert np.abs(b["beliefs"][:, :3] - a["beliefs"]).max() < 1e-14 and np.all(b["beliefs"][:, 3:] == 0)
+    assert np.abs(b["messages"][:, :3] - a["messages"]).max() < 1e-14 and np.all(b["messages"][:, 3:] == 0)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_variable_state_counts_tree_exact(orc, seed):
+    """Irregular trees whose vertices have 2 to 6 states: BP is exact on trees,
+    so every schedule's converged beliefs equal enumeration over the ragged
+    state spaces (absent states have zero probability)."""
+    prob = synth.protein_like(8, seed=seed, k_min=2, k_max=6, tree=True)
+    exact = _exact.brute_force_marginals(prob)
+    for sched, par in (("lbp", 1.0), ("rnbp", 0.5), ("rs", 0.2)):
+        res = orc.run(prob, sched, parallelism=par, eps=1e-12, max_rounds=2000, seed=seed)
+        assert res["converged"]
+        assert np.abs(res["beliefs"] - exact).max() < 1e-12

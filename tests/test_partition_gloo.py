@@ -118,7 +118,7 @@ def _replay_worker(rank, world, port, sched, par, owner, out):
                 pick = np.zeros(plan.n_local_edges, bool)
                 for le, ge in enumerate(plan.edges):
                     if r[le] >= eps:
-                        w = int(oracle.philox4x32_10([int(ge), t, 0, 0], [0, 0])[0])
+                        w = int(oracle.philox4x32_10([int(ge) // 4, t, 0, 0], [0, 0])[int(ge) % 4])
                         pick[le] = p >= 1.0 or w < thr
             n_prev = n_t
             msg[:plan.n_local_edges][pick] = cand[pick]
