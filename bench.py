@@ -140,8 +140,7 @@ def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kern
             phase[key] += pr[key]
     achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
     mappings = sorted({pr.get("kernel_variant", 1) for _, _, _, pr, _ in step})
-    names = {1: "k_eval_bin", 2: "k_eval_bin_tiled", 3: "k_eval_bin", 4: "k_eval_bin_pf<4 edges>",
-             5: "k_eval_bin_pf<8 edges>", 6: "k_eval_bin_stream"}
+    names = {1: "k_eval_bin", 3: "k_eval_bin", 4: "k_eval_bin_pf<4 edges>", 6: "k_eval_bin_stream"}
     kname = " / ".join(dict.fromkeys(names.get(v, "k_eval_bin") for v in mappings))
     in_step = {"achieved": achieved, "frac": (achieved / peak) if achieved else None,
                "avg_launch_us": 1e3 * eval_ms / max(eval_launches, 1)}
@@ -169,10 +168,8 @@ def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kern
 
 
 def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str):
-    """Roofline of the Residual Splash sweep kernel from a profiled step:
-    k_splash_sweep_cluster (every sub-step of a round in one launch, a cluster
-    per graph) or k_splash_list_step (one launch per sub-step), whichever the
-    runs used. The sweeps run over per-level vertex lists: per evaluated
+    """Roofline of the Residual Splash sweep kernel k_splash_list_step (one
+    launch per sub-step) from a profiled step. The sweeps run over per-level vertex lists: per evaluated
     message rev, col, the source's level, the incoming message, exp(-2 beta) and
     the written candidate (13 + 2 s B), per evaluated vertex its list entry,
     row_ptr and unary log-odds (16 B, spread over its d-bar out-messages); per
@@ -180,11 +177,10 @@ def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str)
     list entry and row_ptr (12 B). Every evaluated message is committed once."""
     s = MSG_BYTES[dtype]
     dbar = m / max(n, 1)
-    b, ms, launches, form = 0.0, 0.0, 0, 0
+    b, ms, launches = 0.0, 0.0, 0
     for sched, p, st, pr, gst in step:
         if sched != "rs" or pr["sweep_launches"] == 0:
             continue
-        form = max(form, pr.get("sweep_form", 0))
         upd = st["committed_updates"]
         b += upd * (13 + 2 * s + 16 / dbar) + upd * (2 * s + 12 / dbar)
         ms += pr["sweep_ms"]
@@ -192,13 +188,9 @@ def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str)
     if ms <= 0:
         return None
     a = b / (ms / 1e3) / 1e9
-    name = {1: "k_splash_sweep_cluster ({dtype} messages; all Residual Splash sub-steps of a round in one "
-               "launch, one thread-block cluster per graph, cluster barriers between sub-steps)",
-            2: "k_splash_list_pair ({dtype} messages; Residual Splash sweep over level lists: commit of one "
-               "level fused with the evaluation of the next, a commit and an evaluation entry per thread)",
-            0: "k_splash_list_step ({dtype} messages; Residual Splash sweep over level lists: commit of one "
-               "level fused with the evaluation of the next)"}[form].format(dtype=dtype)
-    return {"bound": "hbm", "kernel": name, "sweep_form": ["per_sub_step", "cluster", "per_sub_step_pair"][form],
+    name = (f"k_splash_list_step ({dtype} messages; Residual Splash sweep over level lists: commit of one "
+            "level fused with the evaluation of the next)")
+    return {"bound": "hbm", "kernel": name, "sweep_form": "per_sub_step",
             "achieved": a,
             "peak": peak, "unit": "GB/s", "peak_source": peak_src, "frac": a / peak, "traffic": None,
             "launches": launches, "bytes_per_launch": b / launches, "avg_launch_us": 1e3 * ms / launches}
@@ -404,15 +396,13 @@ def main():
     ap.add_argument("--direct-launch", action="store_true",
                     help="timed steps launch kernels directly instead of replaying CUDA graphs "
                          "(profiler passes only)")
-    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
+    ap.add_argument("--kernel-variant", type=int, default=0, choices=[0, 1, 3, 4, 6],
                     help="binary update mapping (0 = library's choice)")
-    ap.add_argument("--potts-path", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--potts-path", type=int, default=0, choices=[0, 1],
                     help="shared-table update: 0 automatic, 1 CUDA cores, 2 tensor cores BF16, "
                          "3 tensor cores split")
-    ap.add_argument("--splash-sweep", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="Residual Splash sweeps: 0 library's choice, 1 one launch per sub-step, "
-                         "2 one cluster kernel per round, 3 one launch per sub-step with a commit "
-                         "and an evaluation entry per thread")
+    ap.add_argument("--splash-sweep", type=int, default=0, choices=[0, 1],
+                    help="Residual Splash sweeps: 0 library's choice, 1 one launch per sub-step")
     ap.add_argument("--overlap-launches", type=int, default=0, choices=[0, 1, 2],
                     help="programmatic dependent launches: 0 library's choice, 1 on, 2 off")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "q16", "f64"],

@@ -121,16 +121,16 @@ typedef struct {
                                  messages that are not FP64, 4 when no vertex has more
                                  than 4 edges and 6 when the streamed tiles apply; 1
                                  otherwise), 1 =
-                                 per-round kernels, one thread per vertex, 2 = per-round,
-                                 256-vertex tiles with 4-edge quads, 3 = persistent batch
-                                 kernel: one thread-block cluster per graph runs all of
-                                 its rounds in a single launch, 4 = one thread per vertex
-                                 with the graph arrays of 4 edges prefetched in parallel
-                                 with the graph's status, 5 = the same with 8 edges,
-                                 6 = streamed tiles: warp tiles of <= 128 edges staged in
+                                 per-round kernels, one thread per vertex, 3 = persistent
+                                 batch kernel: one thread-block cluster per graph runs all
+                                 of its rounds in a single launch, 4 = one thread per
+                                 vertex with the graph arrays of 4 edges prefetched in
+                                 parallel with the graph's status, 6 = streamed tiles: warp tiles of <= 128 edges staged in
                                  shared memory by bulk copies from a producer warp, one
                                  lane per edge (FP32 / BF16 / Q16 messages, vertices with
-                                 <= 128 out-edges; BP_ERR_UNSUPPORTED otherwise) */
+                                 <= 128 out-edges; BP_ERR_UNSUPPORTED otherwise); 2 and 5
+                                 (two mappings that never measured fastest) are retired
+                                 and rejected (BP_ERR_INVALID_ARG) */
     int32_t profile;          /* 1: time every round's phases with CUDA events (default 0) */
     int32_t potts_path;       /* shared-table (BP_PAIR_SHARED) update, FP32/BF16 storage,
                                  tiles of <= 128 edges: 0 = automatic (3 for k >= 16,
@@ -142,14 +142,11 @@ typedef struct {
                                  0 = automatic (by an occupancy-based time estimate), 1 =
                                  one thread-block cluster per graph, 2 = grid-wide
                                  kernels (for a few large graphs) */
-    int32_t splash_sweep;     /* RS sweeps (binary messages, splash_depth <= 3; the same
-                                 bits in every form): 0 = automatic (1), 1 = one
-                                 launch per sub-step, one list entry per thread, 2 =
-                                 all sub-steps of a round in one launch, one
-                                 thread-block cluster per graph (used only with the
-                                 cluster selection; with the grid-wide selection it
-                                 runs as 1), 3 = one launch per sub-step, a commit
-                                 entry and an evaluation entry per thread */
+    int32_t splash_sweep;     /* RS sweeps (binary messages, splash_depth <= 3): 0 =
+                                 automatic, 1 = one launch per sub-step over the
+                                 batch-wide level lists, one list entry per thread (the
+                                 only form; 0 selects it). Any other value is
+                                 BP_ERR_INVALID_ARG. */
     int32_t overlap_launches; /* programmatic dependent launches of the per-round update,
                                  decision and RnBP commit kernels (each grid may be
                                  scheduled while the previous kernel drains; it waits
@@ -190,10 +187,8 @@ typedef struct {
     int32_t select_ctas[2];    /* RBP, RS selection of the run: CTAs per graph of the cluster
                                   kernels (0 when the grid-wide kernels ran; always filled) */
     int32_t kernel_variant;    /* the binary update mapping the run used (always filled) */
-    int32_t sweep_ctas;        /* RS: CTAs per graph of the cluster sweep, 0 when the sweeps
-                                  ran one launch per sub-step (always filled) */
-    int32_t sweep_form;        /* RS sweep form of the run: 0 per-sub-step launches, 1 cluster
-                                  kernel, 2 per-sub-step launches with paired entries */
+    int32_t sweep_ctas;        /* always 0 (the RS sweeps run one launch per sub-step) */
+    int32_t sweep_form;        /* always 0: RS sweeps as per-sub-step launches */
     int32_t overlap_launches;  /* 1 when the run used programmatic dependent launches */
 } bp_profile;
 
@@ -202,12 +197,12 @@ void bp_default_options(bp_options *opt);
 
 /* Result of bp_autotune. */
 typedef struct {
-    int32_t kernel_variant;    /* the fastest mapping measured (1 to 6) */
+    int32_t kernel_variant;    /* the fastest mapping measured (1, 3, 4 or 6) */
     int32_t size_class;        /* the key it was recorded under: schedule (bits 0-1), msg_dtype
                                   (2-3), floor(log2(n_vars / n_graphs)) (4-8),
                                   floor(log2(n_graphs)) (9-13), largest vertex degree
                                   <= 4 / <= 8 / more (14-15) */
-    double ms_per_round[8];    /* measured device ms per round, index = mapping (1 to 6); 0 = not tried */
+    double ms_per_round[8];    /* measured device ms per round, index = mapping; 0 = not tried */
     int32_t select_path;       /* RBP / RS: the faster selection path measured (1 cluster, 2
                                   grid-wide; bp_options.select_path), 0 for other schedules */
     double ms_per_round_select[3]; /* device ms per round with the chosen mapping, index =
@@ -348,8 +343,8 @@ int bp_lbp_run_noalloc(int32_t n_vars, int64_t n_dir_edges, const int32_t *row_p
  * (it runs one kernel design); the batch configuration of arbitrary graph
  * sizes calls for a tuned choice per size class.
  *
- * For each mapping (1, 2, 4, 5, 6 where the streamed tiles apply, and 3 when
- * the handle holds more than one graph) it runs bp_run(schedule, parallelism, eps, trial_rounds, opt) twice
+ * For each mapping (1, 4, 6 where the streamed tiles apply, and 3 when the
+ * handle holds more than one graph) it runs bp_run(schedule, parallelism, eps, trial_rounds, opt) twice
  * (the first run captures the rounds; the second is timed by its device_ms)
  * and records the mapping with the least device time per round in a
  * process-wide table under the size class (see bp_tune_result); for RBP and

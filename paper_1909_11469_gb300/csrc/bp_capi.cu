@@ -117,7 +117,6 @@ struct bp_graph {
     int8_t *d_level = nullptr;
     int2 *d_lvl_list = nullptr;                 // Residual Splash level lists (lazy)
     int32_t *d_lvl_cnt = nullptr;
-    int32_t *d_lvl_gcnt = nullptr;              // per-graph level list lengths (cluster sweep)
     double *d_graph_p = nullptr;   // per-graph parallelism (bp_set_graph_parallelism)
     bool graph_p_set = false;
     int32_t max_deg = 0;           // largest vertex degree (size class, mapping heuristic)
@@ -130,8 +129,6 @@ struct bp_graph {
     int32_t max_graph_edges = 0;
     int32_t sel_plan[4][6];          // per message dtype: RBP CTAs, bytes, grid flag; RS the same
     bool sel_planned[4] = {false, false, false, false};
-    int32_t sweep_c[4];              // per message dtype: CTAs per graph of the cluster sweep
-    bool sweep_planned[4] = {false, false, false, false};
     // grid-wide selection buffers (allocated when a plan picks the grid kernels)
     GSelState *d_gsel = nullptr;
     unsigned int *d_gsel_hist = nullptr;
@@ -266,7 +263,6 @@ DevGraph dev_graph(const bp_graph *g, int dtype)
     d.sel_c[0] = d.sel_c[1] = 1;
     d.sel_dyn[0] = d.sel_dyn[1] = 0;
     d.sel_grid[0] = d.sel_grid[1] = 0;
-    d.sweep_c = 1;
     d.row_ptr = g->d_row_ptr;
     d.col = g->d_col;
     d.rev = g->d_rev;
@@ -304,7 +300,6 @@ DevRun dev_run(const bp_graph *g)
     r.queue = g->d_queue;
     r.lvl_list = g->d_lvl_list;
     r.lvl_cnt = g->d_lvl_cnt;
-    r.lvl_gcnt = g->d_lvl_gcnt;
     r.graph_p = g->graph_p_set ? g->d_graph_p : nullptr;
     r.err = g->d_err;
     r.gsel = g->d_gsel;
@@ -327,8 +322,6 @@ void apply_select_plan(const bp_graph *g, int dtype, int sel_grid_bits, DevGraph
         dg.sel_c[1] = g->sel_plan[dtype][3];
         dg.sel_dyn[1] = g->sel_plan[dtype][4];
     }
-    if (g->sweep_planned[dtype])
-        dg.sweep_c = g->sweep_c[dtype];
     dg.sel_grid[0] = sel_grid_bits & 1;
     dg.sel_grid[1] = (sel_grid_bits >> 1) & 1;
 }
@@ -610,13 +603,7 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
             }
             if (ev)
                 cudaEventRecord(ev[3], s);
-            if (rp.sweep_form == SWEEP_CLUSTER) {
-                // every sub-step of the round in one launch, a cluster per graph
-                launch_splash_sweep_cluster(dtype, dg, dr, rp, s);
-                kernels += any;
-                break;
-            }
-            auto step_launch = rp.sweep_form == SWEEP_PAIR ? launch_splash_list_pair : launch_splash_list_step;
+            auto step_launch = launch_splash_list_step;
             // sweep steps launch without programmatic serialization (measured
             // slower between sweep steps); the next round's update still
             // overlaps the last one, which lets its dependents launch early
@@ -992,16 +979,16 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         return fail(BP_ERR_INVALID_ARG, "potts_path must be 0..3");
     if (opt.select_path < 0 || opt.select_path > 2)
         return fail(BP_ERR_INVALID_ARG, "select_path must be 0..2");
-    if (opt.splash_sweep < 0 || opt.splash_sweep > 3)
-        return fail(BP_ERR_INVALID_ARG, "splash_sweep must be 0..3");
+    if (opt.splash_sweep < 0 || opt.splash_sweep > 1)
+        return fail(BP_ERR_INVALID_ARG, "splash_sweep must be 0 or 1");
     if (opt.overlap_launches < 0 || opt.overlap_launches > 2)
         return fail(BP_ERR_INVALID_ARG, "overlap_launches must be 0..2");
     if (opt.dynamic_p < 0 || opt.dynamic_p > 1)
         return fail(BP_ERR_INVALID_ARG, "dynamic_p must be 0 or 1");
     if (opt.dynamic_p && (schedule == BP_RBP || schedule == BP_RS) && !(opt.high_p > 0.0))
         return fail(BP_ERR_INVALID_ARG, "dynamic_p needs high_p > 0 (the RBP / RS HighP fraction)");
-    if (opt.kernel_variant < 0 || opt.kernel_variant > 6)
-        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be in [0, 6]");
+    if (opt.kernel_variant < 0 || opt.kernel_variant > 6 || opt.kernel_variant == 2 || opt.kernel_variant == 5)
+        return fail(BP_ERR_INVALID_ARG, "kernel_variant must be 0, 1, 3, 4 or 6");
     if (opt.splash_depth < 0 || opt.splash_depth > 16)
         return fail(BP_ERR_INVALID_ARG, "splash_depth must be in [0, 16]");
     if (opt.record_trace && opt.trace_capacity < 0)
@@ -1014,8 +1001,7 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     if (schedule == BP_RS && epm_of(g) == 1 && opt.splash_depth <= LVL_MAX && !g->d_lvl_list) {
         // level lists of the Residual Splash sweeps, kept until the handle is destroyed
         if ((rc = dalloc(&g->d_lvl_list, (size_t)(LVL_MAX + 1) * (size_t)std::max(g->n, 1))) != BP_OK ||
-            (rc = dalloc(&g->d_lvl_cnt, (size_t)(LVL_MAX + 1))) != BP_OK ||
-            (rc = dalloc(&g->d_lvl_gcnt, (size_t)(LVL_MAX + 1) * (size_t)std::max(g->G, 1))) != BP_OK)
+            (rc = dalloc(&g->d_lvl_cnt, (size_t)(LVL_MAX + 1))) != BP_OK)
             return rc;
         BP_CK(cudaMemset(g->d_lvl_cnt, 0, sizeof(int32_t) * (LVL_MAX + 1)));
     }
@@ -1074,24 +1060,6 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
             bits = 0;
         apply_select_plan(g, dtype, bits, dg);
         rp.sel_grid = bits;
-    }
-    if (schedule == BP_RS && epm_of(g) == 1 && opt.splash_depth <= LVL_MAX && g->d_lvl_list && variant != 3) {
-        // sweeps over level lists: the per-sub-step forms over the batch-wide
-        // lists, or the cluster sweep over the per-graph lists that only the
-        // cluster selection writes
-        const bool cluster_ok = !(rp.sel_grid & 2);
-        static const int32_t form_of[4] = {SWEEP_LIST, SWEEP_LIST, SWEEP_CLUSTER, SWEEP_PAIR};
-        int32_t form = form_of[opt.splash_sweep];
-        if (form == SWEEP_CLUSTER && !cluster_ok)
-            form = SWEEP_LIST;
-        if (form == SWEEP_CLUSTER) {
-            if (!g->sweep_planned[dtype]) {
-                g->sweep_c[dtype] = plan_sweep(dtype, g->G, g->n, g->max_graph_vertices);
-                g->sweep_planned[dtype] = true;
-            }
-            dg.sweep_c = g->sweep_c[dtype];
-        }
-        rp.sweep_form = form;
     }
     DevRun dr = dev_run(g);
     g->has_result = false;
@@ -1255,13 +1223,13 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
         prof.eval_launches = (int64_t)live;
         // every committing round of an RS run sweeps 2h + 2 fused steps (binary)
         if (schedule == BP_RS && epm_of(g) == 1)
-            prof.sweep_launches = (int64_t)(live > 0 ? live - 1 : 0) * (rp.sweep_form == SWEEP_CLUSTER ? 1 : 2 * opt.splash_depth + 2);
+            prof.sweep_launches = (int64_t)(live > 0 ? live - 1 : 0) * (2 * opt.splash_depth + 2);
     }
     for (int w = 0; w < 2; ++w)
         prof.select_ctas[w] = (dg.sel_grid[w] && dr.gsel) ? 0 : dg.sel_c[w];
     prof.kernel_variant = variant;
-    prof.sweep_ctas = rp.sweep_form == SWEEP_CLUSTER ? dg.sweep_c : 0;
-    prof.sweep_form = rp.sweep_form;
+    prof.sweep_ctas = 0;
+    prof.sweep_form = 0;
     prof.overlap_launches = rp.pdl;
     g->last_profile = prof;
     g->has_result = true;
@@ -1404,10 +1372,10 @@ int bp_autotune(bp_graph *g, int32_t schedule, double parallelism, double eps, c
     o.time_budget_ms = 0.0;
     o.record_trace = 0;
     memset(out, 0, sizeof(*out));
-    static const int32_t cand[] = {1, 2, 4, 5, 6, 3};
+    static const int32_t cand[] = {1, 4, 6, 3};
     double best = std::numeric_limits<double>::infinity();
     int32_t best_v = 1;
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < 4; ++c) {
         if (cand[c] == 3 && g->G == 1)
             continue;   // the persistent kernel runs one cluster per graph
         if (cand[c] == 6 && (o.msg_dtype == BP_F64 || !g->wtiles_ok))
@@ -1627,7 +1595,6 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_level);
     dfree(g->d_lvl_list);
     dfree(g->d_lvl_cnt);
-    dfree(g->d_lvl_gcnt);
     dfree(g->d_graph_p);
     dfree(g->d_gsel);
     dfree(g->d_gsel_hist);

@@ -50,7 +50,6 @@ struct DevGraph {
     int32_t sel_c[2];         // selection clusters: CTAs per graph (RBP, RS), planned per run
     int32_t sel_dyn[2];       // selection clusters: staged-key bytes per CTA (RBP, RS)
     int32_t sel_grid[2];      // 1: select with the grid-wide kernels instead (RBP, RS)
-    int32_t sweep_c;          // CTAs per graph of the cluster splash sweep, planned per run
     const int32_t *row_ptr;   // [n+1]
     const int32_t *col;       // [M]
     const int32_t *rev;       // [M]
@@ -97,13 +96,7 @@ struct RunParams {
     int32_t pdl;              // 1: the update, decision and RnBP commit kernels are launched
                               // with programmatic stream serialization
     int32_t dynamic_p;        // 1: RBP / RS frontier fraction switched per round by EdgeRatio
-    int32_t sweep_form;       // RS sweeps (binary, level lists): SWEEP_LIST one launch per
-                              // sub-step, SWEEP_CLUSTER one cluster kernel per round over
-                              // per-graph level lists, SWEEP_PAIR one launch per sub-step
-                              // with a commit and an evaluation per thread
 };
-
-enum { SWEEP_LIST = 0, SWEEP_CLUSTER = 1, SWEEP_PAIR = 2 };
 
 // eps in the residual type, chosen so that the comparison equals the FP64 test.
 __device__ __forceinline__ float eps_in(const RunParams &rp, float) { return rp.eps_f; }
@@ -135,9 +128,6 @@ struct DevRun {
     int2 *lvl_list;               // [(LVL_MAX+1) * n] Residual Splash vertices of each level:
                                   // (vertex, its first out-edge)
     int32_t *lvl_cnt;             // [LVL_MAX+1] entries of each level list
-    int32_t *lvl_gcnt;            // [G * (LVL_MAX+1)] entries of each graph's level lists, when
-                                  // the lists are per graph: graph gg's level L at
-                                  // lvl_list[L * n + gv_off[gg] + j], j < lvl_gcnt[gg * (LVL_MAX+1) + L]
     const double *graph_p;        // [G] per-graph parallelism, or null: every graph uses rp.low_p
     int32_t *err;                 // [1] set when a bounded device wait runs out
     // grid-wide selection (large graphs; null when unused)

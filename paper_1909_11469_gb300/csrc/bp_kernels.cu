@@ -302,347 +302,106 @@ __device__ __forceinline__ void add_commit_counts(const DevRun &dr, bool uniform
 }
 
 // --------------------------------------------------------------------------
-// Tiled form of the binary update for full evaluations (LBP and frontier
-// modes). A block owns 256 consecutive vertices and their contiguous edge
-// range [e0, e1) (CSR rows are adjacent). Every thread owns up to two quads of
-// 4 consecutive edges of that range, aligned to 4 elements, and issues their
-// 16-byte loads of rev, exp(-2 beta) and the old message at entry, in parallel
-// with the vertex pass; then
-//   0. vertex pass: graph state, local source vertex of every edge (shared)
-//   1. quad pass:   incoming log-odds cur[rev[e]] (the only scattered loads)
-//   2. vertex pass: field h_i = unary log-odds + sum of incoming
-//   3. quad pass:   cavity h_i - u_{j->i}, new message, residual, quad stores
-// Tiles whose edge range exceeds the two quads per thread use a per-vertex
-// loop instead.
+// Vertex tiles of the fallback RnBP commit (k_commit_rnbp_tiled): 256
+// consecutive vertices and their contiguous edge range, up to TILE_E edges
+// staged per tile.
 constexpr int TILE_V = 256;
-constexpr int QUADS = 2;
-constexpr int TILE_E = 4 * TILE_V * QUADS - 8;   // staged edges per tile (alignment slack)
+constexpr int TILE_E = 8 * TILE_V - 8;
 
-template <typename T> struct Vec4;
-template <> struct Vec4<float> { using V = float4; };
-template <> struct Vec4<int32_t> { using V = int4; };
-
-// Loads elements [base, base + 4) of p (base a multiple of 4) into out[],
-// vectorised when p is 16-byte aligned and the quad lies inside [0, count).
-template <typename T> __device__ __forceinline__ void load_quad(const T *p, int base, int count, bool vec, T out[4])
-{
-    if constexpr (sizeof(T) == 4) {
-        if (vec && base >= 0 && base + 3 < count) {
-            typename Vec4<T>::V v = *reinterpret_cast<const typename Vec4<T>::V *>(p + base);
-            out[0] = v.x;
-            out[1] = v.y;
-            out[2] = v.z;
-            out[3] = v.w;
-            return;
-        }
-    } else if constexpr (sizeof(T) == 8) {
-        if (vec && base >= 0 && base + 3 < count) {
-            double2 a = *reinterpret_cast<const double2 *>(p + base);
-            double2 b = *reinterpret_cast<const double2 *>(p + base + 2);
-            out[0] = a.x;
-            out[1] = a.y;
-            out[2] = b.x;
-            out[3] = b.y;
-            return;
-        }
-    } else {   // 2-byte storage
-        if (vec && base >= 0 && base + 3 < count) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(p + base);
-            const unsigned short w[4] = {(unsigned short)(v.x & 0xffffu), (unsigned short)(v.x >> 16),
-                                         (unsigned short)(v.y & 0xffffu), (unsigned short)(v.y >> 16)};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                T t;
-                memcpy(&t, &w[k], sizeof(T));
-                out[k] = t;
-            }
-            return;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (base + k >= 0 && base + k < count)
-            out[k] = p[base + k];
-}
-
-// One thread's (max residual, count) of graph gg into a reduction sub-slot.
-__device__ __forceinline__ void flush_to_graph(const DevRun &dr, int gg, double maxr, unsigned int cnt)
-{
-    if (gg < 0)
-        return;
-    const int slot = blockIdx.x & (NSUB - 1);
-    if (maxr > 0.0)
-        atomicMax(&dr.red_max[(size_t)gg * NSUB + slot], (unsigned long long)__double_as_longlong(maxr));
-    if (cnt)
-        atomicAdd(&dr.red_cnt[(size_t)gg * NSUB + slot], cnt);
-}
-
-template <typename S, int MODE>
-__global__ void __launch_bounds__(TILE_V) k_eval_bin_tiled(DevGraph g, DevRun dr, RunParams rp)
-{
-    using A = typename Store<S>::A;
-    using RT = typename ResidT<S>::T;
-    __shared__ A s_uin[TILE_E];
-    __shared__ A s_h[TILE_V];
-    __shared__ uint8_t s_src[TILE_E];
-    __shared__ int8_t s_cur[TILE_V];
-    const int v0 = blockIdx.x * TILE_V;
-    const int nv = min(TILE_V, g.n - v0);
-    const int e0 = g.row_ptr[v0];
-    const int e1 = g.row_ptr[v0 + nv];
-    const int ne = e1 - e0;
-    const int g0 = g.gid[v0];
-    const bool uniform = (g0 == g.gid[v0 + nv - 1]);
-    const int vl = threadIdx.x;
-    const int v = v0 + vl;
-    const A *q;
-    const A *udiff;
-    if constexpr (sizeof(A) == 8) {
-        q = (const A *)g.q64;
-        udiff = (const A *)g.udiff64;
-    } else {
-        q = (const A *)g.q32;
-        udiff = (const A *)g.udiff32;
-    }
-    RT *R = (RT *)dr.resid;
-    A maxa = 0;
-    const A eps_a = eps_in(rp, (A)0);
-    unsigned int cnt = 0;
-
-    if (ne > TILE_E) {
-        // rare dense tile: per-vertex loop
-        bool valid = false;
-        int gg = g0;
-        if (vl < nv) {
-            gg = g.gid[v];
-            if (dr.gs[gg].status == ST_RUNNING) {
-                valid = true;
-                const int c = dr.gs[gg].cur;
-                const S *cur = (const S *)msg_buf(dr, c);
-                S *out = (S *)msg_buf(dr, c ^ 1);
-                A h = udiff[v];
-                for (int e = g.row_ptr[v]; e < g.row_ptr[v + 1]; ++e)
-                    h += Store<S>::ld(cur + g.rev[e], g.qscale);
-                for (int e = g.row_ptr[v]; e < g.row_ptr[v + 1]; ++e) {
-                    A unew = ising_logodds(q[e], h - Store<S>::ld(cur + g.rev[e], g.qscale));
-                    A r = fabs(m_sigmoid(Store<S>::quant(unew, g.qscale)) -
-                               m_sigmoid(Store<S>::ld(cur + e, g.qscale)));
-                    Store<S>::st(out + e, unew, g.qscale);
-                    if (MODE == MODE_CAND)
-                        R[e] = (RT)r;
-                    maxa = r > maxa ? r : maxa;
-                    cnt += (r >= eps_a) ? 1u : 0u;
-                }
-            }
-        }
-        reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
-        return;
-    }
-
-    // Edge quads of this thread: elements [qb, qb + 4) with qb = e0a + 4 (vl + 256 j).
-    const int e0a = e0 & ~3;
-    const bool vec = g.vec_ok != 0;
-    // buffer of the tile's first graph; edges of a graph in the other buffer
-    // (possible only in LBP tiles that straddle graphs) reload their old value
-    const int c_tile = (MODE == MODE_LBP) ? dr.gs[g0].cur : 0;
-    int rv[QUADS][4];
-    A qv[QUADS][4];
-    S ov[QUADS][4];
-#pragma unroll
-    for (int j = 0; j < QUADS; ++j) {
-        const int qb = e0a + 4 * (vl + TILE_V * j);
-        if (qb < e1) {
-            load_quad(g.rev, qb, g.M, vec, rv[j]);
-            load_quad(q, qb, g.M, vec, qv[j]);
-            load_quad((const S *)msg_buf(dr, c_tile), qb, g.M, vec, ov[j]);
-        }
-    }
-
-    // 0. vertex pass
-    int beg = 0, end = 0;
-    bool act = false;
-    if (vl < nv) {
-        const int gg = g.gid[v];
-        act = dr.gs[gg].status == ST_RUNNING;
-        s_cur[vl] = act ? (int8_t)dr.gs[gg].cur : (int8_t)-1;
-        beg = g.row_ptr[v] - e0;
-        end = g.row_ptr[v + 1] - e0;
-        for (int t = beg; t < end; ++t)
-            s_src[t] = (uint8_t)vl;
-    }
-    __syncthreads();
-    // 1. gather the incoming messages
-    A uin[QUADS][4];
-#pragma unroll
-    for (int j = 0; j < QUADS; ++j) {
-        const int qb = e0a + 4 * (vl + TILE_V * j);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int e = qb + k;
-            if (e >= e0 && e < e1) {
-                const int c = s_cur[s_src[e - e0]];
-                if (c >= 0) {
-                    uin[j][k] = Store<S>::ld((const S *)msg_buf(dr, c) + rv[j][k], g.qscale);
-                    s_uin[e - e0] = uin[j][k];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    // 2. vertex fields
-    if (act) {
-        A h = udiff[v];
-        for (int t = beg; t < end; ++t)
-            h += s_uin[t];
-        s_h[vl] = h;
-    }
-    __syncthreads();
-    // 3. new messages, residuals, reductions. In a tile that spans graphs each
-    // thread accumulates per graph and flushes when its graph changes.
-    int acc_g = -1;
-#pragma unroll
-    for (int j = 0; j < QUADS; ++j) {
-        const int qb = e0a + 4 * (vl + TILE_V * j);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int e = qb + k;
-            if (e < e0 || e >= e1)
-                continue;
-            const int src = s_src[e - e0];
-            const int c = s_cur[src];
-            if (c < 0)
-                continue;
-            const A unew = ising_logodds(qv[j][k], s_h[src] - uin[j][k]);
-            const A old = (c == c_tile) ? Store<S>::val(ov[j][k], g.qscale)
-                                        : Store<S>::ld((const S *)msg_buf(dr, c) + e, g.qscale);
-            const A r = fabs(m_sigmoid(Store<S>::quant(unew, g.qscale)) - m_sigmoid(old));
-            Store<S>::st((S *)msg_buf(dr, c ^ 1) + e, unew, g.qscale);
-            if (MODE == MODE_CAND)
-                R[e] = (RT)r;
-            if (!uniform) {
-                const int gg = g.gid[v0 + src];
-                if (gg != acc_g) {
-                    flush_to_graph(dr, acc_g, (double)maxa, cnt);
-                    acc_g = gg;
-                    maxa = 0;
-                    cnt = 0;
-                }
-            }
-            maxa = r > maxa ? r : maxa;
-            cnt += (r >= eps_a) ? 1u : 0u;
-        }
-    }
-    if (!uniform)
-        flush_to_graph(dr, acc_g, (double)maxa, cnt);
-    reduce_to_graph(dr, uniform, g0, uniform, g0, (double)maxa, cnt);
-}
-
-// RnBP commit, tiled like the update: a vertex pass stages the source of each
-// edge and its graph's round state; an edge pass reads the residuals
-// contiguously, draws Philox for the messages with residual >= eps and copies
-// the selected candidates.
 // RnBP commit over the warp tiles of the streamed update (single-graph runs
-// of consecutive vertices, <= 128 out-edges). A warp takes TPW consecutive
-// tiles and issues the loads of all of them before it uses any: the tile
-// records, then the graphs' round states and the residuals of the tiles'
-// messages. Each lane takes aligned quads of four consecutive messages of a
-// graph, which share one Philox block (one block per quad instead of one
-// per message), applies the eps filter and copies the selected candidates.
-// The kernel is bound by the latency of that short dependent chain (record
-// -> residual and state -> candidate -> store), so it keeps TPW chains in
-// flight per warp and many warps per SM; the commits of a tile are added
-// with one atomic.
-constexpr int COMMIT_TPW = 2;
-
+// of consecutive vertices, <= 128 out-edges): one warp per tile reads the
+// tile record, then together the graph's round state and the residuals of
+// the tile's messages. Each lane takes aligned quads of four consecutive
+// messages of the graph, which share one Philox block (one block per quad
+// instead of one per message), and applies the eps filter; then it issues
+// the loads of all its selected candidates before any store, so a lane keeps
+// up to eight copies in flight. Every warp is independent, so the short
+// dependent chain of one tile (record -> residual and state -> candidate ->
+// store) overlaps with the other resident warps'; the commits of a tile are
+// added with one atomic.
 template <typename S>
-__global__ void __launch_bounds__(BLOCK, 3) k_commit_rnbp_wt(DevGraph g, DevRun dr, RunParams rp)
+__global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun dr, RunParams rp)
 {
     griddep_launch_dependents();
     using RT = typename ResidT<S>::T;
     constexpr int QPL = 2;   // quads per lane: a tile of <= 128 edges meets <= 34 quads
     const int lane = threadIdx.x & 31;
-    const int w = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    int e0[COMMIT_TPW], e1[COMMIT_TPW], gg[COMMIT_TPW], ge0[COMMIT_TPW];
-#pragma unroll
-    for (int i = 0; i < COMMIT_TPW; ++i) {
-        const int t = w * COMMIT_TPW + i;
-        e0[i] = e1[i] = 0;
-        gg[i] = 0;
-        ge0[i] = 0;
-        if (t < g.n_wtiles) {
-            const int4 rec = g.wtiles[t];
-            e0[i] = rec.y;
-            e1[i] = g.wtiles[t + 1].y;
-            gg[i] = rec.z;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < COMMIT_TPW; ++i)
-        if (e1[i] > e0[i])
-            ge0[i] = g.ge_off[gg[i]];
+    const int t = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (t >= g.n_wtiles)
+        return;
+    const int4 rec = g.wtiles[t];
+    const int e0 = rec.y, e1 = g.wtiles[t + 1].y, gg = rec.z;
+    if (e1 == e0)
+        return;
+    const int ge0 = g.ge_off[gg];
+    const int q0 = (e0 - ge0) >> 2, q1 = (e1 - 1 - ge0) >> 2;
     griddep_wait();   // residuals, candidates and round state come from the previous kernels
     const RT *R = (const RT *)dr.resid;
-    RT r[COMMIT_TPW][QPL][4];
-    // the graph's round state: status, rounds, RnBP threshold / always-flag
-    int st_status[COMMIT_TPW], st_rounds[COMMIT_TPW], st_always[COMMIT_TPW];
-    uint32_t st_thr[COMMIT_TPW];
+    RT r[QPL][4];
 #pragma unroll
-    for (int i = 0; i < COMMIT_TPW; ++i) {
-        const int q0 = (e0[i] - ge0[i]) >> 2, q1 = (e1[i] - 1 - ge0[i]) >> 2;
+    for (int k = 0; k < QPL; ++k) {
+        const int q = q0 + lane + 32 * k;
 #pragma unroll
-        for (int k = 0; k < QPL; ++k) {
-            const int q = q0 + lane + 32 * k;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int e = ge0[i] + 4 * q + j;
-                r[i][k][j] = (q <= q1 && e >= e0[i] && e < e1[i]) ? R[e] : (RT)0;
-            }
+        for (int j = 0; j < 4; ++j) {
+            const int e = ge0 + 4 * q + j;
+            r[k][j] = (q <= q1 && e >= e0 && e < e1) ? R[e] : (RT)0;
         }
-        const GState *sp = dr.gs + gg[i];
-        st_status[i] = sp->status;
-        st_rounds[i] = sp->rounds;
-        st_always[i] = sp->always;
-        st_thr[i] = sp->thr;
+    }
+    const GState *sp = dr.gs + gg;
+    const int status = sp->status, rounds = sp->rounds, always = sp->always;
+    const uint32_t thr = sp->thr;
+    if (status != ST_RUNNING)
+        return;
+    const RT eps = eps_in(rp, (RT)0);
+    // selection bit (k, j) of this lane
+    unsigned pick = 0;
+#pragma unroll
+    for (int k = 0; k < QPL; ++k) {
+        const int q = q0 + lane + 32 * k;
+        const bool any = r[k][0] >= eps || r[k][1] >= eps || r[k][2] >= eps || r[k][3] >= eps;
+        if (q > q1 || !any)
+            continue;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (!always)
+            w = rnbp_block(rp, (uint32_t)q, (uint32_t)rounds, (uint32_t)gg);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = ge0 + 4 * q + j;
+            if (e >= e0 && e < e1 && r[k][j] >= eps && (always || rnbp_word(w, (uint32_t)j) < thr))
+                pick |= 1u << (4 * k + j);
+        }
     }
     S *dst = (S *)dr.msg[0];
     const S *src = (const S *)dr.msg[1];
     const int epm = g.epm;
-    const RT eps = eps_in(rp, (RT)0);
+    if (epm == 1) {
+        S v[QPL * 4];
 #pragma unroll
-    for (int i = 0; i < COMMIT_TPW; ++i) {
-        if (e1[i] == e0[i] || st_status[i] != ST_RUNNING)
-            continue;
-        const bool tr = rp.record_trace && st_rounds[i] <= rp.trace_capacity;
-        const int q0 = (e0[i] - ge0[i]) >> 2, q1 = (e1[i] - 1 - ge0[i]) >> 2;
-        unsigned int c = 0;
+        for (int b = 0; b < QPL * 4; ++b)
+            if (pick >> b & 1u)
+                v[b] = src[ge0 + 4 * (q0 + lane + 32 * (b >> 2)) + (b & 3)];
 #pragma unroll
-        for (int k = 0; k < QPL; ++k) {
-            const int q = q0 + lane + 32 * k;
-            if (q > q1)
-                continue;
-            const bool any = r[i][k][0] >= eps || r[i][k][1] >= eps || r[i][k][2] >= eps || r[i][k][3] >= eps;
-            if (!any)
-                continue;
-            uint4 wd = make_uint4(0u, 0u, 0u, 0u);
-            if (!st_always[i])
-                wd = rnbp_block(rp, (uint32_t)q, (uint32_t)st_rounds[i], (uint32_t)gg[i]);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int e = ge0[i] + 4 * q + j;
-                if (e < e0[i] || e >= e1[i] || r[i][k][j] < eps ||
-                    !(st_always[i] || rnbp_word(wd, (uint32_t)j) < st_thr[i]))
-                    continue;
+        for (int b = 0; b < QPL * 4; ++b)
+            if (pick >> b & 1u)
+                dst[ge0 + 4 * (q0 + lane + 32 * (b >> 2)) + (b & 3)] = v[b];
+    } else {
+        for (int b = 0; b < QPL * 4; ++b)
+            if (pick >> b & 1u) {
+                const size_t e = (size_t)(ge0 + 4 * (q0 + lane + 32 * (b >> 2)) + (b & 3));
                 for (int x = 0; x < epm; ++x)
-                    dst[(size_t)e * epm + x] = src[(size_t)e * epm + x];
-                ++c;
-                if (tr)
-                    atomicOr(&dr.trace[(size_t)(st_rounds[i] - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
+                    dst[e * epm + x] = src[e * epm + x];
             }
-        }
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0 && c)
-            atomicAdd(&dr.gs[gg[i]].committed, (unsigned long long)c);
     }
+    if (rp.record_trace && rounds <= rp.trace_capacity) {
+        for (int b = 0; b < QPL * 4; ++b)
+            if (pick >> b & 1u) {
+                const int e = ge0 + 4 * (q0 + lane + 32 * (b >> 2)) + (b & 3);
+                atomicOr(&dr.trace[(size_t)(rounds - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
+            }
+    }
+    const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)__popc(pick));
+    if (lane == 0 && c)
+        atomicAdd(&dr.gs[gg].committed, (unsigned long long)c);
 }
 
 template <typename S>
@@ -904,24 +663,6 @@ __global__ void __launch_bounds__(BLOCK, 6) k_splash_list_step(DevGraph g, DevRu
     }
 }
 
-// The same sub-step with thread t taking commit entry t and evaluation entry
-// t together (max(nc, ne) threads instead of nc + ne). Entries at t >= the
-// count are not used; every index t < max(nc, ne) <= n stays inside a list.
-template <typename S>
-__global__ void __launch_bounds__(BLOCK, 6) k_splash_list_pair(DevGraph g, DevRun dr, int Lc, int Le)
-{
-    const int nc = Lc >= 0 ? dr.lvl_cnt[Lc] : 0;
-    const int ne = Le >= 0 ? dr.lvl_cnt[Le] : 0;
-    const int2 *lc = dr.lvl_list + (size_t)(Lc >= 0 ? Lc : 0) * g.n;
-    const int2 *le = dr.lvl_list + (size_t)(Le >= 0 ? Le : 0) * g.n;
-    const int total = nc > ne ? nc : ne;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int2 vc = lc[t];
-        const int2 ve = le[t];
-        splash_pair_vertex_b<S>(g, dr, t < nc, vc.x, vc.y, t < ne, ve.x, ve.y, Lc);
-    }
-}
-
 // --------------------------------------------------------------------------
 // Set-up of a run.
 template <typename S>
@@ -1125,35 +866,24 @@ static void launch_eval_bin(const DevGraph &g, const DevRun &dr, const RunParams
 {
     int nb = blocks_for(g.n, BLOCK);
     (void)level_L;   // binary splash sweeps use k_splash_step / k_splash_list_step
-    // mapping: thread per vertex (variant 1), 256-vertex tiles with edge quads
-    // (variant 2), thread per vertex with prefetched graph arrays of 4 (variant
-    // 4, 40 registers: 6 blocks per SM) or 8 edges (variant 5, 4 blocks per SM)
-    const bool tiled = rp.variant == 2;
+    // mapping: thread per vertex (1), thread per vertex with the graph arrays
+    // of 4 edges prefetched (4; 40 registers: 6 blocks per SM), streamed warp
+    // tiles (6)
     if (rp.variant == 6) {
         launch_eval_stream(dtype_of<S>(), g, dr, rp, mode, s);
         return;
     }
-    if (rp.variant >= 4) {
-        if (mode == MODE_LBP) {
-            if (rp.variant == 4) launch_k(rp.pdl, k_eval_bin_pf<S, MODE_LBP, 4, 6>, nb, BLOCK, s, g, dr, rp);
-            else launch_k(rp.pdl, k_eval_bin_pf<S, MODE_LBP, 8, 4>, nb, BLOCK, s, g, dr, rp);
-        } else {
-            if (rp.variant == 4) launch_k(rp.pdl, k_eval_bin_pf<S, MODE_CAND, 4, 6>, nb, BLOCK, s, g, dr, rp);
-            else launch_k(rp.pdl, k_eval_bin_pf<S, MODE_CAND, 8, 4>, nb, BLOCK, s, g, dr, rp);
-        }
+    if (rp.variant == 4) {
+        if (mode == MODE_LBP)
+            launch_k(rp.pdl, k_eval_bin_pf<S, MODE_LBP, 4, 6>, nb, BLOCK, s, g, dr, rp);
+        else
+            launch_k(rp.pdl, k_eval_bin_pf<S, MODE_CAND, 4, 6>, nb, BLOCK, s, g, dr, rp);
         return;
     }
-    if (mode == MODE_LBP) {
-        if (tiled)
-            k_eval_bin_tiled<S, MODE_LBP><<<blocks_for(g.n, TILE_V), TILE_V, 0, s>>>(g, dr, rp);
-        else
-            k_eval_bin<S, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp);
-    } else {
-        if (tiled)
-            k_eval_bin_tiled<S, MODE_CAND><<<blocks_for(g.n, TILE_V), TILE_V, 0, s>>>(g, dr, rp);
-        else
-            k_eval_bin<S, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp);
-    }
+    if (mode == MODE_LBP)
+        k_eval_bin<S, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp);
+    else
+        k_eval_bin<S, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp);
 }
 
 template <typename S, int KP>
@@ -1210,9 +940,9 @@ void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const Ru
     if (g.n == 0)
         return;
     if (g.n_wtiles > 0) {
-        // COMMIT_TPW warp tiles per warp
-        BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_wt<S>,
-                                       blocks_for(g.n_wtiles, COMMIT_TPW * (BLOCK / 32)), BLOCK, s, g, dr, rp)));
+        // one warp per warp tile
+        BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_wt<S>, blocks_for(g.n_wtiles, BLOCK / 32), BLOCK, s,
+                                       g, dr, rp)));
         return;
     }
     BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_tiled<S>, blocks_for(g.n, TILE_V), TILE_V, s, g, dr, rp)));
@@ -1239,15 +969,6 @@ void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int
         return;
     const int nb = std::min(blocks_for(g.n, BLOCK), 152 * 6);   // one wave at 6 blocks per SM
     BPG_DISPATCH4(dtype, (launch_k(pdl, k_splash_list_step<S>, nb, BLOCK, s, g, dr, Lc, Le)));
-}
-
-void launch_splash_list_pair(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s,
-                             bool)
-{
-    if (g.n == 0)
-        return;
-    const int nb = std::min(blocks_for(g.n, BLOCK), 152 * 6);   // one wave at 6 blocks per SM
-    BPG_DISPATCH4(dtype, (k_splash_list_pair<S><<<nb, BLOCK, 0, s>>>(g, dr, Lc, Le)));
 }
 
 void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int level_L, cudaStream_t s)

@@ -53,17 +53,6 @@ void launch_bfs_level_lists(const DevGraph &g, const DevRun &dr, int d, int h, c
 // pdl: launch with programmatic stream serialization.
 void launch_splash_list_step(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s,
                              bool pdl = false);
-// The same sub-step with a commit entry and an evaluation entry per thread
-// (always launched without programmatic serialization).
-void launch_splash_list_pair(int dtype, const DevGraph &g, const DevRun &dr, int Lc, int Le, cudaStream_t s,
-                             bool pdl = false);
-// Residual Splash with one thread-block cluster per graph (binary messages,
-// depth <= LVL_MAX, cluster selection): every sub-step of a round's sweeps in
-// one launch over the per-graph level lists of k_select_rs. plan_sweep
-// returns its CTAs per graph (host occupancy queries; outside stream capture).
-int plan_sweep(int dtype, int G, int n, int max_gv);
-void launch_splash_sweep_cluster(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp,
-                                 cudaStream_t s);
 void launch_splash_commit(int dtype, const DevGraph &g, const DevRun &dr, int level_L, cudaStream_t s);
 void launch_stop_running(const DevGraph &g, const DevRun &dr, cudaStream_t s);
 void launch_beliefs(int dtype, const DevGraph &g, const DevRun &dr, int kp, cudaStream_t s);

@@ -80,16 +80,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_rbp(DevGraph g, DevRun d
 // RS: vertex residual = max residual of the messages into the vertex; select
 // the top k_sel vertices as splash roots (level 0), every other vertex gets
 // level -1, then the BFS levels 1..h and (binary messages) the per-level
-// vertex lists of the sweeps: one list per level for the whole batch, or,
-// for the cluster sweep (rp.sweep_form == SWEEP_CLUSTER), one per graph and level inside
-// the graph's vertex range. Each CTA owns a slice of the graph's vertices.
+// vertex lists of the sweeps, one list per level for the whole batch. Each
+// CTA owns a slice of the graph's vertices.
 template <typename S>
 __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun dr, RunParams rp)
 {
     using RT = typename ResidT<S>::T;
     using KeyT = decltype(key_bits((RT)0));
     __shared__ SelShared<KeyT> sh;
-    __shared__ int s_gcnt[LVL_MAX + 1];   // CTA rank 0: the graph's level list lengths
     extern __shared__ __align__(16) unsigned char sel_smem[];
     cg::cluster_group cl = cg::this_cluster();
     const unsigned C = cl.num_blocks(), rank = cl.block_rank();
@@ -101,10 +99,6 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun
     const int nv = g.gv_off[gg + 1] - v0;
     if (nv == 0)
         return;
-    const bool per_graph = rp.sweep_form == SWEEP_CLUSTER;
-    // (the selection's cluster barriers order this before the peers' additions)
-    if (per_graph && rank == 0 && threadIdx.x <= (unsigned)LVL_MAX)
-        s_gcnt[threadIdx.x] = 0;
     int lo, hi;
     slice_of(nv, rank, C, lo, hi);
     const int per = (nv + (int)C - 1) / (int)C;
@@ -209,8 +203,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun
             const int c = s_cnt[threadIdx.x];
             int b = 0;
             if (c)
-                b = per_graph ? atomicAdd(cl.map_shared_rank(&s_gcnt[threadIdx.x], 0), c)
-                              : atomicAdd(&dr.lvl_cnt[threadIdx.x], c);
+                b = atomicAdd(&dr.lvl_cnt[threadIdx.x], c);
             s_base[threadIdx.x] = b;
             s_cnt[threadIdx.x] = 0;
         }
@@ -228,7 +221,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun
                 wpos = __shfl_sync(0xffffffffu, wpos, 0);
                 if (lv == L) {
                     const int beg = g.row_ptr[v];
-                    dr.lvl_list[(size_t)L * g.n + (per_graph ? v0 : 0) + s_base[L] + wpos +
+                    dr.lvl_list[(size_t)L * g.n + s_base[L] + wpos +
                                 __popc(m & ((1u << lane) - 1u))] = make_int2(v, beg);
                     c += (unsigned long long)(g.row_ptr[v + 1] - beg) * (L == 0 ? 1u : 2u);
                 }
@@ -248,57 +241,6 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select_rs(DevGraph g, DevRun
         }
     }
     cl.sync();   // no CTA leaves while a peer may still address its shared memory
-    if (per_graph && rank == 0 && dr.lvl_list && h <= LVL_MAX && g.epm == 1 && threadIdx.x <= (unsigned)h)
-        dr.lvl_gcnt[(size_t)gg * (LVL_MAX + 1) + threadIdx.x] = s_gcnt[threadIdx.x];
-}
-
-// Residual Splash sweeps of one round with one thread-block cluster per graph
-// (binary messages): the sub-steps of the per-level launches -- evaluate level
-// h; commit level L and evaluate the next level of the sequence h, ..., 1, 0,
-// 1, ..., h; commit level h -- over the graph's level lists, separated by
-// cluster barriers instead of kernel boundaries. The barrier's release and
-// acquire make one sub-step's messages, written by any CTA of the cluster,
-// visible to the next. Within a sub-step the reads and writes are the
-// launch form's: commits write the state buffer at level-Lc out-edges,
-// evaluations read it elsewhere and write candidates at level-Le out-edges.
-constexpr int SWEEP_THREADS = 512;
-
-template <typename S>
-__global__ void __launch_bounds__(SWEEP_THREADS, 3) k_splash_sweep_cluster(DevGraph g, DevRun dr, RunParams rp)
-{
-    cg::cluster_group cl = cg::this_cluster();
-    const unsigned C = cl.num_blocks(), rank = cl.block_rank();
-    const int gg = blockIdx.x / C;
-    // both tests give the same answer in every CTA of the cluster, so every
-    // CTA reaches the same barriers
-    if (dr.gs[gg].status != ST_RUNNING)
-        return;
-    const int v0 = g.gv_off[gg];
-    if (g.gv_off[gg + 1] == v0)
-        return;
-    const int h = rp.splash_depth;
-    const int32_t *cnt = dr.lvl_gcnt + (size_t)gg * (LVL_MAX + 1);
-    const int tid = (int)(rank * blockDim.x + threadIdx.x);
-    const int nth = (int)(C * blockDim.x);
-    for (int step = 0; step <= 2 * h + 1; ++step) {
-        const int Lc = step > 0 ? (step - 1 <= h ? h - (step - 1) : step - 1 - h) : -1;
-        const int Le = step <= 2 * h ? (step <= h ? h - step : step - h) : -1;
-        if (step > 0)
-            cl.sync();
-        const int nc = Lc >= 0 ? cnt[Lc] : 0;
-        const int ne = Le >= 0 ? cnt[Le] : 0;
-        const int2 *lc = dr.lvl_list + (size_t)(Lc >= 0 ? Lc : 0) * g.n + v0;
-        const int2 *le = dr.lvl_list + (size_t)(Le >= 0 ? Le : 0) * g.n + v0;
-        for (int t = tid; t < nc + ne; t += nth) {
-            if (t < nc) {
-                const int2 vb = lc[t];
-                splash_commit_vertex_b<S>(g, dr, vb.x, vb.y);
-            } else {
-                const int2 vb = le[t - nc];
-                splash_eval_vertex_b<S, 4>(g, dr, vb.x, vb.y, Lc);
-            }
-        }
-    }
 }
 
 template <typename K> static void set_smem_attr(K kernel)
@@ -364,103 +306,10 @@ static double plan_one(K kernel, int G, int max_keys, int key_bytes, int32_t &c_
     return best;
 }
 
+
 // Estimated time of the grid-wide selection: ~6 us per kernel (measured: 50
 // graphs of 39,600 keys took ~70 us in 10 kernels) plus every key of every
 // graph at ~150,000 keys per us over the whole GPU.
-// Clusters of c CTAs of the sweep kernel resident at once (0 if none fit).
-template <typename K>
-static int sweep_clusters(K kernel, int c, int G)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(c * std::max(1, std::min(G, 64))), 1, 1);
-    cfg.blockDim = dim3(SWEEP_THREADS, 1, 1);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)c;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, kernel, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return ncl;
-}
-
-// Cluster size of the sweep kernel: the c (1, 2, 4, 8) with the least
-// estimated time per sub-step -- per wave of resident clusters ~1 us (barrier)
-// plus ~1.2 us per pass of the cluster's c * SWEEP_THREADS threads over a
-// level of an average graph, plus the passes the largest graph adds. (The
-// cluster sweep is taken on request only: on 50 graphs of 10,000 vertices the
-// per-sub-step launches measured faster, 1035 vs 1146 ms per RS batch run of
-// 10,000 rounds, since a sub-step of either form is bound by its dependent
-// loads rather than by the launch.)
-template <typename K>
-static int plan_sweep_kernel(K kernel, int G, int n, int max_gv)
-{
-    const double avg = G > 0 ? (double)n / (double)G : 0.0;
-    double best = 1e300;
-    int best_c = 1;
-    for (int c = 1; c <= 8; c *= 2) {
-        const int ncl = sweep_clusters(kernel, c, G);
-        if (ncl < 1)
-            continue;
-        const double per = (double)c * SWEEP_THREADS;
-        const double pass_avg = std::max(1.0, std::ceil(0.5 * avg / per));
-        const double pass_max = std::max(pass_avg, std::ceil(0.5 * (double)max_gv / per));
-        const double waves = std::ceil((double)G / (double)ncl);
-        const double t = waves * (1.0 + 1.2 * pass_avg) + 1.2 * (pass_max - pass_avg);
-        if (t < best) {
-            best = t;
-            best_c = c;
-        }
-    }
-    return best_c;
-}
-
-int plan_sweep(int dtype, int G, int n, int max_gv)
-{
-    switch (dtype) {
-    case DT_F64: return plan_sweep_kernel(k_splash_sweep_cluster<double>, G, n, max_gv);
-    case DT_F32: return plan_sweep_kernel(k_splash_sweep_cluster<float>, G, n, max_gv);
-    case DT_BF16: return plan_sweep_kernel(k_splash_sweep_cluster<__nv_bfloat16>, G, n, max_gv);
-    default: return plan_sweep_kernel(k_splash_sweep_cluster<int16_t>, G, n, max_gv);
-    }
-}
-
-template <typename K>
-static void launch_sweep(K kernel, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
-{
-    const unsigned C = (unsigned)std::max(1, g.sweep_c);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)g.G * C, 1, 1);
-    cfg.blockDim = dim3(SWEEP_THREADS, 1, 1);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, g, dr, rp);
-}
-
-void launch_splash_sweep_cluster(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp,
-                                 cudaStream_t s)
-{
-    if (g.n == 0 || g.G == 0)
-        return;
-    switch (dtype) {
-    case DT_F64: launch_sweep(k_splash_sweep_cluster<double>, g, dr, rp, s); break;
-    case DT_F32: launch_sweep(k_splash_sweep_cluster<float>, g, dr, rp, s); break;
-    case DT_BF16: launch_sweep(k_splash_sweep_cluster<__nv_bfloat16>, g, dr, rp, s); break;
-    default: launch_sweep(k_splash_sweep_cluster<int16_t>, g, dr, rp, s); break;
-    }
-}
-
 static double grid_cost(int dtype, bool rs, int G, int max_keys)
 {
     return 6.0 * grid_select_launches(dtype, rs) + (double)G * (double)max_keys / 150000.0;

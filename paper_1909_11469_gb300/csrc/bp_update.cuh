@@ -290,94 +290,6 @@ __device__ __forceinline__ void splash_eval_vertex_b(const DevGraph &g, const De
         Store<S>::st(b1 + e, ising_logodds(q[e], h - incoming(e)), g.qscale);
 }
 
-// A commit of one listed vertex (ic, first out-edge bc; when hc) and the
-// evaluation of another (ie, be; when he) in one thread, their dependent
-// loads issued side by side: the commit's candidates next to the
-// evaluation's graph arrays, then the evaluation's incoming messages, then
-// the commit's stores and the evaluation's. The evaluation reads the state
-// buffer only at out-edges of sources outside level Lc (a level-Lc source is
-// read from the candidate buffer) and the commit writes it only at out-edges
-// of level-Lc vertices, so every value equals the one-entry-per-thread form.
-template <typename S>
-__device__ __forceinline__ void splash_pair_vertex_b(const DevGraph &g, const DevRun &dr, bool hc, int ic, int bc,
-                                                     bool he, int ie, int be, int Lc)
-{
-    using A = typename Store<S>::A;
-    constexpr int CACHE = 4;
-    S *b0 = (S *)dr.msg[0];
-    S *b1 = (S *)dr.msg[1];
-    S v[CACHE];
-    int endc = bc;
-    if (hc) {
-#pragma unroll
-        for (int k = 0; k < CACHE; ++k)
-            if (bc + k < g.M)
-                v[k] = b1[bc + k];
-        endc = g.row_ptr[ic + 1];
-    }
-    A h = 0;
-    const A *q;
-    if constexpr (sizeof(A) == 8)
-        q = (const A *)g.q64;
-    else
-        q = (const A *)g.q32;
-    int rf[CACHE], rc[CACHE];
-    int ende = be;
-    if (he) {
-        if constexpr (sizeof(A) == 8)
-            h = g.udiff64[ie];
-        else
-            h = g.udiff32[ie];
-#pragma unroll
-        for (int k = 0; k < CACHE; ++k) {
-            if (be + k < g.M) {
-                rf[k] = g.rev[be + k];
-                rc[k] = g.col[be + k];
-            }
-        }
-        ende = g.row_ptr[ie + 1];
-    }
-    const int dege = ende - be;
-    A uin[CACHE];
-#pragma unroll
-    for (int k = 0; k < CACHE; ++k) {
-        if (k < dege) {
-            const A u0 = Store<S>::ld(b0 + rf[k], g.qscale);
-            if (Lc >= 0) {
-                const A u1 = Store<S>::ld((const S *)b1 + rf[k], g.qscale);
-                uin[k] = dr.level[rc[k]] == Lc ? u1 : u0;
-            } else {
-                uin[k] = u0;
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < CACHE; ++k)
-        if (bc + k < endc)
-            b0[bc + k] = v[k];
-    for (int e = bc + CACHE; e < endc; ++e)
-        b0[e] = b1[e];
-    if (dege <= 0)
-        return;
-    auto incoming = [&](int e) -> A {
-        const int f = g.rev[e];
-        const bool fresh = Lc >= 0 && dr.level[g.col[e]] == Lc;
-        return Store<S>::ld((fresh ? (const S *)b1 : (const S *)b0) + f, g.qscale);
-    };
-#pragma unroll
-    for (int k = 0; k < CACHE; ++k)
-        if (k < dege)
-            h += uin[k];
-    for (int e = be + CACHE; e < ende; ++e)
-        h += incoming(e);
-#pragma unroll
-    for (int k = 0; k < CACHE; ++k)
-        if (k < dege)
-            Store<S>::st(b1 + be + k, ising_logodds(q[be + k], h - uin[k]), g.qscale);
-    for (int e = be + CACHE; e < ende; ++e)
-        Store<S>::st(b1 + e, ising_logodds(q[e], h - incoming(e)), g.qscale);
-}
-
 // Residual Splash sweep step for vertex i with level lv: commit its
 // out-messages when lv == Lc, or evaluate them when lv == Le. Returns the
 // number of messages committed.

@@ -75,7 +75,7 @@ def test_default_options(L):
     assert o.msg_dtype == bp.BP_F32 and o.cuda_stream is None
     # automatic choices: update mapping, selection path, sweep form, launch overlap
     assert o.kernel_variant == 0 and o.select_path == 0 and o.splash_sweep == 0 and o.overlap_launches == 0
-    assert bp.bp_default_options(splash_sweep=2, overlap_launches=2).splash_sweep == 2
+    assert bp.bp_default_options(splash_sweep=1, overlap_launches=2).splash_sweep == 1
 
 
 def _expect(code, fn):

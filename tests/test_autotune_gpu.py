@@ -29,9 +29,9 @@ def test_autotune_records_choice():
     prob = synth.ising_grid_batch(40, 2.5, range(8))
     with bp.Graph(prob) as g:
         r = g.autotune("rnbp", 0.5, eps=1e-4, trial_rounds=8)
-        assert r["kernel_variant"] in (1, 2, 3, 4, 5, 6)
-        tried = [v for v in (1, 2, 3, 4, 5, 6) if r["ms_per_round"][v] > 0]
-        assert tried == [1, 2, 3, 4, 5, 6]
+        assert r["kernel_variant"] in (1, 3, 4, 6)
+        tried = [v for v in range(8) if r["ms_per_round"][v] > 0]
+        assert tried == [1, 3, 4, 6]
         best = min(tried, key=lambda v: r["ms_per_round"][v])
         assert r["kernel_variant"] == best
         sc = r["size_class"]

@@ -248,7 +248,7 @@ def test_potts_trace_follow(dtype, tol, sched, par):
 
 
 # ------------------------------------------------------------ batches
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 3, 4])
 @pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5), ("rbp", 0.05), ("rs", 0.05)])
 def test_batch_equals_independent_runs(sched, par, variant):
     """A batch of uneven graphs: every graph converges or stops on its own and

@@ -1,6 +1,6 @@
-"""The binary update mappings (thread per vertex, tiled edge quads, the
-persistent cluster kernel, the prefetching thread-per-vertex forms, the
-streamed warp tiles) compute the same arithmetic in the same order, so every
+"""The binary update mappings (thread per vertex, the persistent cluster
+kernel, the prefetching thread-per-vertex form, the streamed warp tiles)
+compute the same arithmetic in the same order, so every
 schedule and storage format gives bit-identical beliefs, rounds and counters
 whichever mapping runs."""
 import numpy as np
@@ -10,7 +10,7 @@ from paper_1909_11469_gb300 import bp, synth
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [1, 2, 3, 4, 5, 6]
+VARIANTS = [1, 3, 4, 6]
 
 
 @pytest.fixture(scope="module", autouse=True)
