@@ -210,27 +210,39 @@ __global__ void __launch_bounds__(BLOCK) k_eval_gen(DevGraph g, DevRun dr, RunPa
 }
 
 // --------------------------------------------------------------------------
-// Per-graph decision after an evaluation (one warp per graph).
-__global__ void k_decide(DevGraph g, DevRun dr, RunParams rp)
+// Per-graph decision after an evaluation: one warp per graph, eight graphs
+// per block (a batch of thousands of graphs launches a few hundred blocks, not
+// one tiny block per graph). The graph's state, its reduction sub-slots and
+// its frontier fraction are independent loads, issued together; the slots of
+// a stopped graph are already zero (its evaluations are skipped), so only a
+// running graph clears them.
+constexpr int DECIDE_BLOCK = 256;
+
+__global__ void __launch_bounds__(DECIDE_BLOCK) k_decide(DevGraph g, DevRun dr, RunParams rp)
 {
     griddep_launch_dependents();
     griddep_wait();
-    const int gg = blockIdx.x;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int gg = (int)(((unsigned)blockIdx.x * DECIDE_BLOCK + threadIdx.x) >> 5);
     if (gg == 0 && lane <= LVL_MAX && dr.lvl_cnt)
         dr.lvl_cnt[lane] = 0;   // Residual Splash level lists of this round start empty
-    GState *stp = dr.gs + gg;
-    if (stp->status != ST_RUNNING)
+    if (gg >= g.G)
         return;
+    GState *stp = dr.gs + gg;
+    GState st = {};
+    if (lane == 0)
+        st = *stp;
     unsigned long long mb = dr.red_max[(size_t)gg * NSUB + lane];
     unsigned int c = dr.red_cnt[(size_t)gg * NSUB + lane];
+    const double low_p = lane == 0 ? graph_low_p(dr, rp, gg) : 0.0;
+    if (__shfl_sync(0xffffffffu, st.status, 0) != ST_RUNNING)
+        return;
     dr.red_max[(size_t)gg * NSUB + lane] = 0ull;
     dr.red_cnt[(size_t)gg * NSUB + lane] = 0u;
     mb = warp_max_u64(mb);
     c = warp_sum_u32(c);
     if (lane != 0)
         return;
-    GState st = *stp;
     const double maxr = __longlong_as_double((long long)mb);
     const int64_t Mg = g.ge_off[gg + 1] - g.ge_off[gg];
     const int64_t ng = g.gv_off[gg + 1] - g.gv_off[gg];
@@ -249,14 +261,13 @@ __global__ void k_decide(DevGraph g, DevRun dr, RunParams rp)
             st.cur ^= 1;
             st.committed += (unsigned long long)Mg;
         } else if (rp.schedule == SCHED_RNBP) {
-            const double p = edge_ratio_p(rp, graph_low_p(dr, rp, gg), st.rounds, c, st.n_prev);
+            const double p = edge_ratio_p(rp, low_p, st.rounds, c, st.n_prev);
             st.always = (p >= 1.0) ? 1 : 0;
             st.thr = (p <= 0.0 || p >= 1.0) ? 0u : (uint32_t)(uint64_t)(p * 4294967296.0);
         } else {
             const int64_t base = (rp.schedule == SCHED_RS && rp.rs_roots_mode == 1) ? ng : Mg;
             const int64_t hi = (rp.schedule == SCHED_RS) ? ng : Mg;
-            const double p = rp.dynamic_p ? edge_ratio_p(rp, graph_low_p(dr, rp, gg), st.rounds, c, st.n_prev)
-                                          : graph_low_p(dr, rp, gg);
+            const double p = rp.dynamic_p ? edge_ratio_p(rp, low_p, st.rounds, c, st.n_prev) : low_p;
             double v = ceil(p * (double)base);
             int64_t kk = (v > (double)hi) ? hi : (int64_t)v;
             kk = kk < 1 ? 1 : kk;
@@ -932,7 +943,8 @@ cudaError_t preload_lbp_f32_kernels()
 
 void launch_decide(const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)
 {
-    launch_k(rp.pdl, k_decide, g.G, 32, s, g, dr, rp);
+    const int per_block = DECIDE_BLOCK / 32;
+    launch_k(rp.pdl, k_decide, (g.G + per_block - 1) / per_block, DECIDE_BLOCK, s, g, dr, rp);
 }
 
 void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, cudaStream_t s)

@@ -39,6 +39,45 @@ def test_mappings_bit_identical(name, dtype, sched, par):
         assert np.array_equal(bel, bel0), (v, float(np.abs(bel - bel0).max()))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "q16"])
+def test_rnbp_state_bit_identical(dtype):
+    """RnBP on the streamed mapping (warp-tile commit) and on the thread-per-
+    vertex mapping (vertex-tile commit): the stored messages, the final
+    residuals, the per-round commit trace and the per-graph counters are the
+    same bits, on a batch whose graphs stop at different rounds."""
+    prob = synth.concat_batch([synth.er_batch(30, 5, n_max=600), synth.ising_grid(12, 0.3, seed=4),
+                               synth.ising_chain(50, 0.2, seed=2)])
+    out = {}
+    for v in (1, 6):
+        with bp.Graph(prob) as g:
+            st = g.run("rnbp", 0.5, eps=1e-4, max_rounds=60, msg_dtype=dtype, seed=7, kernel_variant=v,
+                       record_trace=1, trace_capacity=61)
+            out[v] = (st["rounds"], st["committed_updates"], g.messages(), g.residuals(), g.trace("rnbp"),
+                      [(x["converged"], x["rounds"], x["committed_updates"]) for x in g.graph_stats()])
+    assert out[1][0] == out[6][0] and out[1][1] == out[6][1]
+    assert out[1][5] == out[6][5]
+    assert len({r for _, r, _ in out[6][5]}) > 1          # graphs stopped at different rounds
+    for i in (2, 3, 4):
+        assert np.array_equal(out[1][i], out[6][i]), i
+
+
+def test_rnbp_time_budget_stop_equals_round_cap():
+    """A run stopped by its wall-clock budget ends after a whole round (the
+    round's commit included): its messages equal those of a run of the other
+    mapping stopped by max_rounds at the same committed round."""
+    prob = synth.ising_grid(60, 3.0, seed=1)
+    with bp.Graph(prob) as g:
+        st = g.run("rnbp", 0.5, eps=1e-12, max_rounds=10_000_000, time_budget_ms=50.0, kernel_variant=6,
+                   seed=2)
+        assert st["status"] == bp.BP_ERR_TIMEOUT and not st["converged"]
+        rounds, committed, msg = st["rounds"], st["committed_updates"], g.messages()
+    assert rounds > 1
+    with bp.Graph(prob) as g:
+        st1 = g.run("rnbp", 0.5, eps=1e-12, max_rounds=rounds, kernel_variant=1, seed=2)
+        assert st1["rounds"] == rounds and st1["committed_updates"] == committed
+        assert np.array_equal(g.messages(), msg)
+
+
 def _star_batch(leaves_list, seed=0):
     """Stars (one hub joined to `leaves` vertices) followed by isolated
     vertices, as one batch: hubs at the tile edge limit, tiles cut by the
