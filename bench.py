@@ -547,8 +547,9 @@ def main():
     elif prof_step:
         kname = ""
         if prob.k > 2:
-            kname = {1: "k_potts_tc (CUDA cores)", 2: "k_potts_tc (tcgen05, BF16 products)",
-                     3: "k_potts_tc (tcgen05, split BF16 products)"}.get(
+            tc_name = "k_potts_ws" if prob.k == 32 else "k_potts_tc"   # k = 32: warp-specialised form
+            kname = {1: "k_potts_tc_pipe (CUDA cores)", 2: f"{tc_name} (tcgen05, BF16 products)",
+                     3: f"{tc_name} (tcgen05, split BF16 products)"}.get(
                         args.potts_path or (3 if prob.k >= 16 else 0), "k_eval_gen")
         iso = {}
         for sched, p in wl["schedules"]:

@@ -136,6 +136,7 @@ struct bp_graph {
     int32_t n_chunks_rbp = 0, n_chunks_rs = 0;
     // tensor-core tiles of consecutive vertices (<= 128 out-edges, <= 32 vertices)
     int32_t *d_tc_tiles = nullptr;
+    TcTileRec *d_tc_rec = nullptr;   // one static record per tile
     int32_t n_tc_tiles = 0;
     bool tc_tiles_ok = false;
     int32_t *d_err = nullptr;
@@ -489,6 +490,31 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
         if ((rc = dalloc(&g->d_tc_tiles, tv.size())))
             return rc;
         BP_CK(cudaMemcpy(g->d_tc_tiles, tv.data(), sizeof(int32_t) * tv.size(), cudaMemcpyHostToDevice));
+        if (ok && g->n_tc_tiles > 0) {
+            std::vector<TcTileRec> rec((size_t)g->n_tc_tiles);
+            for (int32_t t = 0; t < g->n_tc_tiles; ++t) {
+                TcTileRec &r = rec[(size_t)t];
+                memset(&r, 0, sizeof(r));
+                const int32_t va = tv[(size_t)t], vb = tv[(size_t)t + 1];
+                r.va = va;
+                r.nvt = vb - va;
+                r.e0 = (int32_t)row_ptr[va];
+                r.ne = (int32_t)(row_ptr[vb] - row_ptr[va]);
+                r.gg0 = gid[(size_t)va];
+                r.gg1 = gid[(size_t)vb - 1];
+                for (int32_t v = va; v < vb; ++v) {
+                    r.rpl[v - va] = (uint8_t)(row_ptr[v] - r.e0);
+                    for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+                        r.src[e - r.e0] = (uint8_t)(v - va);
+                        r.rev[e - r.e0] = rev[e];
+                    }
+                }
+                r.rpl[r.nvt] = (uint8_t)r.ne;
+            }
+            if ((rc = dalloc(&g->d_tc_rec, rec.size())))
+                return rc;
+            BP_CK(cudaMemcpy(g->d_tc_rec, rec.data(), sizeof(TcTileRec) * rec.size(), cudaMemcpyHostToDevice));
+        }
     }
     if ((rc = dalloc(&g->d_err, 1)))
         return rc;
@@ -565,7 +591,8 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
         cudaEventRecord(ev[0], s);
     const int emode = rp.schedule == SCHED_LBP ? MODE_LBP : MODE_CAND;
     if (rp.tc_path)
-        launch_potts_tc(dtype, dg, dr, rp, emode, g->d_tc_tiles, g->n_tc_tiles, rp.tc_path, g->d_err, s);
+        launch_potts_tc(dtype, dg, dr, rp, emode, g->d_tc_tiles, g->d_tc_rec, g->n_tc_tiles, rp.tc_path, g->d_err,
+                        s);
     else
         launch_eval(dtype, dg, dr, rp, emode, 0, g->kp, s);
     kernels += any;
@@ -1519,7 +1546,8 @@ int bp_time_update(bp_graph *g, int32_t schedule, double parallelism, const bp_o
     BP_CK(cudaEventRecord(g->ev0, s));
     for (int32_t l = 0; l < launches; ++l) {
         if (rp.tc_path)
-            launch_potts_tc(dtype, dg, dr, rp, emode, g->d_tc_tiles, g->n_tc_tiles, rp.tc_path, g->d_err, s);
+            launch_potts_tc(dtype, dg, dr, rp, emode, g->d_tc_tiles, g->d_tc_rec, g->n_tc_tiles, rp.tc_path, g->d_err,
+                        s);
         else
             launch_eval(dtype, dg, dr, rp, emode, 0, g->kp, s);
     }
@@ -1606,6 +1634,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_running);
     dfree(g->d_queue);
     dfree(g->d_tc_tiles);
+    dfree(g->d_tc_rec);
     dfree(g->d_err);
     dfree(g->d_wtiles);
     dfree(g->d_trace);

@@ -63,13 +63,27 @@ void launch_messages(int dtype, const DevGraph &g, const DevRun &dr, int kp, dou
 cudaError_t launch_persistent(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp,
                               long long budget_ns, cudaStream_t s);
 
+// Static description of one shared-table tile (built on the host with the
+// tiles): its vertex and edge range, the graphs of its first and last vertex,
+// the local first row of every vertex (rpl[nvt] = ne), the local source vertex
+// and the rev of every row (0 past the tile). A multiple of 16 bytes.
+struct TcTileRec {
+    int32_t va, nvt, e0, ne;
+    int32_t gg0, gg1, pad0, pad1;
+    uint8_t rpl[48];
+    uint8_t src[128];
+    int32_t rev[128];
+};
+static_assert(sizeof(TcTileRec) % 16 == 0, "tile records are copied in 16-byte words");
+
 // Shared-table (Potts) update in tiles of consecutive vertices with at most
-// 128 out-edges and 32 vertices (tile_v, n_tiles + 1 entries); path 1 = CUDA
-// cores, 2 = tensor cores with BF16 products, 3 = tensor cores with the BF16
-// residual products added. FP32 or BF16 storage.
+// 128 out-edges and 32 vertices (tile_v, n_tiles + 1 entries; tile_rec, one
+// record per tile); path 1 = CUDA cores, 2 = tensor cores with BF16 products,
+// 3 = tensor cores with the BF16 residual products added. FP32 or BF16 storage.
 void prepare_potts_tc();
 void launch_potts_tc(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode,
-                     const int *tile_v, int n_tiles, int path, int *err_flag, cudaStream_t s);
+                     const int *tile_v, const TcTileRec *tile_rec, int n_tiles, int path, int *err_flag,
+                     cudaStream_t s);
 
 // Sets the calling thread's message returned by bp_last_error().
 void set_last_error(const std::string &msg);

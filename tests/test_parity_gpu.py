@@ -390,6 +390,42 @@ def test_potts_tensor_core_ragged_tiles():
     assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F32
 
 
+def _potts_members_shared_table():
+    """k = 32 members of one shared table: two grids, a chain (a tree: exact
+    after its diameter) and a pair of vertices, so tensor-core tiles span
+    graph boundaries and graphs stop at different rounds."""
+    members = [synth.potts_grid(7, 32, seed=1), synth.potts_grid(13, 32, seed=3, cols=5),
+               synth.potts_grid(1, 32, seed=4, cols=40), synth.potts_grid(1, 32, seed=5, cols=2)]
+    for mbr in members[1:]:
+        mbr.pair_log = members[0].pair_log.copy()
+    return members
+
+
+@pytest.mark.parametrize("path,dtype,tol", [(3, "f32", TOL_F32), (2, "f32", TOL_BF16), (3, "bf16", 1.6e-2)])
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.5)])
+def test_potts_tensor_core_batch(path, dtype, tol, sched, par):
+    """A batch of k = 32 graphs on the tensor-core paths: every graph matches
+    the oracle run of that graph alone that follows the graph's own recorded
+    frontiers for its own rounds (BF16 storage: the BF16-emulating oracle)."""
+    members = _potts_members_shared_table()
+    batch = synth.concat_batch(members)
+    res = gpu_run(batch, sched, par, 1e-4, 60, dtype, trace=61, seed=4, potts_path=path)
+    rounds = [x["rounds"] for x in res["graph_stats"]]
+    assert len(set(rounds)) > 1, rounds
+    storage = "bf16" if dtype == "bf16" else "f64"
+    for gi, mbr in enumerate(members):
+        v0, v1 = batch.graph_var_offsets[gi], batch.graph_var_offsets[gi + 1]
+        e0, e1 = batch.row_ptr[v0], batch.row_ptr[v1]
+        r = rounds[gi]
+        if sched == "lbp":
+            tr = all_ones_trace(mbr.m, r)
+        else:
+            tr = _trace_bits(res["trace"][:r], int(e0), int(e1))
+        ref = oracle.run(mbr, sched, eps=1e-4, storage=storage, trace_in=tr, trace_rounds=r)
+        err = np.abs(res["beliefs"][v0:v1] - ref["beliefs"]).max()
+        assert err < tol, (gi, err)
+
+
 def _random_graph(n, m, seed):
     rng = np.random.default_rng(seed)
     seen = set()
