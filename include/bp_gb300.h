@@ -246,7 +246,11 @@ int bp_create_batch(int32_t n_graphs, const int64_t *graph_var_offsets, int32_t 
  * the start of a run, no mass on the absent ones) and absent states get
  * belief 0. Needs BP_PAIR_TABLE (BP_ERR_UNSUPPORTED otherwise; table entries
  * may also be -inf) and at least one present state per vertex
- * (BP_ERR_NONFINITE). NaN and +inf are rejected everywhere.
+ * (BP_ERR_NONFINITE). NaN and +inf are rejected everywhere. Binary Ising
+ * couplings (BP_PAIR_ISING_BETA) are copied as they are and checked and
+ * turned into the update's arrays on the device (the call returns when that
+ * work is done); after a rejected call the handle has no potentials until the
+ * next successful one.
  */
 int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind,
                       const float *pair_log);

@@ -140,6 +140,8 @@ struct bp_graph {
     int32_t n_tc_tiles = 0;
     bool tc_tiles_ok = false;
     int32_t *d_err = nullptr;
+    PotCheck *d_potcheck = nullptr;   // checks of the device-side Ising potentials
+    int32_t pot_bufs_kind = -1;       // pair kind whose potential buffers are allocated
     // warp tiles of the streamed update (mapping 6), n_wtiles + 1 records; 0
     // tiles when a vertex has more than STREAM_WT out-edges
     int4 *d_wtiles = nullptr;
@@ -828,6 +830,68 @@ int bp_create_batch(int32_t n_graphs, const int64_t *graph_var_offsets, int32_t 
     return create_common(n_graphs, graph_var_offsets, n, n_states, n_dir_edges, row_ptr, col, rev, out);
 }
 
+// Binary Ising potentials: the raw unary log-potentials and couplings are
+// copied to the device, where kernels check them and derive the arrays of the
+// update (launch_pot_ising), instead of host loops over every edge. The
+// buffers keep their addresses across calls (their sizes are fixed by the
+// graph), so captured rounds are dropped only when the storage scales change.
+static int set_ising_potentials(bp_graph *g, const float *unary_log, const float *beta)
+{
+    const int32_t n = g->n;
+    const int64_t M = g->M;
+    int rc;
+    g->has_pot = false;
+    g->has_result = false;
+    if (g->pot_bufs_kind != BP_PAIR_ISING_BETA) {
+        dfree(g->d_unary);
+        dfree(g->d_udiff32);
+        dfree(g->d_udiff64);
+        dfree(g->d_q32);
+        dfree(g->d_q64);
+        dfree(g->d_pair);
+        dfree(g->d_psi_shared);
+        dfree(g->d_kpresent);
+        clear_cache(g);
+        g->pot_bufs_kind = -1;
+        if ((rc = dalloc(&g->d_unary, (size_t)n * 2)) || (rc = dalloc(&g->d_udiff64, (size_t)n)) ||
+            (rc = dalloc(&g->d_udiff32, (size_t)n + PAD)) || (rc = dalloc(&g->d_q64, (size_t)M)) ||
+            (rc = dalloc(&g->d_q32, (size_t)M + PAD)))
+            return rc;
+        g->pot_bufs_kind = BP_PAIR_ISING_BETA;
+    }
+    if (!g->d_potcheck && (rc = dalloc(&g->d_potcheck, 1)))
+        return rc;
+    if (n)
+        BP_CK(cudaMemcpy(g->d_unary, unary_log, sizeof(float) * (size_t)n * 2, cudaMemcpyHostToDevice));
+    if (M)
+        BP_CK(cudaMemcpy(g->d_q32, beta, sizeof(float) * (size_t)M, cudaMemcpyHostToDevice));
+    PotCheck hc;
+    BP_CK(launch_pot_ising(g->d_unary, g->d_q32, g->d_q64, g->d_udiff32, g->d_udiff64, g->d_rev, n, (int)M,
+                           g->d_potcheck, &hc));
+    if (hc.flags & 1u)
+        return fail(BP_ERR_NONFINITE, "NaN or +inf unary log-potential");
+    if (hc.flags & 2u)
+        return fail(BP_ERR_NONFINITE, "a vertex has no present state");
+    if (hc.flags & 4u)
+        return fail(BP_ERR_UNSUPPORTED, "absent states (unary -inf) need per-edge tables (BP_PAIR_TABLE)");
+    if (hc.flags & 8u)
+        return fail(BP_ERR_NONFINITE, "NaN, +inf or (outside tables) -inf pairwise log-potential");
+    if (hc.flags & 16u)
+        return fail(BP_ERR_NONFINITE, "beta[rev[e]] != beta[e] at edge " + std::to_string(hc.bad_edge));
+    float bmaxf;
+    memcpy(&bmaxf, &hc.bmax_bits, sizeof(float));
+    const double bmax = (double)bmaxf;
+    const float qs = bmax > 0.0 ? (float)(2.0 * bmax / 32767.0) : 1.0f / 32767.0f;
+    const float bs = bf16_scale(bmax > 0.0 ? bmax : 0.5);
+    if (qs != g->qscale || bs != g->bscale)
+        clear_cache(g);   // captured rounds hold the storage scales by value
+    g->qscale = qs;
+    g->bscale = bs;
+    g->pair_kind = BP_PAIR_ISING_BETA;
+    g->has_pot = true;
+    return BP_OK;
+}
+
 int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, const float *pair_log)
 {
     if (!g || !unary_log || (!pair_log && !(pair_kind == BP_PAIR_ISING_BETA && g->M == 0) &&
@@ -840,6 +904,8 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
         return fail(BP_ERR_INVALID_ARG, "unknown pair kind");
     if (pair_kind == BP_PAIR_ISING_BETA && k != 2)
         return fail(BP_ERR_INVALID_ARG, "Ising beta potentials need n_states = 2");
+    if (pair_kind == BP_PAIR_ISING_BETA)
+        return set_ising_potentials(g, unary_log, pair_log);
     if (!finite_or_neg_inf(unary_log, (size_t)n * k))
         return fail(BP_ERR_NONFINITE, "NaN or +inf unary log-potential");
     // a state with unary log-potential -inf is absent (variable state counts)
@@ -856,16 +922,11 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
     }
     if (absent && pair_kind != BP_PAIR_TABLE)
         return fail(BP_ERR_UNSUPPORTED, "absent states (unary -inf) need per-edge tables (BP_PAIR_TABLE)");
-    size_t plen = pair_kind == BP_PAIR_ISING_BETA ? (size_t)M
-                  : pair_kind == BP_PAIR_TABLE    ? (size_t)M * k * k
-                                                  : (size_t)k * k;
+    // (binary Ising potentials took the device path above)
+    size_t plen = pair_kind == BP_PAIR_TABLE ? (size_t)M * k * k : (size_t)k * k;
     if (plen && !(pair_kind == BP_PAIR_TABLE ? finite_or_neg_inf(pair_log, plen) : all_finite(pair_log, plen)))
         return fail(BP_ERR_NONFINITE, "NaN, +inf or (outside tables) -inf pairwise log-potential");
-    if (pair_kind == BP_PAIR_ISING_BETA) {
-        for (int64_t e = 0; e < M; ++e)
-            if (pair_log[e] != pair_log[g->h_rev[(size_t)e]])
-                return fail(BP_ERR_NONFINITE, "beta[rev[e]] != beta[e] at edge " + std::to_string(e));
-    } else if (pair_kind == BP_PAIR_TABLE) {
+    if (pair_kind == BP_PAIR_TABLE) {
         for (int64_t e = 0; e < M; ++e) {
             const float *a = pair_log + (size_t)e * k * k;
             const float *b = pair_log + (size_t)g->h_rev[(size_t)e] * k * k;
@@ -883,6 +944,7 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
     }
     g->has_pot = false;
     g->has_result = false;
+    g->pot_bufs_kind = -1;
     dfree(g->d_unary);
     dfree(g->d_udiff32);
     dfree(g->d_udiff64);
@@ -915,28 +977,7 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind, co
     }
     g->qscale = 1.0f / 32767.0f;
     g->bscale = bf16_scale(0.5);
-    if (pair_kind == BP_PAIR_ISING_BETA) {
-        double bmax = 0.0;
-        for (int64_t e = 0; e < M; ++e)
-            bmax = std::max(bmax, std::fabs((double)pair_log[e]));
-        if (bmax > 0.0) {
-            g->qscale = (float)(2.0 * bmax / 32767.0);
-            g->bscale = bf16_scale(bmax);
-        }
-        std::vector<double> q64((size_t)M);
-        std::vector<float> q32((size_t)M);
-        for (int64_t e = 0; e < M; ++e) {
-            double q = std::exp(-2.0 * (double)pair_log[e]);
-            q64[(size_t)e] = std::min(std::max(q, 1e-300), 1e300);
-            q32[(size_t)e] = (float)std::min(std::max(q, 1e-30), 1e30);
-        }
-        if ((rc = dalloc(&g->d_q64, (size_t)M)) || (rc = dalloc(&g->d_q32, (size_t)M + PAD)))
-            return rc;
-        if (M) {
-            BP_CK(cudaMemcpy(g->d_q64, q64.data(), sizeof(double) * (size_t)M, cudaMemcpyHostToDevice));
-            BP_CK(cudaMemcpy(g->d_q32, q32.data(), sizeof(float) * (size_t)M, cudaMemcpyHostToDevice));
-        }
-    } else if (pair_kind == BP_PAIR_TABLE) {
+    if (pair_kind == BP_PAIR_TABLE) {
         if ((rc = dalloc(&g->d_pair, plen)))
             return rc;
         if (plen && absent) {
@@ -1636,6 +1677,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_tc_tiles);
     dfree(g->d_tc_rec);
     dfree(g->d_err);
+    dfree(g->d_potcheck);
     dfree(g->d_wtiles);
     dfree(g->d_trace);
     dfree(g->d_beliefs);

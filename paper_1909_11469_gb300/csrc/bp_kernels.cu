@@ -704,6 +704,101 @@ __global__ void k_init_msgs_var(DevGraph g, S *a, S *b)
     }
 }
 
+// --------------------------------------------------------------------------
+// Binary Ising potentials (Eq. 1 with the coupling table of the Ising layout):
+// validation and derived arrays on the device, so that setting the
+// potentials of a large batch costs two copies and two passes.
+// Checks: unary log-potentials finite (flags bit 0: NaN or +inf; bit 1: a
+// vertex with both states -inf; bit 2: one state -inf, an absent state),
+// couplings finite (bit 3) and symmetric, beta[rev e] == beta[e] (bit 4, the
+// lowest such edge in bad_edge); max |beta| as float bits.
+__global__ void k_pot_check_ising(const float *unary, const float *beta, const int32_t *rev, int n, int M,
+                                  PotCheck *out)
+{
+    unsigned flags = 0, bmax = 0;
+    int bad = 0x7fffffff;
+    const int stride = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < max(n, M); t += stride) {
+        if (t < n) {
+            const float u0 = unary[2 * (size_t)t], u1 = unary[2 * (size_t)t + 1];
+            if (isnan(u0) || isnan(u1) || (isinf(u0) && u0 > 0.0f) || (isinf(u1) && u1 > 0.0f))
+                flags |= 1u;
+            const int ninf = (isinf(u0) && u0 < 0.0f) + (isinf(u1) && u1 < 0.0f);
+            flags |= ninf == 2 ? 2u : (ninf == 1 ? 4u : 0u);
+        }
+        if (t < M) {
+            const float b = beta[t];
+            if (!isfinite(b)) {
+                flags |= 8u;
+            } else {
+                bmax = max(bmax, __float_as_uint(fabsf(b)));
+                if (beta[rev[t]] != b) {
+                    flags |= 16u;
+                    bad = min(bad, t);
+                }
+            }
+        }
+    }
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    bmax = __reduce_max_sync(0xffffffffu, bmax);
+    bad = __reduce_min_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        if (flags)
+            atomicOr(&out->flags, flags);
+        if (bmax)
+            atomicMax(&out->bmax_bits, bmax);
+        if (bad != 0x7fffffff)
+            atomicMin(&out->bad_edge, bad);
+    }
+}
+
+// Derived arrays: udiff = u(1) - u(0) (FP64 and FP32), q = exp(-2 beta)
+// clamped to [1e-300, 1e300] (FP64) and [1e-30, 1e30] (FP32). q32 holds beta
+// on entry; each element is read and rewritten by the same thread.
+__global__ void k_pot_derive_ising(const float *unary, float *q32, double *q64, float *ud32, double *ud64, int n,
+                                   int M)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < max(n, M); t += stride) {
+        if (t < n) {
+            const double d = (double)unary[2 * (size_t)t + 1] - (double)unary[2 * (size_t)t];
+            ud64[t] = d;
+            ud32[t] = (float)d;
+        }
+        if (t < M) {
+            const double q = exp(-2.0 * (double)q32[t]);
+            q64[t] = fmin(fmax(q, 1e-300), 1e300);
+            q32[t] = (float)fmin(fmax(q, 1e-30), 1e30);
+        }
+    }
+}
+
+cudaError_t launch_pot_ising(const float *unary, float *beta_q32, double *q64, float *ud32, double *ud64,
+                             const int32_t *rev, int n, int M, PotCheck *check, PotCheck *host_check)
+{
+    const int total = std::max(std::max(n, M), 1);
+    const int nb = std::min((total + BLOCK - 1) / BLOCK, 152 * 16);
+    cudaError_t e;
+    PotCheck init;
+    init.flags = 0;
+    init.bad_edge = 0x7fffffff;
+    init.bmax_bits = 0;
+    init.pad = 0;
+    if ((e = cudaMemcpy(check, &init, sizeof(PotCheck), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    k_pot_check_ising<<<nb, BLOCK>>>(unary, beta_q32, rev, n, M, check);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpy(host_check, check, sizeof(PotCheck), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    if (host_check->flags)
+        return cudaSuccess;   // the caller reports the first failed check; nothing derived
+    k_pot_derive_ising<<<nb, BLOCK>>>(unary, beta_q32, q64, ud32, ud64, n, M);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    return cudaDeviceSynchronize();
+}
+
 __global__ void k_init_state(DevRun dr, int G)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G * NSUB; t += gridDim.x * blockDim.x) {

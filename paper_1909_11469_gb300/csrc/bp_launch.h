@@ -12,6 +12,20 @@ enum { SCHED_LBP = 0, SCHED_RBP = 1, SCHED_RS = 2, SCHED_RNBP = 3 };
 enum { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2, DT_Q16 = 3 };
 
 void launch_init(int dtype, const DevGraph &g, const DevRun &dr, cudaStream_t s);
+// Binary Ising potentials on the device (bp_set_potentials): checks, then
+// (when every check passes) the derived arrays. beta_q32 holds beta on entry
+// and exp(-2 beta) in FP32 on return; host_check receives the checks (flags
+// bit 0 unary NaN / +inf, bit 1 a vertex without a present state, bit 2 an
+// absent state, bit 3 non-finite beta, bit 4 beta[rev e] != beta[e] with the
+// lowest such e in bad_edge) and max |beta| as float bits. Synchronous.
+struct PotCheck {
+    unsigned flags;
+    int bad_edge;
+    unsigned bmax_bits;
+    int pad;
+};
+cudaError_t launch_pot_ising(const float *unary, float *beta_q32, double *q64, float *ud32, double *ud64,
+                             const int32_t *rev, int n, int M, PotCheck *check, PotCheck *host_check);
 void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode, int level_L,
                  int kp, cudaStream_t s);
 // Streamed warp-tile update (bp_stream.cu, update mapping 6; FP32, BF16, Q16).
