@@ -123,6 +123,7 @@ struct bp_graph {
     GState *d_gs = nullptr;
     unsigned long long *d_red_max = nullptr;
     unsigned int *d_red_cnt = nullptr;
+    unsigned int *d_red_commit = nullptr;
     int32_t *d_running = nullptr;
     int32_t *d_queue = nullptr;
     int32_t max_graph_vertices = 0;
@@ -145,6 +146,7 @@ struct bp_graph {
     // warp tiles of the streamed update (mapping 6), n_wtiles + 1 records; 0
     // tiles when a vertex has more than STREAM_WT out-edges
     int4 *d_wtiles = nullptr;
+    uint32_t *d_eps_words = nullptr;   // RnBP eps flag words, 4 per warp tile (lazy)
     int32_t n_wtiles = 0;
     bool wtiles_ok = false;
     uint32_t *d_trace = nullptr;
@@ -297,6 +299,7 @@ DevRun dev_run(const bp_graph *g)
     r.gs = g->d_gs;
     r.red_max = g->d_red_max;
     r.red_cnt = g->d_red_cnt;
+    r.red_commit = g->d_red_commit;
     r.n_running = g->d_running;
     r.trace = g->d_trace;
     r.beliefs = g->d_beliefs;
@@ -305,6 +308,7 @@ DevRun dev_run(const bp_graph *g)
     r.lvl_cnt = g->d_lvl_cnt;
     r.graph_p = g->graph_p_set ? g->d_graph_p : nullptr;
     r.err = g->d_err;
+    r.eps_words = g->d_eps_words;
     r.gsel = g->d_gsel;
     r.gsel_hist = g->d_gsel_hist;
     r.gsel_tie = g->d_gsel_tie;
@@ -461,7 +465,8 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     BP_CK(cudaMemcpy(g->d_ge_off, ge.data(), sizeof(int32_t) * ge.size(), cudaMemcpyHostToDevice));
     // per-graph state, reductions, beliefs
     if ((rc = dalloc(&g->d_gs, (size_t)n_graphs)) || (rc = dalloc(&g->d_red_max, (size_t)n_graphs * NSUB)) ||
-        (rc = dalloc(&g->d_red_cnt, (size_t)n_graphs * NSUB)) || (rc = dalloc(&g->d_running, 1)) ||
+        (rc = dalloc(&g->d_red_cnt, (size_t)n_graphs * NSUB)) ||
+        (rc = dalloc(&g->d_red_commit, (size_t)n_graphs * NSUB)) || (rc = dalloc(&g->d_running, 1)) ||
         (rc = dalloc(&g->d_queue, 1)) ||
         (rc = dalloc(&g->d_level, (size_t)std::max(n, 1))) ||
         (rc = dalloc(&g->d_beliefs, (size_t)n * (size_t)k)))
@@ -771,6 +776,8 @@ static int build_run_params(const bp_graph *g, int32_t schedule, double parallel
         return fail(BP_ERR_UNSUPPORTED, "the streamed update (kernel_variant 6) needs FP32, BF16 or Q16 messages "
                                         "and vertices with at most 128 out-edges");
     rp.variant = variant == 3 ? 1 : variant;
+    // RnBP on the streamed update: the update hands the commit its eps test as flag words
+    rp.eps_words = (schedule == BP_RNBP && rp.variant == 6) ? 1 : 0;
     rp.eps_f = float_at_least(eps);
     // shared-table update in vertex tiles: 0 = per-vertex k-state kernel,
     // 1 = tiles on CUDA cores, 2 = tiles on tensor cores, 3 = tensor cores split
@@ -1078,6 +1085,11 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     int32_t variant = 1;
     if ((rc = build_run_params(g, schedule, parallelism, eps, max_rounds, opt, dtype, rp, variant)) != BP_OK)
         return rc;
+    if (rp.eps_words && !g->d_eps_words) {
+        // kept until the handle is destroyed (4 words per warp tile)
+        if ((rc = dalloc(&g->d_eps_words, (size_t)g->n_wtiles * 4)) != BP_OK)
+            return rc;
+    }
     if (rp.record_trace) {
         size_t words = (size_t)rp.trace_capacity * (size_t)rp.trace_words;
         if (words > g->trace_alloc_words) {
@@ -1672,6 +1684,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_gs);
     dfree(g->d_red_max);
     dfree(g->d_red_cnt);
+    dfree(g->d_red_commit);
     dfree(g->d_running);
     dfree(g->d_queue);
     dfree(g->d_tc_tiles);
@@ -1679,6 +1692,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_err);
     dfree(g->d_potcheck);
     dfree(g->d_wtiles);
+    dfree(g->d_eps_words);
     dfree(g->d_trace);
     dfree(g->d_beliefs);
     if (g->h_running)

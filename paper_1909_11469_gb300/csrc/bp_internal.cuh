@@ -96,6 +96,8 @@ struct RunParams {
     int32_t pdl;              // 1: the update, decision and RnBP commit kernels are launched
                               // with programmatic stream serialization
     int32_t dynamic_p;        // 1: RBP / RS frontier fraction switched per round by EdgeRatio
+    int32_t eps_words;        // 1: the streamed update writes the eps flag words (DevRun::eps_words)
+                              // and the RnBP commit reads them instead of the residuals
 };
 
 // eps in the residual type, chosen so that the comparison equals the FP64 test.
@@ -121,6 +123,8 @@ struct DevRun {
     GState *gs;                   // [G]
     unsigned long long *red_max;  // [G*NSUB] double bits
     unsigned int *red_cnt;        // [G*NSUB]
+    unsigned int *red_commit;     // [G*NSUB] RnBP commits of the round per sub-slot, folded into
+                                  // GState::committed by the next decision (null: not used)
     int32_t *n_running;           // [1]
     uint32_t *trace;              // [trace_capacity * trace_words]
     double *beliefs;              // [n*k]
@@ -130,6 +134,8 @@ struct DevRun {
     int32_t *lvl_cnt;             // [LVL_MAX+1] entries of each level list
     const double *graph_p;        // [G] per-graph parallelism, or null: every graph uses rp.low_p
     int32_t *err;                 // [1] set when a bounded device wait runs out
+    uint32_t *eps_words;          // [4 n_wtiles] per warp tile of the streamed update: bit i of
+                                  // word w = message e0 + 32 w + i has residual >= eps
     // grid-wide selection (large graphs; null when unused)
     GSelState *gsel;              // [G]
     unsigned int *gsel_hist;      // [G * 2048]

@@ -234,15 +234,20 @@ __global__ void __launch_bounds__(DECIDE_BLOCK) k_decide(DevGraph g, DevRun dr, 
         st = *stp;
     unsigned long long mb = dr.red_max[(size_t)gg * NSUB + lane];
     unsigned int c = dr.red_cnt[(size_t)gg * NSUB + lane];
+    unsigned int cm = dr.red_commit ? dr.red_commit[(size_t)gg * NSUB + lane] : 0u;
     const double low_p = lane == 0 ? graph_low_p(dr, rp, gg) : 0.0;
     if (__shfl_sync(0xffffffffu, st.status, 0) != ST_RUNNING)
         return;
     dr.red_max[(size_t)gg * NSUB + lane] = 0ull;
     dr.red_cnt[(size_t)gg * NSUB + lane] = 0u;
+    if (dr.red_commit)
+        dr.red_commit[(size_t)gg * NSUB + lane] = 0u;
     mb = warp_max_u64(mb);
     c = warp_sum_u32(c);
+    cm = warp_sum_u32(cm);
     if (lane != 0)
         return;
+    st.committed += (unsigned long long)cm;   // the RnBP commit of the previous round
     const double maxr = __longlong_as_double((long long)mb);
     const int64_t Mg = g.ge_off[gg + 1] - g.ge_off[gg];
     const int64_t ng = g.gv_off[gg + 1] - g.gv_off[gg];
@@ -321,15 +326,17 @@ constexpr int TILE_E = 8 * TILE_V - 8;
 
 // RnBP commit over the warp tiles of the streamed update (single-graph runs
 // of consecutive vertices, <= 128 out-edges): one warp per tile reads the
-// tile record, then together the graph's round state and the residuals of
-// the tile's messages. Each lane takes aligned quads of four consecutive
-// messages of the graph, which share one Philox block (one block per quad
-// instead of one per message), and applies the eps filter; then it issues
-// the loads of all its selected candidates before any store, so a lane keeps
-// up to eight copies in flight. Every warp is independent, so the short
-// dependent chain of one tile (record -> residual and state -> candidate ->
-// store) overlaps with the other resident warps'; the commits of a tile are
-// added with one atomic.
+// tile record, then together the graph's round state and the eps test of the
+// tile's messages: with the streamed update, four flag words per tile that
+// the update wrote with warp ballots (one bit per message, 16 bytes per tile
+// instead of the tile's residuals), else the residuals. Each lane takes
+// aligned quads of four consecutive messages of the graph, which share one
+// Philox block (one block per quad instead of one per message), and applies
+// the eps filter; then it issues the loads of all its selected candidates
+// before any store, so a lane keeps up to eight copies in flight. Every warp
+// is independent, so the short dependent chain of one tile (record -> flags
+// and state -> candidate -> store) overlaps with the other resident warps';
+// the commits of a tile are added with one atomic.
 template <typename S>
 __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun dr, RunParams rp)
 {
@@ -347,15 +354,35 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
     const int ge0 = g.ge_off[gg];
     const int q0 = (e0 - ge0) >> 2, q1 = (e1 - 1 - ge0) >> 2;
     griddep_wait();   // residuals, candidates and round state come from the previous kernels
-    const RT *R = (const RT *)dr.resid;
-    RT r[QPL][4];
+    // eligibility bit (k, j) of this lane: residual >= eps (Eq. 4 against eps),
+    // from the tile's four flag words the streamed update wrote, else from the
+    // residuals themselves
+    unsigned elig = 0;
+    if (rp.eps_words) {
+        const uint4 fw = *reinterpret_cast<const uint4 *>(dr.eps_words + (size_t)t * 4);
+        const unsigned words[4] = {fw.x, fw.y, fw.z, fw.w};
 #pragma unroll
-    for (int k = 0; k < QPL; ++k) {
-        const int q = q0 + lane + 32 * k;
+        for (int k = 0; k < QPL; ++k) {
+            const int q = q0 + lane + 32 * k;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int e = ge0 + 4 * q + j;
-            r[k][j] = (q <= q1 && e >= e0 && e < e1) ? R[e] : (RT)0;
+            for (int j = 0; j < 4; ++j) {
+                const int li = ge0 + 4 * q + j - e0;   // index inside the tile
+                if (q <= q1 && li >= 0 && li < e1 - e0 && ((words[li >> 5] >> (li & 31)) & 1u))
+                    elig |= 1u << (4 * k + j);
+            }
+        }
+    } else {
+        const RT *R = (const RT *)dr.resid;
+        const RT eps = eps_in(rp, (RT)0);
+#pragma unroll
+        for (int k = 0; k < QPL; ++k) {
+            const int q = q0 + lane + 32 * k;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int e = ge0 + 4 * q + j;
+                if (q <= q1 && e >= e0 && e < e1 && R[e] >= eps)
+                    elig |= 1u << (4 * k + j);
+            }
         }
     }
     const GState *sp = dr.gs + gg;
@@ -363,24 +390,20 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
     const uint32_t thr = sp->thr;
     if (status != ST_RUNNING)
         return;
-    const RT eps = eps_in(rp, (RT)0);
     // selection bit (k, j) of this lane
     unsigned pick = 0;
 #pragma unroll
     for (int k = 0; k < QPL; ++k) {
         const int q = q0 + lane + 32 * k;
-        const bool any = r[k][0] >= eps || r[k][1] >= eps || r[k][2] >= eps || r[k][3] >= eps;
-        if (q > q1 || !any)
+        if (!((elig >> (4 * k)) & 15u))
             continue;
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
         if (!always)
             w = rnbp_block(rp, (uint32_t)q, (uint32_t)rounds, (uint32_t)gg);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int e = ge0 + 4 * q + j;
-            if (e >= e0 && e < e1 && r[k][j] >= eps && (always || rnbp_word(w, (uint32_t)j) < thr))
+        for (int j = 0; j < 4; ++j)
+            if (((elig >> (4 * k + j)) & 1u) && (always || rnbp_word(w, (uint32_t)j) < thr))
                 pick |= 1u << (4 * k + j);
-        }
     }
     S *dst = (S *)dr.msg[0];
     const S *src = (const S *)dr.msg[1];
@@ -410,9 +433,11 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
                 atomicOr(&dr.trace[(size_t)(rounds - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
             }
     }
+    // one atomic per tile into one of the graph's sub-slots (a single-graph
+    // run has tens of thousands of tiles: one counter would serialise them)
     const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)__popc(pick));
     if (lane == 0 && c)
-        atomicAdd(&dr.gs[gg].committed, (unsigned long long)c);
+        atomicAdd(&dr.red_commit[(size_t)gg * NSUB + (t & (NSUB - 1))], c);
 }
 
 template <typename S>
@@ -804,6 +829,8 @@ __global__ void k_init_state(DevRun dr, int G)
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G * NSUB; t += gridDim.x * blockDim.x) {
         dr.red_max[t] = 0ull;
         dr.red_cnt[t] = 0u;
+        if (dr.red_commit)
+            dr.red_commit[t] = 0u;
         if (t < G) {
             GState st;
             st.status = ST_RUNNING;
@@ -829,11 +856,20 @@ __global__ void k_init_state(DevRun dr, int G)
     }
 }
 
-// Marks every still-running graph as stopped (wall-clock budget).
+// Marks every still-running graph as stopped (wall-clock budget), folding the
+// commits of its last round into its count.
 __global__ void k_stop_running(DevRun dr, int G)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
         if (dr.gs[t].status == ST_RUNNING) {
+            if (dr.red_commit) {
+                unsigned long long c = 0;
+                for (int q = 0; q < NSUB; ++q) {
+                    c += dr.red_commit[(size_t)t * NSUB + q];
+                    dr.red_commit[(size_t)t * NSUB + q] = 0u;
+                }
+                dr.gs[t].committed += c;
+            }
             dr.gs[t].status = ST_STOPPED;
             atomicSub(dr.n_running, 1);
         }

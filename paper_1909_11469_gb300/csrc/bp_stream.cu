@@ -294,9 +294,11 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
             }
             __syncwarp();
             // 3. out-messages, residuals
+            const size_t wt = ((size_t)blockIdx.x + (size_t)i * gridDim.x) * SW_CONSUMERS + c;   // warp tile
 #pragma unroll
             for (int k = 0; k < EPL; ++k) {
                 const int idx = lane + 32 * k;
+                bool hit = false;
                 if (idx < ne) {
                     const int e = e0 + idx;
                     const A unew = ising_logodds(s_q[idx], s_h[s_src[idx]] - uin[k]);
@@ -306,7 +308,14 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
                     if (MODE == MODE_CAND)
                         R[e] = (RT)r;
                     maxa = r > maxa ? r : maxa;
-                    cnt += (r >= eps_a) ? 1u : 0u;
+                    hit = r >= eps_a;
+                    cnt += hit ? 1u : 0u;
+                }
+                if (MODE == MODE_CAND && rp.eps_words) {
+                    // the eps test of 32 consecutive messages of the tile, for the RnBP commit
+                    const unsigned w = __ballot_sync(0xffffffffu, hit);
+                    if (lane == 0)
+                        dr.eps_words[wt * 4 + k] = w;
                 }
             }
         }
