@@ -359,17 +359,18 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
     // residuals themselves
     unsigned elig = 0;
     if (rp.eps_words) {
-        const uint4 fw = *reinterpret_cast<const uint4 *>(dr.eps_words + (size_t)t * 4);
-        const unsigned words[4] = {fw.x, fw.y, fw.z, fw.w};
+        // the quad's four bits from the tile's words (bits past the tile's
+        // messages are 0; the first quad may start up to 3 messages before it)
+        const uint32_t *fw = dr.eps_words + (size_t)t * 4;
 #pragma unroll
         for (int k = 0; k < QPL; ++k) {
-            const int q = q0 + lane + 32 * k;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int li = ge0 + 4 * q + j - e0;   // index inside the tile
-                if (q <= q1 && li >= 0 && li < e1 - e0 && ((words[li >> 5] >> (li & 31)) & 1u))
-                    elig |= 1u << (4 * k + j);
-            }
+            const int li0 = ge0 + 4 * (q0 + lane + 32 * k) - e0;   // index inside the tile
+            unsigned b4 = 0;
+            if (li0 < 0)
+                b4 = fw[0] << (-li0);
+            else if (li0 < STREAM_WT)
+                b4 = __funnelshift_r(fw[li0 >> 5], (li0 >> 5) < 3 ? fw[(li0 >> 5) + 1] : 0u, li0 & 31);
+            elig |= (b4 & 15u) << (4 * k);
         }
     } else {
         const RT *R = (const RT *)dr.resid;
