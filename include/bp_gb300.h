@@ -133,8 +133,8 @@ typedef struct {
                                  and rejected (BP_ERR_INVALID_ARG) */
     int32_t profile;          /* 1: time every round's phases with CUDA events (default 0) */
     int32_t potts_path;       /* shared-table (BP_PAIR_SHARED) update, FP32/BF16 storage,
-                                 tiles of <= 128 edges: 0 = automatic (3 for k >= 16,
-                                 else the per-vertex k-state kernel), 1 = tiles on the
+                                 k <= 32, tiles of <= 128 edges: 0 = automatic (3 for
+                                 16 <= k <= 32, else the per-vertex k-state kernel), 1 = tiles on the
                                  CUDA cores, 2 = tiles on the tensor cores with BF16
                                  products, 3 = tensor cores with the BF16 residual
                                  products added (close to FP32) */
@@ -214,7 +214,7 @@ typedef struct {
  * (Section II-A), one variable per vertex and one pairwise factor per
  * undirected edge, stored as the adjacency list with edge and vertex ids that
  * Section III-B describes. n_states = k (uniform over vertices,
- * 2 <= k <= 32). row_ptr has n_vars + 1 entries (row_ptr[0] = 0,
+ * 2 <= k <= 128). row_ptr has n_vars + 1 entries (row_ptr[0] = 0,
  * row_ptr[n_vars] = n_dir_edges), col and rev have n_dir_edges entries.
  * The CSR is validated (BP_ERR_BAD_GRAPH) and copied to the device.
  * n_dir_edges must be below 2^31. *out receives the handle.

@@ -369,8 +369,8 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
 {
     if (n < 0 || M < 0 || n_graphs < 1)
         return fail(BP_ERR_INVALID_ARG, "negative size or no graph");
-    if (k < 2 || k > 32)
-        return fail(BP_ERR_UNSUPPORTED, "n_states must be in [2, 32]");
+    if (k < 2 || k > 128)
+        return fail(BP_ERR_UNSUPPORTED, "n_states must be in [2, 128]");
     if (M >= ((int64_t)1 << 31) - 1 || (int64_t)n * k >= ((int64_t)1 << 31))
         return fail(BP_ERR_UNSUPPORTED, "graph too large for 32-bit device indexing");
     if (!row_ptr || (M > 0 && (!col || !rev)))
@@ -430,7 +430,9 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     g->k = k;
     g->M = M;
     g->G = n_graphs;
-    g->kp = k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32));
+    // lanes per vertex of the k-state kernels; above 32 a warp per vertex with
+    // 2 (k <= 64) or 4 (k <= 128) states per lane
+    g->kp = k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 64 ? 64 : 128))));
     g->h_rev.assign(rev, rev + M);
     g->h_col.assign(col, col + M);
     g->h_src = src;
@@ -782,15 +784,15 @@ static int build_run_params(const bp_graph *g, int32_t schedule, double parallel
     // shared-table update in vertex tiles: 0 = per-vertex k-state kernel,
     // 1 = tiles on CUDA cores, 2 = tiles on tensor cores, 3 = tensor cores split
     rp.tc_path = 0;
-    if (g->pair_kind == BP_PAIR_SHARED && g->tc_tiles_ok && (dtype == BP_F32 || dtype == BP_BF16)) {
+    if (g->pair_kind == BP_PAIR_SHARED && g->tc_tiles_ok && g->k <= 32 && (dtype == BP_F32 || dtype == BP_BF16)) {
         if (opt.potts_path >= 1)
             rp.tc_path = opt.potts_path;
         else if (g->k >= 16)
             rp.tc_path = 3;
     }
     if (opt.potts_path >= 1 && rp.tc_path == 0)
-        return fail(BP_ERR_UNSUPPORTED, "the tiled shared-table update needs a shared table, FP32/BF16 "
-                                        "storage and vertices with at most 128 out-edges");
+        return fail(BP_ERR_UNSUPPORTED, "the tiled shared-table update needs a shared table with at most 32 "
+                                        "states, FP32/BF16 storage and vertices with at most 128 out-edges");
     return BP_OK;
 }
 

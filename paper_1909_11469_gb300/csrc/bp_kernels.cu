@@ -955,6 +955,189 @@ __global__ void __launch_bounds__(BLOCK) k_messages_gen(DevGraph g, DevRun dr, d
 }
 
 // --------------------------------------------------------------------------
+// k-state messages with 32 < k <= 32 * SPL (the protein-folding graphs of
+// Section IV-E reach 81 states): one warp per vertex, lane l holds states
+// l, l + 32, ..., l + 32 (SPL - 1); the same Eq. 2 / Eq. 3 / Eq. 4 arithmetic
+// as k_eval_gen, state by state. The shared table (k^2 floats, up to 64 KB)
+// is read through the read-only cache instead of shared memory.
+template <typename S, int SPL, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_eval_wide(DevGraph g, DevRun dr, RunParams rp, int level_L)
+{
+    using A = typename Store<S>::A;
+    using RT = typename ResidT<S>::T;
+    const int k = g.k;
+    constexpr int NPB = BLOCK / 32;
+    const int lane = threadIdx.x & 31;
+    const int first = blockIdx.x * NPB;
+    const int last = min(g.n - 1, first + NPB - 1);
+    const int g0 = g.gid[first];
+    const bool uniform = (g0 == g.gid[last]);
+    const int i = first + (int)threadIdx.x / 32;
+    bool ok[SPL];
+#pragma unroll
+    for (int s = 0; s < SPL; ++s)
+        ok[s] = lane + 32 * s < k;
+    bool valid = false;
+    int gg = g0;
+    A maxa = 0;
+    const A eps_a = eps_in(rp, (A)0);
+    unsigned int cnt = 0;
+    bool act = false;
+    if (i < g.n) {
+        gg = g.gid[i];
+        act = dr.gs[gg].status == ST_RUNNING;
+        if (MODE == MODE_SPLASH)
+            act = act && (dr.level[i] == level_L);
+    }
+    if (act) {   // uniform across the warp
+        valid = (lane == 0);
+        const int cur_idx = dr.gs[gg].cur;
+        const S *cur = (const S *)msg_buf(dr, cur_idx);
+        S *out = (S *)msg_buf(dr, cur_idx ^ 1);
+        const int beg = g.row_ptr[i], end = g.row_ptr[i + 1];
+        A Sx[SPL];
+#pragma unroll
+        for (int s = 0; s < SPL; ++s)
+            Sx[s] = ok[s] ? (A)g.unary[(size_t)i * k + lane + 32 * s] : (A)0;
+        for (int e = beg; e < end; ++e) {
+            const S *in = cur + (size_t)g.rev[e] * k + lane;
+#pragma unroll
+            for (int s = 0; s < SPL; ++s)
+                if (ok[s])
+                    Sx[s] += Store<S>::ld(in + 32 * s, g.qscale);
+        }
+        RT *R = (RT *)dr.resid;
+        for (int e = beg; e < end; ++e) {
+            const S *in = cur + (size_t)g.rev[e] * k + lane;
+            A cav[SPL], a[SPL], acc[SPL];
+            A mloc = (A)(-1e30);
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                const A lin = ok[s] ? Store<S>::ld(in + 32 * s, g.qscale) : (A)0;
+                cav[s] = ok[s] ? Sx[s] - lin : (A)(-1e30);
+                mloc = cav[s] > mloc ? cav[s] : mloc;
+            }
+            const A mx = grp_max<32>(0xffffffffu, mloc);
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                a[s] = ok[s] ? m_exp(cav[s] - mx) : (A)0;
+                acc[s] = 0;
+            }
+            const float *tab = g.pair + (size_t)e * k * k;
+#pragma unroll
+            for (int sx = 0; sx < SPL; ++sx) {
+                for (int src = 0; src < 32; ++src) {
+                    const int x = 32 * sx + src;
+                    if (x >= k)
+                        break;   // uniform across the warp
+                    const A ax = __shfl_sync(0xffffffffu, a[sx], src);
+#pragma unroll
+                    for (int s = 0; s < SPL; ++s) {
+                        if (!ok[s])
+                            continue;
+                        const int y = lane + 32 * s;
+                        const A psi = g.pair_kind == 2 ? (A)__ldg(&g.psi_shared[x * k + y]) : m_exp((A)tab[x * k + y]);
+                        acc[s] += ax * psi;
+                    }
+                }
+            }
+            A part = 0;
+#pragma unroll
+            for (int s = 0; s < SPL; ++s)
+                part += ok[s] ? acc[s] : (A)0;
+            const A z = grp_sum<32>(0xffffffffu, part);
+            A lnew[SPL];
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                lnew[s] = ok[s] ? m_log(m_div(acc[s], z)) : (A)0;
+                lnew[s] = lnew[s] > log_floor<A>() ? lnew[s] : log_floor<A>();
+            }
+            S *o = out + (size_t)e * k + lane;
+            if (MODE == MODE_SPLASH) {
+#pragma unroll
+                for (int s = 0; s < SPL; ++s)
+                    if (ok[s])
+                        Store<S>::st(o + 32 * s, lnew[s], g.qscale);
+                continue;
+            }
+            A rl = 0;
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                if (!ok[s])
+                    continue;
+                const A pn = m_exp(Store<S>::quant(lnew[s], g.qscale));
+                const A po = m_exp(Store<S>::ld(cur + (size_t)e * k + lane + 32 * s, g.qscale));
+                const A d = fabs(pn - po);
+                rl = d > rl ? d : rl;
+            }
+            const A r = grp_max<32>(0xffffffffu, rl);
+#pragma unroll
+            for (int s = 0; s < SPL; ++s)
+                if (ok[s])
+                    Store<S>::st(o + 32 * s, lnew[s], g.qscale);
+            if (MODE == MODE_CAND && lane == 0)
+                R[e] = (RT)r;
+            maxa = r > maxa ? r : maxa;
+            cnt += (r >= eps_a) ? 1u : 0u;
+        }
+    }
+    if (MODE != MODE_SPLASH)
+        reduce_to_graph(dr, uniform, g0, valid, gg, (double)maxa, cnt);
+}
+
+// Beliefs (Eq. 3) and messages in the probability domain for 32 < k <= 32 SPL.
+template <typename S, int SPL>
+__global__ void __launch_bounds__(BLOCK) k_beliefs_wide(DevGraph g, DevRun dr)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (BLOCK / 32) + (int)threadIdx.x / 32;
+    if (i >= g.n)
+        return;
+    const int k = g.k;
+    const S *cur = (const S *)msg_buf(dr, dr.gs[g.gid[i]].cur);
+    double sv[SPL];
+    double mloc = -1e300;
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+        const int x = lane + 32 * s;
+        sv[s] = x < k ? (double)g.unary[(size_t)i * k + x] : -1e300;
+        for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
+            if (x < k)
+                sv[s] += (double)Store<S>::ld(cur + (size_t)g.rev[e] * k + x, g.qscale);
+        mloc = fmax(mloc, sv[s]);
+    }
+    const double mx = grp_max<32>(0xffffffffu, mloc);
+    double w[SPL], part = 0.0;
+#pragma unroll
+    for (int s = 0; s < SPL; ++s) {
+        w[s] = lane + 32 * s < k ? exp(sv[s] - mx) : 0.0;
+        part += w[s];
+    }
+    const double z = grp_sum<32>(0xffffffffu, part);
+#pragma unroll
+    for (int s = 0; s < SPL; ++s)
+        if (lane + 32 * s < k)
+            dr.beliefs[(size_t)i * k + lane + 32 * s] = w[s] / z;
+}
+
+template <typename S, int SPL>
+__global__ void __launch_bounds__(BLOCK) k_messages_wide(DevGraph g, DevRun dr, double *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (BLOCK / 32) + (int)threadIdx.x / 32;
+    if (i >= g.n)
+        return;
+    const int k = g.k;
+    const S *cur = (const S *)msg_buf(dr, dr.gs[g.gid[i]].cur);
+    for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e)
+#pragma unroll
+        for (int s = 0; s < SPL; ++s)
+            if (lane + 32 * s < k)
+                out[(size_t)e * k + lane + 32 * s] =
+                    exp((double)Store<S>::ld(cur + (size_t)e * k + lane + 32 * s, g.qscale));
+}
+
+// --------------------------------------------------------------------------
 // Host-side launchers.
 static inline int blocks_for(int n, int per_block) { return (n + per_block - 1) / per_block; }
 
@@ -1052,7 +1235,22 @@ void launch_eval(int dtype, const DevGraph &g, const DevRun &dr, const RunParams
         return;
     }
     // (k-state messages use one KP-lane group per vertex)
-    if (kp == 4)
+    if (kp > 32) {
+        // 32 < k <= 128: a warp per vertex, 2 or 4 states per lane
+        const int nb = blocks_for(g.n, BLOCK / 32);
+        auto go = [&](auto spl) {
+            constexpr int SPL = decltype(spl)::value;
+            BPG_DISPATCH3(dtype, (mode == MODE_LBP
+                                      ? k_eval_wide<S, SPL, MODE_LBP><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L)
+                                      : mode == MODE_CAND
+                                            ? k_eval_wide<S, SPL, MODE_CAND><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L)
+                                            : k_eval_wide<S, SPL, MODE_SPLASH><<<nb, BLOCK, 0, s>>>(g, dr, rp, level_L)))
+        };
+        if (kp == 64)
+            go(std::integral_constant<int, 2>());
+        else
+            go(std::integral_constant<int, 4>());
+    } else if (kp == 4)
         BPG_DISPATCH3(dtype, (launch_eval_gen<S, 4>(g, dr, rp, mode, level_L, s)))
     else if (kp == 8)
         BPG_DISPATCH3(dtype, (launch_eval_gen<S, 8>(g, dr, rp, mode, level_L, s)))
@@ -1161,7 +1359,11 @@ void launch_beliefs(int dtype, const DevGraph &g, const DevRun &dr, int kp, cuda
         BPG_DISPATCH4(dtype, (k_beliefs_bin<S><<<nb, BLOCK, 0, s>>>(g, dr)));
         return;
     }
-    if (kp == 4)
+    if (kp == 64)
+        BPG_DISPATCH3(dtype, (k_beliefs_wide<S, 2><<<blocks_for(g.n, BLOCK / 32), BLOCK, 0, s>>>(g, dr)))
+    else if (kp > 64)
+        BPG_DISPATCH3(dtype, (k_beliefs_wide<S, 4><<<blocks_for(g.n, BLOCK / 32), BLOCK, 0, s>>>(g, dr)))
+    else if (kp == 4)
         BPG_DISPATCH3(dtype, (k_beliefs_gen<S, 4><<<blocks_for(g.n, BLOCK / 4), BLOCK, 0, s>>>(g, dr)))
     else if (kp == 8)
         BPG_DISPATCH3(dtype, (k_beliefs_gen<S, 8><<<blocks_for(g.n, BLOCK / 8), BLOCK, 0, s>>>(g, dr)))
@@ -1180,7 +1382,11 @@ void launch_messages(int dtype, const DevGraph &g, const DevRun &dr, int kp, dou
         BPG_DISPATCH4(dtype, (k_messages_bin<S><<<nb, BLOCK, 0, s>>>(g, dr, out)));
         return;
     }
-    if (kp == 4)
+    if (kp == 64)
+        BPG_DISPATCH3(dtype, (k_messages_wide<S, 2><<<blocks_for(g.n, BLOCK / 32), BLOCK, 0, s>>>(g, dr, out)))
+    else if (kp > 64)
+        BPG_DISPATCH3(dtype, (k_messages_wide<S, 4><<<blocks_for(g.n, BLOCK / 32), BLOCK, 0, s>>>(g, dr, out)))
+    else if (kp == 4)
         BPG_DISPATCH3(dtype, (k_messages_gen<S, 4><<<blocks_for(g.n, BLOCK / 4), BLOCK, 0, s>>>(g, dr, out)))
     else if (kp == 8)
         BPG_DISPATCH3(dtype, (k_messages_gen<S, 8><<<blocks_for(g.n, BLOCK / 8), BLOCK, 0, s>>>(g, dr, out)))

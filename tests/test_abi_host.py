@@ -102,7 +102,7 @@ def test_invalid_graphs_rejected_on_host(L):
     # self-loop: 2 vertices, edge 0->0 with rev = itself
     _expect(bp.BP_ERR_BAD_GRAPH, lambda: bp.bp_create_graph(
         2, 2, np.array([0, 1, 1]), np.array([0], np.int32), np.array([0], np.int32)))
-    _expect(bp.BP_ERR_UNSUPPORTED, lambda: bp.bp_create_graph(p.n, 33, rp, col, rev))
+    _expect(bp.BP_ERR_UNSUPPORTED, lambda: bp.bp_create_graph(p.n, 129, rp, col, rev))
     _expect(bp.BP_ERR_UNSUPPORTED, lambda: bp.bp_create_graph(p.n, 1, rp, col, rev))
     # a batch whose edge crosses from graph 0 into graph 1
     _expect(bp.BP_ERR_BAD_GRAPH, lambda: bp.bp_create_batch(

@@ -564,6 +564,53 @@ def test_variable_states_tree_exact(dtype, tol):
     assert np.abs(res["beliefs"] - _exact.brute_force_marginals(prob)).max() < tol
 
 
+@pytest.mark.parametrize("sched,par", [("lbp", 1.0), ("rnbp", 0.4)])
+def test_wide_states_fp64_exact_replay(sched, par):
+    """Up to 81 states per vertex (the protein-folding range of Section IV-E;
+    the layout has 81 states, a warp per vertex with 3 states per lane): FP64
+    messages replay the oracle's frontiers, rounds and beliefs; absent states
+    get no belief."""
+    prob = synth.protein_like(60, seed=4, k_min=2, k_max=81)
+    assert prob.k == 81
+    T = 30
+    ref = oracle.run(prob, sched, parallelism=par, high_p=0.9, eps=1e-4, max_rounds=T, seed=2, trace_cap=T)
+    res = gpu_run(prob, sched, par, 1e-4, T, "f64", trace=T, seed=2, high_p=0.9)
+    assert res["stats"]["rounds"] == ref["rounds"]
+    if sched != "lbp":
+        assert np.array_equal(res["trace"], ref["trace"][:ref["rounds"]])
+    assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F64
+    absent = np.isinf(prob.unary_log.reshape(prob.n, prob.k))
+    assert np.all(res["beliefs"][absent] == 0)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", TOL_F32), ("bf16", 1.6e-2)])
+@pytest.mark.parametrize("sched,par", [("rnbp", 0.4), ("rs", 0.2)])
+def test_wide_states_trace_follow(dtype, tol, sched, par):
+    """81 states per vertex at most, FP32 / BF16 storage, RnBP and Residual
+    Splash (the k-state splash runs the same kernel per level), against the
+    oracle following the GPU frontiers."""
+    prob = synth.protein_like(120, seed=5, k_min=2, k_max=81)
+    res = gpu_run(prob, sched, par, 1e-4, 25, dtype, trace=25, seed=1, high_p=0.9)
+    ref = follow(prob, sched, res, 1e-4, "bf16" if dtype == "bf16" else "f64")
+    assert np.abs(res["beliefs"] - ref["beliefs"]).max() < tol
+
+
+@pytest.mark.parametrize("k", [40, 128])
+def test_wide_shared_table(k):
+    """A shared k x k table with k > 32 (no tensor-core tiles: the warp-per-
+    vertex kernel reads the table through the read-only cache): FP32 LBP on a
+    grid against the oracle for the same rounds."""
+    prob = synth.potts_grid(8, k, seed=3)
+    res = gpu_run(prob, "lbp", 1.0, 1e-4, 15, "f32")
+    ref = oracle.run(prob, "lbp", eps=1e-4, trace_in=all_ones_trace(prob.m, res["stats"]["rounds"]),
+                     trace_rounds=res["stats"]["rounds"])
+    assert np.abs(res["beliefs"] - ref["beliefs"]).max() < TOL_F32
+    with bp.Graph(prob) as g:
+        with pytest.raises(bp.BPError) as ei:
+            g.run("lbp", 1.0, max_rounds=2, potts_path=3)
+        assert ei.value.code == bp.BP_ERR_UNSUPPORTED
+
+
 def test_absent_states_need_tables():
     prob = synth.potts_grid(4, 5, seed=0)
     un = prob.unary_log.copy()
