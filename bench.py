@@ -82,7 +82,7 @@ MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
 # residual stored: 2/3 of the step's update launches); an LBP launch moves 4 B
 # per message less.
 NCU_SWEEP_TRAFFIC = {}
-NCU_UPDATE_TRAFFIC = {("er4096_b3", "f32", 6): 254.413312e6 + 107.854080e6}
+NCU_UPDATE_TRAFFIC = {("er4096_b3", "f32", 6): 254.175744e6 + 109.242880e6}
 BYTES_PER_VERTEX = 12
 
 
