@@ -325,46 +325,50 @@ constexpr int TILE_V = 256;
 constexpr int TILE_E = 8 * TILE_V - 8;
 
 // RnBP commit over the warp tiles of the streamed update (single-graph runs
-// of consecutive vertices, <= 128 out-edges): one warp per tile reads the
-// tile record, then together the graph's round state and the eps test of the
-// tile's messages: with the streamed update, four flag words per tile that
-// the update wrote with warp ballots (one bit per message, 16 bytes per tile
-// instead of the tile's residuals), else the residuals. Each lane takes
-// aligned quads of four consecutive messages of the graph, which share one
-// Philox block (one block per quad instead of one per message), and applies
-// the eps filter; then it issues the loads of all its selected candidates
-// before any store, so a lane keeps up to eight copies in flight. Every warp
-// is independent, so the short dependent chain of one tile (record -> flags
-// and state -> candidate -> store) overlaps with the other resident warps';
-// the commits of a tile are added with one atomic.
+// of consecutive vertices, <= 128 out-edges): one half warp per tile (a warp
+// carries two tiles' loads in flight: the kernel is bound by the latency of
+// its short dependent chain) reads the tile record, then together the graph's
+// round state and the eps test of the tile's messages: with the streamed
+// update, four flag words per tile that the update wrote with warp ballots
+// (one bit per message, 16 bytes per tile instead of the tile's residuals),
+// else the residuals. Each lane takes aligned quads of four consecutive
+// messages of the graph, which share one Philox block (one block per quad
+// instead of one per message), and applies the eps filter; then it issues the
+// loads of all its selected candidates before any store. The chain of a tile
+// (record -> flags and state -> candidate -> store) overlaps with the other
+// resident warps'; the commits of a tile are added with one atomic.
 template <typename S>
 __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun dr, RunParams rp)
 {
     griddep_launch_dependents();
     using RT = typename ResidT<S>::T;
-    constexpr int QPL = 2;   // quads per lane: a tile of <= 128 edges meets <= 34 quads
-    const int lane = threadIdx.x & 31;
-    const int t = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (t >= g.n_wtiles)
-        return;
-    const int4 rec = g.wtiles[t];
-    const int e0 = rec.y, e1 = g.wtiles[t + 1].y, gg = rec.z;
-    if (e1 == e0)
-        return;
-    const int ge0 = g.ge_off[gg];
-    const int q0 = (e0 - ge0) >> 2, q1 = (e1 - 1 - ge0) >> 2;
-    griddep_wait();   // residuals, candidates and round state come from the previous kernels
+    constexpr int QPL = 3;   // quads per lane: a half warp per tile, a tile of <= 128 edges meets <= 34 quads
+    const int lane = threadIdx.x & 31, hl = lane & 15;
+    const unsigned hmask = lane < 16 ? 0x0000ffffu : 0xffff0000u;
+    const int t = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4);   // this half warp's tile
+    bool act = t < g.n_wtiles;
+    int e0 = 0, e1 = 0, gg = 0;
+    if (act) {
+        const int4 rec = g.wtiles[t];
+        e0 = rec.y;
+        e1 = g.wtiles[t + 1].y;
+        gg = rec.z;
+        act = e1 > e0;
+    }
+    const int ge0 = act ? g.ge_off[gg] : 0;
+    const int q0 = (e0 - ge0) >> 2, q1 = act ? (e1 - 1 - ge0) >> 2 : -1;
+    griddep_wait();   // flags or residuals, candidates and round state come from the previous kernels
     // eligibility bit (k, j) of this lane: residual >= eps (Eq. 4 against eps),
     // from the tile's four flag words the streamed update wrote, else from the
     // residuals themselves
     unsigned elig = 0;
-    if (rp.eps_words) {
+    if (act && rp.eps_words) {
         // the quad's four bits from the tile's words (bits past the tile's
         // messages are 0; the first quad may start up to 3 messages before it)
         const uint32_t *fw = dr.eps_words + (size_t)t * 4;
 #pragma unroll
         for (int k = 0; k < QPL; ++k) {
-            const int li0 = ge0 + 4 * (q0 + lane + 32 * k) - e0;   // index inside the tile
+            const int li0 = ge0 + 4 * (q0 + hl + 16 * k) - e0;   // index inside the tile
             unsigned b4 = 0;
             if (li0 < 0)
                 b4 = fw[0] << (-li0);
@@ -372,12 +376,12 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
                 b4 = __funnelshift_r(fw[li0 >> 5], (li0 >> 5) < 3 ? fw[(li0 >> 5) + 1] : 0u, li0 & 31);
             elig |= (b4 & 15u) << (4 * k);
         }
-    } else {
+    } else if (act) {
         const RT *R = (const RT *)dr.resid;
         const RT eps = eps_in(rp, (RT)0);
 #pragma unroll
         for (int k = 0; k < QPL; ++k) {
-            const int q = q0 + lane + 32 * k;
+            const int q = q0 + hl + 16 * k;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int e = ge0 + 4 * q + j;
@@ -386,26 +390,33 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
             }
         }
     }
-    const GState *sp = dr.gs + gg;
-    const int status = sp->status, rounds = sp->rounds, always = sp->always;
-    const uint32_t thr = sp->thr;
-    if (status != ST_RUNNING)
-        return;
-    // selection bit (k, j) of this lane
-    unsigned pick = 0;
+    int rounds = 0;
+    if (act) {
+        const GState *sp = dr.gs + gg;
+        const int status = sp->status, always = sp->always;
+        const uint32_t thr = sp->thr;
+        rounds = sp->rounds;
+        act = status == ST_RUNNING;
+        if (!act)
+            elig = 0;
+        // selection bit (k, j) of this lane
+        unsigned pick = 0;
 #pragma unroll
-    for (int k = 0; k < QPL; ++k) {
-        const int q = q0 + lane + 32 * k;
-        if (!((elig >> (4 * k)) & 15u))
-            continue;
-        uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        if (!always)
-            w = rnbp_block(rp, (uint32_t)q, (uint32_t)rounds, (uint32_t)gg);
+        for (int k = 0; k < QPL; ++k) {
+            const int q = q0 + hl + 16 * k;
+            if (!((elig >> (4 * k)) & 15u))
+                continue;
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (!always)
+                w = rnbp_block(rp, (uint32_t)q, (uint32_t)rounds, (uint32_t)gg);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (((elig >> (4 * k + j)) & 1u) && (always || rnbp_word(w, (uint32_t)j) < thr))
-                pick |= 1u << (4 * k + j);
+            for (int j = 0; j < 4; ++j)
+                if (((elig >> (4 * k + j)) & 1u) && (always || rnbp_word(w, (uint32_t)j) < thr))
+                    pick |= 1u << (4 * k + j);
+        }
+        elig = pick;
     }
+    const unsigned pick = elig;
     S *dst = (S *)dr.msg[0];
     const S *src = (const S *)dr.msg[1];
     const int epm = g.epm;
@@ -414,15 +425,15 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
 #pragma unroll
         for (int b = 0; b < QPL * 4; ++b)
             if (pick >> b & 1u)
-                v[b] = src[ge0 + 4 * (q0 + lane + 32 * (b >> 2)) + (b & 3)];
+                v[b] = src[ge0 + 4 * (q0 + hl + 16 * (b >> 2)) + (b & 3)];
 #pragma unroll
         for (int b = 0; b < QPL * 4; ++b)
             if (pick >> b & 1u)
-                dst[ge0 + 4 * (q0 + lane + 32 * (b >> 2)) + (b & 3)] = v[b];
+                dst[ge0 + 4 * (q0 + hl + 16 * (b >> 2)) + (b & 3)] = v[b];
     } else {
         for (int b = 0; b < QPL * 4; ++b)
             if (pick >> b & 1u) {
-                const size_t e = (size_t)(ge0 + 4 * (q0 + lane + 32 * (b >> 2)) + (b & 3));
+                const size_t e = (size_t)(ge0 + 4 * (q0 + hl + 16 * (b >> 2)) + (b & 3));
                 for (int x = 0; x < epm; ++x)
                     dst[e * epm + x] = src[e * epm + x];
             }
@@ -430,14 +441,14 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
     if (rp.record_trace && rounds <= rp.trace_capacity) {
         for (int b = 0; b < QPL * 4; ++b)
             if (pick >> b & 1u) {
-                const int e = ge0 + 4 * (q0 + lane + 32 * (b >> 2)) + (b & 3);
+                const int e = ge0 + 4 * (q0 + hl + 16 * (b >> 2)) + (b & 3);
                 atomicOr(&dr.trace[(size_t)(rounds - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
             }
     }
     // one atomic per tile into one of the graph's sub-slots (a single-graph
     // run has tens of thousands of tiles: one counter would serialise them)
-    const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)__popc(pick));
-    if (lane == 0 && c)
+    const unsigned c = __reduce_add_sync(hmask, (unsigned)__popc(pick));
+    if (hl == 0 && c)
         atomicAdd(&dr.red_commit[(size_t)gg * NSUB + (t & (NSUB - 1))], c);
 }
 
@@ -1282,8 +1293,8 @@ void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const Ru
     if (g.n == 0)
         return;
     if (g.n_wtiles > 0) {
-        // one warp per warp tile
-        BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_wt<S>, blocks_for(g.n_wtiles, BLOCK / 32), BLOCK, s,
+        // one half warp per warp tile
+        BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_wt<S>, blocks_for(g.n_wtiles, BLOCK / 16), BLOCK, s,
                                        g, dr, rp)));
         return;
     }
