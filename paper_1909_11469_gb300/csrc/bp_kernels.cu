@@ -325,9 +325,9 @@ constexpr int TILE_V = 256;
 constexpr int TILE_E = 8 * TILE_V - 8;
 
 // RnBP commit over the warp tiles of the streamed update (single-graph runs
-// of consecutive vertices, <= 128 out-edges): one half warp per tile (a warp
-// carries two tiles' loads in flight: the kernel is bound by the latency of
-// its short dependent chain) reads the tile record, then together the graph's
+// of consecutive vertices, <= 128 out-edges): eight lanes per tile (a warp
+// carries four tiles' loads in flight: the kernel is bound by the latency of
+// its short dependent chain) read the tile record, then together the graph's
 // round state and the eps test of the tile's messages: with the streamed
 // update, four flag words per tile that the update wrote with warp ballots
 // (one bit per message, 16 bytes per tile instead of the tile's residuals),
@@ -337,15 +337,22 @@ constexpr int TILE_E = 8 * TILE_V - 8;
 // loads of all its selected candidates before any store. The chain of a tile
 // (record -> flags and state -> candidate -> store) overlaps with the other
 // resident warps'; the commits of a tile are added with one atomic.
+// lanes per tile of the warp-tile commit: 8 (four tiles' loads in flight per
+// warp) measured 43 us per launch on the 4096-graph ER batch, 16 lanes 48 us,
+// a warp per tile 58 us
+constexpr int COMMIT_LPT = 8;
+
 template <typename S>
 __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun dr, RunParams rp)
 {
     griddep_launch_dependents();
     using RT = typename ResidT<S>::T;
-    constexpr int QPL = 3;   // quads per lane: a half warp per tile, a tile of <= 128 edges meets <= 34 quads
-    const int lane = threadIdx.x & 31, hl = lane & 15;
-    const unsigned hmask = lane < 16 ? 0x0000ffffu : 0xffff0000u;
-    const int t = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4);   // this half warp's tile
+    constexpr int LPT = COMMIT_LPT;             // lanes per tile
+    constexpr int QPL = (34 + LPT - 1) / LPT;   // quads per lane: a tile of <= 128 edges meets <= 34 quads
+    static_assert(QPL * 4 <= 32, "a lane's eligibility and pick bits fit one word");
+    const int lane = threadIdx.x & 31, hl = lane % LPT;
+    const unsigned hmask = (LPT == 32 ? 0xffffffffu : ((1u << LPT) - 1u)) << (lane - hl);
+    const int t = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) / LPT);   // this lane group's tile
     bool act = t < g.n_wtiles;
     int e0 = 0, e1 = 0, gg = 0;
     if (act) {
@@ -368,7 +375,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
         const uint32_t *fw = dr.eps_words + (size_t)t * 4;
 #pragma unroll
         for (int k = 0; k < QPL; ++k) {
-            const int li0 = ge0 + 4 * (q0 + hl + 16 * k) - e0;   // index inside the tile
+            const int li0 = ge0 + 4 * (q0 + hl + LPT * k) - e0;   // index inside the tile
             unsigned b4 = 0;
             if (li0 < 0)
                 b4 = fw[0] << (-li0);
@@ -381,7 +388,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
         const RT eps = eps_in(rp, (RT)0);
 #pragma unroll
         for (int k = 0; k < QPL; ++k) {
-            const int q = q0 + hl + 16 * k;
+            const int q = q0 + hl + LPT * k;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int e = ge0 + 4 * q + j;
@@ -403,7 +410,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
         unsigned pick = 0;
 #pragma unroll
         for (int k = 0; k < QPL; ++k) {
-            const int q = q0 + hl + 16 * k;
+            const int q = q0 + hl + LPT * k;
             if (!((elig >> (4 * k)) & 15u))
                 continue;
             uint4 w = make_uint4(0u, 0u, 0u, 0u);
@@ -425,15 +432,15 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
 #pragma unroll
         for (int b = 0; b < QPL * 4; ++b)
             if (pick >> b & 1u)
-                v[b] = src[ge0 + 4 * (q0 + hl + 16 * (b >> 2)) + (b & 3)];
+                v[b] = src[ge0 + 4 * (q0 + hl + LPT * (b >> 2)) + (b & 3)];
 #pragma unroll
         for (int b = 0; b < QPL * 4; ++b)
             if (pick >> b & 1u)
-                dst[ge0 + 4 * (q0 + hl + 16 * (b >> 2)) + (b & 3)] = v[b];
+                dst[ge0 + 4 * (q0 + hl + LPT * (b >> 2)) + (b & 3)] = v[b];
     } else {
         for (int b = 0; b < QPL * 4; ++b)
             if (pick >> b & 1u) {
-                const size_t e = (size_t)(ge0 + 4 * (q0 + hl + 16 * (b >> 2)) + (b & 3));
+                const size_t e = (size_t)(ge0 + 4 * (q0 + hl + LPT * (b >> 2)) + (b & 3));
                 for (int x = 0; x < epm; ++x)
                     dst[e * epm + x] = src[e * epm + x];
             }
@@ -441,7 +448,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun 
     if (rp.record_trace && rounds <= rp.trace_capacity) {
         for (int b = 0; b < QPL * 4; ++b)
             if (pick >> b & 1u) {
-                const int e = ge0 + 4 * (q0 + hl + 16 * (b >> 2)) + (b & 3);
+                const int e = ge0 + 4 * (q0 + hl + LPT * (b >> 2)) + (b & 3);
                 atomicOr(&dr.trace[(size_t)(rounds - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
             }
     }
@@ -1293,8 +1300,8 @@ void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const Ru
     if (g.n == 0)
         return;
     if (g.n_wtiles > 0) {
-        // one half warp per warp tile
-        BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_wt<S>, blocks_for(g.n_wtiles, BLOCK / 16), BLOCK, s,
+        // eight lanes per warp tile
+        BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_wt<S>, blocks_for(g.n_wtiles, BLOCK / COMMIT_LPT), BLOCK, s,
                                        g, dr, rp)));
         return;
     }
