@@ -70,29 +70,30 @@ DEFAULT_WORKLOAD = "er4096_b3"
 L2_FLUSH_BYTES = 512 << 20          # > 126 MB of L2
 # Algorithmic bytes of the full-evaluation kernel (binary Ising): per evaluated
 # message rev (4), incoming message (s), exp(-2 beta) (4), old message (s), new
-# message (s), + residual (4) in the frontier modes; per processed vertex
-# row_ptr, unary log-odds and graph id (12). s = 4 (FP32) or 2 (BF16, Q16).
+# message (s), + residual (4) in the frontier modes, + the second outcome (s)
+# of the fused RnBP rounds; per processed vertex row_ptr, unary log-odds and
+# graph id (12). s = 4 (FP32) or 2 (BF16, Q16).
 MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # roofline kernel from one ncu capture on the workload, valid only while the
 # kernel is unchanged since the capture (the summaries and commands are in
 # profiles/). Captures are cold (ncu flushes the caches), so they bound the warm
 # traffic from above. Keys: (workload, storage, update mapping) and (workload,
-# storage, sweep form). The 4096-graph ER capture is of an RnBP launch (the
-# residual stored: 2/3 of the step's update launches); an LBP launch moves 4 B
-# per message less.
+# storage, sweep form).
 NCU_SWEEP_TRAFFIC = {}
-NCU_UPDATE_TRAFFIC = {("er4096_b3", "f32", 6): 254.175744e6 + 109.242880e6}
+NCU_UPDATE_TRAFFIC = {}
 BYTES_PER_VERTEX = 12
 
 
-def bytes_per_msg(sched: str, dtype: str, k: int = 2) -> int:
+def bytes_per_msg(sched: str, dtype: str, k: int = 2, fused: bool = False) -> int:
     """Per evaluated message: rev, incoming message, old message, new message
     (k values each for k-state messages, one log-odds for binary ones), the
-    Ising exp(-2 beta) (binary only), + the residual in the frontier modes."""
+    Ising exp(-2 beta) (binary only), + the residual in the frontier modes;
+    fused RnBP rounds (commit inside the streamed update) write a second
+    outcome of s bytes."""
     s = MSG_BYTES[dtype]
     if k == 2:
-        return 8 + 3 * s + (0 if sched == "lbp" else (8 if dtype == "f64" else 4))
+        return 8 + 3 * s + (0 if sched == "lbp" else (8 if dtype == "f64" else 4)) + (s if fused else 0)
     return 4 + 3 * k * s + (0 if sched == "lbp" else 4)
 
 
@@ -133,7 +134,9 @@ def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kern
     alg_bytes, eval_ms, eval_launches = 0.0, 0.0, 0
     phase = {"eval_ms": 0.0, "decide_ms": 0.0, "frontier_ms": 0.0}
     for sched, p, st, pr, gst in step:
-        alg_bytes += bytes_per_msg(sched, dtype, k) * pr["full_evals"] + bytes_per_vertex(k) * pr["active_vertices"]
+        fused = bool(pr.get("fused_commit", 0))
+        alg_bytes += (bytes_per_msg(sched, dtype, k, fused) * pr["full_evals"]
+                      + bytes_per_vertex(k) * pr["active_vertices"])
         eval_ms += pr["eval_ms"]
         eval_launches += pr["eval_launches"]
         for key in phase:
@@ -155,7 +158,8 @@ def eval_roofline(step, dtype: str, peak: float, peak_src: str, k: int = 2, kern
             if sched not in isolated or pr["eval_launches"] == 0:
                 continue
             w = pr["eval_launches"]
-            b_tot += w * (bytes_per_msg(sched, dtype, k) * m + bytes_per_vertex(k) * n)
+            fused = bool(pr.get("fused_commit", 0))
+            b_tot += w * (bytes_per_msg(sched, dtype, k, fused) * m + bytes_per_vertex(k) * n)
             t_tot += w * isolated[sched]
             w_tot += w
         if t_tot > 0:

@@ -190,6 +190,9 @@ typedef struct {
     int32_t sweep_ctas;        /* always 0 (the RS sweeps run one launch per sub-step) */
     int32_t sweep_form;        /* always 0: RS sweeps as per-sub-step launches */
     int32_t overlap_launches;  /* 1 when the run used programmatic dependent launches */
+    int32_t fused_commit;      /* 1 when the RnBP rounds committed inside the streamed update
+                                  (kernel_variant 6 without a recorded trace: both EdgeRatio
+                                  outcomes written, no commit kernel; always filled) */
 } bp_profile;
 
 /* Fills *opt with the defaults listed above. */

@@ -38,10 +38,11 @@
  *   test, select, commit simultaneously (Jacobi); rounds = committing rounds;
  *   RBP/RS ties broken by smaller id; RBP k = clamp(ceil(p*M), 1, M); RS roots
  *   = clamp(ceil(p*M), 1, n) (or ceil(p*n) in the alternative mode); RnBP draws
- *   one Philox4x32-10 word per message -- word e mod 4 of the block with key
- *   seed and counter (floor(e / 4), round, graph, 0) -- and selects iff the
- *   word is below floor(p * 2^32); EdgeRatio uses this round's and last round's
- *   unconverged counts, round 1 uses HighP.
+ *   one 16-bit uniform per message -- half e mod 2 (0: low, 1: high) of word
+ *   (e mod 8) / 2 of the Philox4x32-10 block with key seed and counter
+ *   (floor(e / 8), round, graph, 0) -- and selects iff it is below
+ *   floor(p * 2^16); EdgeRatio uses this round's and last round's unconverged
+ *   counts, round 1 uses HighP.
  */
 #include <math.h>
 #include <stdint.h>
@@ -130,15 +131,17 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
 }
 
 /* RnBP random filter draw for message e in round t of graph g: one Philox
- * block per four consecutive messages, counter (floor(e / 4), t, g, 0); message
- * e takes word e mod 4. */
+ * block per eight consecutive messages, counter (floor(e / 8), t, g, 0);
+ * message e takes the 16-bit half e mod 2 (0: low, 1: high) of word
+ * (e mod 8) / 2, a uniform integer in [0, 2^16). */
 static uint32_t rnbp_draw(uint64_t seed, uint32_t e, uint32_t t, uint32_t g)
 {
-    uint32_t ctr[4] = {e >> 2, t, g, 0u};
+    uint32_t ctr[4] = {e / 8u, t, g, 0u};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t out[4];
     orc_philox4x32_10(ctr, key, out);
-    return out[e & 3u];
+    uint32_t word = out[(e % 8u) / 2u];
+    return (e % 2u == 0u) ? (word & 0xffffu) : (word >> 16);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -603,7 +606,7 @@ int orc_run(const orc_problem *pb, const orc_params *pr, double *beliefs_out,
             } else { /* RnBP */
                 double p = p_round;
                 int always = (p >= 1.0);
-                uint64_t thr = (p <= 0.0) ? 0u : (uint64_t)(p * 4294967296.0);
+                uint64_t thr = (p <= 0.0) ? 0u : (uint64_t)(p * 65536.0);
                 for (int64_t e = 0; e < m; ++e) {
                     chosen[e] = 0;
                     if (r[e] >= pr->eps) {                      /* eps filter */

@@ -68,7 +68,8 @@ class bp_profile(ctypes.Structure):
                 ("select_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double),
                 ("sweep_launches", ctypes.c_int64), ("select_ctas", ctypes.c_int32 * 2),
                 ("kernel_variant", ctypes.c_int32), ("sweep_ctas", ctypes.c_int32),
-                ("sweep_form", ctypes.c_int32), ("overlap_launches", ctypes.c_int32)]
+                ("sweep_form", ctypes.c_int32), ("overlap_launches", ctypes.c_int32),
+                ("fused_commit", ctypes.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -112,7 +112,7 @@ struct bp_graph {
     // run buffers
     int buf_dtype = -1;
     int buf_epm = 0;
-    void *d_msg[2] = {nullptr, nullptr};
+    void *d_msg[3] = {nullptr, nullptr, nullptr};   // the third: fused RnBP rounds (lazy)
     void *d_resid = nullptr, *d_vres = nullptr;
     int8_t *d_level = nullptr;
     int2 *d_lvl_list = nullptr;                 // Residual Splash level lists (lazy)
@@ -124,6 +124,7 @@ struct bp_graph {
     unsigned long long *d_red_max = nullptr;
     unsigned int *d_red_cnt = nullptr;
     unsigned int *d_red_commit = nullptr;
+    unsigned int *d_red_commit_lo = nullptr;
     int32_t *d_running = nullptr;
     int32_t *d_queue = nullptr;
     int32_t max_graph_vertices = 0;
@@ -146,6 +147,7 @@ struct bp_graph {
     // warp tiles of the streamed update (mapping 6), n_wtiles + 1 records; 0
     // tiles when a vertex has more than STREAM_WT out-edges
     int4 *d_wtiles = nullptr;
+    int4 *d_ctiles = nullptr;  // commit records of the warp tiles {e0, e1, graph, graph's e0}
     uint32_t *d_eps_words = nullptr;   // RnBP eps flag words, 4 per warp tile (lazy)
     int32_t n_wtiles = 0;
     bool wtiles_ok = false;
@@ -181,6 +183,7 @@ void free_run_buffers(bp_graph *g)
     clear_cache(g);
     dfree(g->d_msg[0]);
     dfree(g->d_msg[1]);
+    dfree(g->d_msg[2]);
     dfree(g->d_resid);
     dfree(g->d_vres);
     g->buf_dtype = -1;
@@ -284,6 +287,7 @@ DevGraph dev_graph(const bp_graph *g, int dtype)
     d.psi_shared = g->d_psi_shared;
     d.kpresent = g->d_kpresent;
     d.wtiles = g->d_wtiles;
+    d.ctiles = g->d_ctiles;
     d.n_wtiles = g->n_wtiles;
     return d;
 }
@@ -293,6 +297,7 @@ DevRun dev_run(const bp_graph *g)
     DevRun r;
     r.msg[0] = g->d_msg[0];
     r.msg[1] = g->d_msg[1];
+    r.msg[2] = g->d_msg[2];
     r.resid = g->d_resid;
     r.vres = g->d_vres;
     r.level = g->d_level;
@@ -300,6 +305,7 @@ DevRun dev_run(const bp_graph *g)
     r.red_max = g->d_red_max;
     r.red_cnt = g->d_red_cnt;
     r.red_commit = g->d_red_commit;
+    r.red_commit_lo = g->d_red_commit_lo;
     r.n_running = g->d_running;
     r.trace = g->d_trace;
     r.beliefs = g->d_beliefs;
@@ -468,7 +474,8 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
     // per-graph state, reductions, beliefs
     if ((rc = dalloc(&g->d_gs, (size_t)n_graphs)) || (rc = dalloc(&g->d_red_max, (size_t)n_graphs * NSUB)) ||
         (rc = dalloc(&g->d_red_cnt, (size_t)n_graphs * NSUB)) ||
-        (rc = dalloc(&g->d_red_commit, (size_t)n_graphs * NSUB)) || (rc = dalloc(&g->d_running, 1)) ||
+        (rc = dalloc(&g->d_red_commit, (size_t)n_graphs * NSUB)) ||
+        (rc = dalloc(&g->d_red_commit_lo, (size_t)n_graphs * NSUB)) || (rc = dalloc(&g->d_running, 1)) ||
         (rc = dalloc(&g->d_queue, 1)) ||
         (rc = dalloc(&g->d_level, (size_t)std::max(n, 1))) ||
         (rc = dalloc(&g->d_beliefs, (size_t)n * (size_t)k)))
@@ -557,6 +564,14 @@ int validate_and_upload(bp_graph *g, int32_t n_graphs, const int64_t *gvo, int32
         if ((rc = dalloc(&g->d_wtiles, rec.size())))
             return rc;
         BP_CK(cudaMemcpy(g->d_wtiles, rec.data(), sizeof(int4) * rec.size(), cudaMemcpyHostToDevice));
+        std::vector<int4> crec;
+        for (size_t t = 0; t + 1 < rec.size(); ++t)
+            crec.push_back(make_int4(rec[t].y, rec[t + 1].y, rec[t].z, ge[(size_t)rec[t].z]));
+        if (!crec.empty()) {
+            if ((rc = dalloc(&g->d_ctiles, crec.size())))
+                return rc;
+            BP_CK(cudaMemcpy(g->d_ctiles, crec.data(), sizeof(int4) * crec.size(), cudaMemcpyHostToDevice));
+        }
     }
     BP_CK(cudaMallocHost((void **)&g->h_running, sizeof(int32_t)));
     BP_CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
@@ -587,6 +602,13 @@ int create_common(int32_t n_graphs, const int64_t *gvo, int32_t n, int32_t k, in
     return BP_OK;
 }
 
+// Update mode of a round: LBP, RnBP with the commit inside the streamed
+// update, or candidates and residuals.
+int eval_mode(const RunParams &rp)
+{
+    return rp.schedule == SCHED_LBP ? MODE_LBP : (rp.fused_rnbp ? MODE_RNBP_FUSED : MODE_CAND);
+}
+
 // Records one round (evaluation, decision, frontier work) on stream s and
 // returns the number of kernels it launched. ev (nullable) receives 5 events:
 // round start, after evaluation, after decision, after selection (and splash
@@ -598,7 +620,7 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
     int64_t kernels = 0;
     if (ev)
         cudaEventRecord(ev[0], s);
-    const int emode = rp.schedule == SCHED_LBP ? MODE_LBP : MODE_CAND;
+    const int emode = eval_mode(rp);
     if (rp.tc_path)
         launch_potts_tc(dtype, dg, dr, rp, emode, g->d_tc_tiles, g->d_tc_rec, g->n_tc_tiles, rp.tc_path, g->d_err,
                         s);
@@ -615,8 +637,10 @@ int64_t record_round(bp_graph *g, int dtype, const DevGraph &dg, const DevRun &d
     case SCHED_LBP:
         break;
     case SCHED_RNBP:
-        launch_commit_rnbp(dtype, dg, dr, rp, s);
-        kernels += any;
+        if (!rp.fused_rnbp) {
+            launch_commit_rnbp(dtype, dg, dr, rp, s);
+            kernels += any;
+        }
         break;
     case SCHED_RBP:
         launch_select_rbp(dtype, dg, dr, rp, s);
@@ -778,8 +802,12 @@ static int build_run_params(const bp_graph *g, int32_t schedule, double parallel
         return fail(BP_ERR_UNSUPPORTED, "the streamed update (kernel_variant 6) needs FP32, BF16 or Q16 messages "
                                         "and vertices with at most 128 out-edges");
     rp.variant = variant == 3 ? 1 : variant;
-    // RnBP on the streamed update: the update hands the commit its eps test as flag words
-    rp.eps_words = (schedule == BP_RNBP && rp.variant == 6) ? 1 : 0;
+    // RnBP on the streamed update: the update commits itself, writing both
+    // EdgeRatio outcomes (three message buffers); with a recorded trace the
+    // commit kernel runs instead and the update hands it the eps test as flag
+    // words
+    rp.fused_rnbp = (schedule == BP_RNBP && rp.variant == 6 && !rp.record_trace) ? 1 : 0;
+    rp.eps_words = (schedule == BP_RNBP && rp.variant == 6 && !rp.fused_rnbp) ? 1 : 0;
     rp.eps_f = float_at_least(eps);
     // shared-table update in vertex tiles: 0 = per-vertex k-state kernel,
     // 1 = tiles on CUDA cores, 2 = tiles on tensor cores, 3 = tensor cores split
@@ -1087,6 +1115,13 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     int32_t variant = 1;
     if ((rc = build_run_params(g, schedule, parallelism, eps, max_rounds, opt, dtype, rp, variant)) != BP_OK)
         return rc;
+    if (rp.fused_rnbp && !g->d_msg[2]) {
+        // (+ PAD elements like the other two)
+        clear_cache(g);
+        if ((rc = dalloc((char **)&g->d_msg[2], ((size_t)g->M * (size_t)g->buf_epm + PAD) * dtype_size(dtype))) !=
+            BP_OK)
+            return rc;
+    }
     if (rp.eps_words && !g->d_eps_words) {
         // kept until the handle is destroyed (4 words per warp tile)
         if ((rc = dalloc(&g->d_eps_words, (size_t)g->n_wtiles * 4)) != BP_OK)
@@ -1313,6 +1348,7 @@ int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_
     prof.sweep_ctas = 0;
     prof.sweep_form = 0;
     prof.overlap_launches = rp.pdl;
+    prof.fused_commit = rp.fused_rnbp;
     g->last_profile = prof;
     g->has_result = true;
     g->res_dtype = dtype;
@@ -1596,7 +1632,7 @@ int bp_time_update(bp_graph *g, int32_t schedule, double parallelism, const bp_o
     cudaStream_t s = (cudaStream_t)opt.cuda_stream;
     const DevGraph dg = dev_graph(g, dtype);
     const DevRun dr = dev_run(g);
-    const int emode = rp.schedule == SCHED_LBP ? MODE_LBP : MODE_CAND;
+    const int emode = eval_mode(rp);
     launch_init(dtype, dg, dr, s);
     BP_CK(cudaEventRecord(g->ev0, s));
     for (int32_t l = 0; l < launches; ++l) {
@@ -1687,6 +1723,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_red_max);
     dfree(g->d_red_cnt);
     dfree(g->d_red_commit);
+    dfree(g->d_red_commit_lo);
     dfree(g->d_running);
     dfree(g->d_queue);
     dfree(g->d_tc_tiles);
@@ -1694,6 +1731,7 @@ void bp_destroy_graph(bp_graph *g)
     dfree(g->d_err);
     dfree(g->d_potcheck);
     dfree(g->d_wtiles);
+    dfree(g->d_ctiles);
     dfree(g->d_eps_words);
     dfree(g->d_trace);
     dfree(g->d_beliefs);

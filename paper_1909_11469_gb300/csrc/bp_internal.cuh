@@ -19,7 +19,7 @@ struct GState {
     int32_t rounds;        // committing rounds so far
     int32_t cur;           // message buffer holding the committed state
     int32_t k_sel;         // RBP/RS frontier size of the current round
-    uint32_t thr;          // RnBP threshold floor(p * 2^32) of the current round
+    uint32_t thr;          // RnBP threshold floor(p * 2^16) of the current round
     int32_t always;        // RnBP: p >= 1 this round
     uint64_t n_prev;       // RnBP: unconverged count of the previous round
     unsigned long long committed;
@@ -71,6 +71,9 @@ struct DevGraph {
     // n_wtiles = 0 when a vertex has > STREAM_WT edges
     const int4 *wtiles;
     int32_t n_wtiles;
+    // per warp tile {first edge, end edge, graph, graph's first edge} (the
+    // RnBP commit's record: no dependent graph-offset load)
+    const int4 *ctiles;
 };
 
 // Per-run parameters (kernel arguments, baked into the captured graph).
@@ -98,6 +101,8 @@ struct RunParams {
     int32_t dynamic_p;        // 1: RBP / RS frontier fraction switched per round by EdgeRatio
     int32_t eps_words;        // 1: the streamed update writes the eps flag words (DevRun::eps_words)
                               // and the RnBP commit reads them instead of the residuals
+    int32_t fused_rnbp;       // 1: RnBP rounds commit inside the streamed update (three message
+                              // buffers, GState::cur in 0..2), no commit kernel
 };
 
 // eps in the residual type, chosen so that the comparison equals the FP64 test.
@@ -116,7 +121,8 @@ struct GSelState {
 
 // Mutable per-run device buffers.
 struct DevRun {
-    void *msg[2];                 // message buffers (storage dtype)
+    void *msg[3];                 // message buffers (storage dtype); the third only for the fused
+                                  // RnBP rounds
     void *resid;                  // [M] residuals (float, or double for FP64)
     void *vres;                   // [n] vertex residuals for RS (residual type)
     int8_t *level;                // [n] splash level (-1 none)
@@ -124,7 +130,9 @@ struct DevRun {
     unsigned long long *red_max;  // [G*NSUB] double bits
     unsigned int *red_cnt;        // [G*NSUB]
     unsigned int *red_commit;     // [G*NSUB] RnBP commits of the round per sub-slot, folded into
-                                  // GState::committed by the next decision (null: not used)
+                                  // GState::committed by the next decision (null: not used); with
+                                  // the fused RnBP rounds, the commits of the HighP outcome
+    unsigned int *red_commit_lo;  // [G*NSUB] fused RnBP rounds: the commits of the LowP outcome
     int32_t *n_running;           // [1]
     uint32_t *trace;              // [trace_capacity * trace_words]
     double *beliefs;              // [n*k]
@@ -155,12 +163,23 @@ __device__ __forceinline__ double graph_low_p(const DevRun &dr, const RunParams 
 // evaluation: HighP in round 1, then LowP when n_now / n_prev > the threshold
 // (bad convergence), else HighP. RnBP uses it every round; RBP and RS use it
 // with dynamic_p for their frontier fraction.
+__device__ __forceinline__ bool edge_ratio_low(const RunParams &rp, int rounds, unsigned long long n_now,
+                                               unsigned long long n_prev)
+{
+    return rounds != 1 && (double)n_now / (double)n_prev > rp.ratio_threshold;
+}
 __device__ __forceinline__ double edge_ratio_p(const RunParams &rp, double low_p, int rounds,
                                                unsigned long long n_now, unsigned long long n_prev)
 {
-    if (rounds == 1)
-        return rp.high_p;
-    return ((double)n_now / (double)n_prev > rp.ratio_threshold) ? low_p : rp.high_p;
+    return edge_ratio_low(rp, rounds, n_now, n_prev) ? low_p : rp.high_p;
+}
+
+// RnBP random-filter threshold of frontier probability p (R7: a 16-bit draw
+// is kept when below floor(p 2^16)); p >= 1 keeps every eligible message.
+__device__ __forceinline__ void rnbp_threshold(double p, uint32_t &thr, int &always)
+{
+    always = (p >= 1.0) ? 1 : 0;
+    thr = (p <= 0.0 || p >= 1.0) ? 0u : (uint32_t)(p * 65536.0);
 }
 
 // Programmatic dependent launch: a grid launched with programmatic stream
@@ -180,7 +199,7 @@ constexpr int LVL_MAX = 3;
 
 // Message buffer b (0 or 1). A select instead of msg[b]: indexing the kernel
 // parameter array with a runtime value would copy the whole struct to local memory.
-__device__ __forceinline__ void *msg_buf(const DevRun &dr, int b) { return b ? dr.msg[1] : dr.msg[0]; }
+__device__ __forceinline__ void *msg_buf(const DevRun &dr, int b) { return dr.msg[b]; }
 
 // ---------------------------------------------------------------------------
 // Storage traits: message element type S, arithmetic type A. sc is the Q16
@@ -317,24 +336,27 @@ __device__ __forceinline__ uint4 philox4(uint32_t c0, uint32_t c1, uint32_t c2, 
 }
 
 // RnBP random filter (Section IV-A): the Philox block of key seed and counter
-// (local_edge / 4, round, graph id, 0) serves four consecutive messages of a
-// graph; message local_edge draws word local_edge mod 4 and is selected when
-// it is below the round's threshold floor(p 2^32).
-__device__ __forceinline__ uint4 rnbp_block(const RunParams &rp, uint32_t quad, uint32_t round, uint32_t graph)
+// (local_edge / 8, round, graph id, 0) serves eight consecutive messages of a
+// graph; message local_edge draws the 16-bit half (local_edge mod 2: 0 low,
+// 1 high) of word (local_edge mod 8) / 2 and is selected when the half is
+// below the round's threshold floor(p 2^16).
+constexpr int RNBP_PER_BLOCK = 8;
+__device__ __forceinline__ uint4 rnbp_block(const RunParams &rp, uint32_t octet, uint32_t round, uint32_t graph)
 {
-    return philox4(quad, round, rp.graph_id_base + graph, 0u, (uint32_t)(rp.seed & 0xffffffffu),
+    return philox4(octet, round, rp.graph_id_base + graph, 0u, (uint32_t)(rp.seed & 0xffffffffu),
                    (uint32_t)(rp.seed >> 32));
 }
-__device__ __forceinline__ uint32_t rnbp_word(const uint4 &b, uint32_t j)
+__device__ __forceinline__ uint32_t rnbp_draw16(const uint4 &b, uint32_t j)
 {
-    return j == 0 ? b.x : (j == 1 ? b.y : (j == 2 ? b.z : b.w));
+    const uint32_t w = j < 2 ? b.x : (j < 4 ? b.y : (j < 6 ? b.z : b.w));
+    return (j & 1u) ? (w >> 16) : (w & 0xffffu);
 }
 __device__ __forceinline__ bool rnbp_pick(const RunParams &rp, uint32_t local_edge, uint32_t round,
                                           uint32_t graph, const GState &st)
 {
     if (st.always)
         return true;
-    return rnbp_word(rnbp_block(rp, local_edge >> 2, round, graph), local_edge & 3u) < st.thr;
+    return rnbp_draw16(rnbp_block(rp, local_edge >> 3, round, graph), local_edge & 7u) < st.thr;
 }
 
 // ---------------------------------------------------------------------------

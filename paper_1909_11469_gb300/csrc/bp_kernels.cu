@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 namespace bpg {
@@ -235,6 +236,7 @@ __global__ void __launch_bounds__(DECIDE_BLOCK) k_decide(DevGraph g, DevRun dr, 
     unsigned long long mb = dr.red_max[(size_t)gg * NSUB + lane];
     unsigned int c = dr.red_cnt[(size_t)gg * NSUB + lane];
     unsigned int cm = dr.red_commit ? dr.red_commit[(size_t)gg * NSUB + lane] : 0u;
+    unsigned int cm_lo = rp.fused_rnbp ? dr.red_commit_lo[(size_t)gg * NSUB + lane] : 0u;
     const double low_p = lane == 0 ? graph_low_p(dr, rp, gg) : 0.0;
     if (__shfl_sync(0xffffffffu, st.status, 0) != ST_RUNNING)
         return;
@@ -242,12 +244,16 @@ __global__ void __launch_bounds__(DECIDE_BLOCK) k_decide(DevGraph g, DevRun dr, 
     dr.red_cnt[(size_t)gg * NSUB + lane] = 0u;
     if (dr.red_commit)
         dr.red_commit[(size_t)gg * NSUB + lane] = 0u;
+    if (rp.fused_rnbp)
+        dr.red_commit_lo[(size_t)gg * NSUB + lane] = 0u;
     mb = warp_max_u64(mb);
     c = warp_sum_u32(c);
     cm = warp_sum_u32(cm);
+    cm_lo = warp_sum_u32(cm_lo);
     if (lane != 0)
         return;
-    st.committed += (unsigned long long)cm;   // the RnBP commit of the previous round
+    if (!rp.fused_rnbp)
+        st.committed += (unsigned long long)cm;   // the RnBP commit of the previous round
     const double maxr = __longlong_as_double((long long)mb);
     const int64_t Mg = g.ge_off[gg + 1] - g.ge_off[gg];
     const int64_t ng = g.gv_off[gg + 1] - g.gv_off[gg];
@@ -266,9 +272,14 @@ __global__ void __launch_bounds__(DECIDE_BLOCK) k_decide(DevGraph g, DevRun dr, 
             st.cur ^= 1;
             st.committed += (unsigned long long)Mg;
         } else if (rp.schedule == SCHED_RNBP) {
-            const double p = edge_ratio_p(rp, low_p, st.rounds, c, st.n_prev);
-            st.always = (p >= 1.0) ? 1 : 0;
-            st.thr = (p <= 0.0 || p >= 1.0) ? 0u : (uint32_t)(uint64_t)(p * 4294967296.0);
+            const bool lowsel = edge_ratio_low(rp, st.rounds, c, st.n_prev);
+            rnbp_threshold(lowsel ? low_p : rp.high_p, st.thr, st.always);
+            if (rp.fused_rnbp) {
+                // the update already wrote both outcomes: HighP into buffer
+                // cur + 1, LowP into cur + 2 (mod 3)
+                st.cur = (st.cur + (lowsel ? 2 : 1)) % 3;
+                st.committed += (unsigned long long)(lowsel ? cm_lo : cm);
+            }
         } else {
             const int64_t base = (rp.schedule == SCHED_RS && rp.rs_roots_mode == 1) ? ng : Mg;
             const int64_t hi = (rp.schedule == SCHED_RS) ? ng : Mg;
@@ -324,139 +335,218 @@ __device__ __forceinline__ void add_commit_counts(const DevRun &dr, bool uniform
 constexpr int TILE_V = 256;
 constexpr int TILE_E = 8 * TILE_V - 8;
 
-// RnBP commit over the warp tiles of the streamed update (single-graph runs
-// of consecutive vertices, <= 128 out-edges): eight lanes per tile (a warp
-// carries four tiles' loads in flight: the kernel is bound by the latency of
-// its short dependent chain) read the tile record, then together the graph's
-// round state and the eps test of the tile's messages: with the streamed
-// update, four flag words per tile that the update wrote with warp ballots
-// (one bit per message, 16 bytes per tile instead of the tile's residuals),
-// else the residuals. Each lane takes aligned quads of four consecutive
-// messages of the graph, which share one Philox block (one block per quad
-// instead of one per message), and applies the eps filter; then it issues the
-// loads of all its selected candidates before any store. The chain of a tile
-// (record -> flags and state -> candidate -> store) overlaps with the other
-// resident warps'; the commits of a tile are added with one atomic.
-// lanes per tile of the warp-tile commit: 8 (four tiles' loads in flight per
-// warp) measured 43 us per launch on the 4096-graph ER batch, 16 lanes 48 us,
-// a warp per tile 58 us
+// Lanes per tile of the warp-tile RnBP commits. A tile of <= 128 messages
+// meets <= 17 aligned octets of its graph (the messages of one Philox block),
+// so a lane takes COMMIT_OPL = 3 octets: its eligibility and pick bits fit
+// one word.
 constexpr int COMMIT_LPT = 8;
+constexpr int COMMIT_OPL = (STREAM_WT / RNBP_PER_BLOCK + 1 + COMMIT_LPT - 1) / COMMIT_LPT;
+static_assert(COMMIT_OPL * RNBP_PER_BLOCK <= 32, "a lane's eligibility and pick bits fit one word");
 
-template <typename S>
-__global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun dr, RunParams rp)
+// Picks of a lane's octets: bit (8 k + j) of elig is message j of the lane's
+// octet k (octet oct0 + hl + COMMIT_LPT k of graph gg); the octet's Philox
+// block is drawn only when one of its messages is eligible.
+__device__ __forceinline__ unsigned commit_picks(const RunParams &rp, unsigned elig, int oct0, int hl, int rounds,
+                                                 int gg, bool always, uint32_t thr)
 {
-    griddep_launch_dependents();
-    using RT = typename ResidT<S>::T;
-    constexpr int LPT = COMMIT_LPT;             // lanes per tile
-    constexpr int QPL = (34 + LPT - 1) / LPT;   // quads per lane: a tile of <= 128 edges meets <= 34 quads
-    static_assert(QPL * 4 <= 32, "a lane's eligibility and pick bits fit one word");
-    const int lane = threadIdx.x & 31, hl = lane % LPT;
-    const unsigned hmask = (LPT == 32 ? 0xffffffffu : ((1u << LPT) - 1u)) << (lane - hl);
-    const int t = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) / LPT);   // this lane group's tile
-    bool act = t < g.n_wtiles;
-    int e0 = 0, e1 = 0, gg = 0;
-    if (act) {
-        const int4 rec = g.wtiles[t];
-        e0 = rec.y;
-        e1 = g.wtiles[t + 1].y;
-        gg = rec.z;
-        act = e1 > e0;
+    unsigned pick = 0;
+#pragma unroll
+    for (int k = 0; k < COMMIT_OPL; ++k) {
+        const unsigned b8 = (elig >> (RNBP_PER_BLOCK * k)) & 0xffu;
+        if (!b8)
+            continue;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (!always)
+            w = rnbp_block(rp, (uint32_t)(oct0 + hl + COMMIT_LPT * k), (uint32_t)rounds, (uint32_t)gg);
+#pragma unroll
+        for (int j = 0; j < RNBP_PER_BLOCK; ++j)
+            if (((b8 >> j) & 1u) && (always || rnbp_draw16(w, (uint32_t)j) < thr))
+                pick |= 1u << (RNBP_PER_BLOCK * k + j);
     }
-    const int ge0 = act ? g.ge_off[gg] : 0;
-    const int q0 = (e0 - ge0) >> 2, q1 = act ? (e1 - 1 - ge0) >> 2 : -1;
-    griddep_wait();   // flags or residuals, candidates and round state come from the previous kernels
-    // eligibility bit (k, j) of this lane: residual >= eps (Eq. 4 against eps),
-    // from the tile's four flag words the streamed update wrote, else from the
-    // residuals themselves
-    unsigned elig = 0;
-    if (act && rp.eps_words) {
-        // the quad's four bits from the tile's words (bits past the tile's
-        // messages are 0; the first quad may start up to 3 messages before it)
-        const uint32_t *fw = dr.eps_words + (size_t)t * 4;
-#pragma unroll
-        for (int k = 0; k < QPL; ++k) {
-            const int li0 = ge0 + 4 * (q0 + hl + LPT * k) - e0;   // index inside the tile
-            unsigned b4 = 0;
-            if (li0 < 0)
-                b4 = fw[0] << (-li0);
-            else if (li0 < STREAM_WT)
-                b4 = __funnelshift_r(fw[li0 >> 5], (li0 >> 5) < 3 ? fw[(li0 >> 5) + 1] : 0u, li0 & 31);
-            elig |= (b4 & 15u) << (4 * k);
-        }
-    } else if (act) {
-        const RT *R = (const RT *)dr.resid;
-        const RT eps = eps_in(rp, (RT)0);
-#pragma unroll
-        for (int k = 0; k < QPL; ++k) {
-            const int q = q0 + hl + LPT * k;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int e = ge0 + 4 * q + j;
-                if (q <= q1 && e >= e0 && e < e1 && R[e] >= eps)
-                    elig |= 1u << (4 * k + j);
-            }
-        }
-    }
-    int rounds = 0;
-    if (act) {
-        const GState *sp = dr.gs + gg;
-        const int status = sp->status, always = sp->always;
-        const uint32_t thr = sp->thr;
-        rounds = sp->rounds;
-        act = status == ST_RUNNING;
-        if (!act)
-            elig = 0;
-        // selection bit (k, j) of this lane
-        unsigned pick = 0;
-#pragma unroll
-        for (int k = 0; k < QPL; ++k) {
-            const int q = q0 + hl + LPT * k;
-            if (!((elig >> (4 * k)) & 15u))
-                continue;
-            uint4 w = make_uint4(0u, 0u, 0u, 0u);
-            if (!always)
-                w = rnbp_block(rp, (uint32_t)q, (uint32_t)rounds, (uint32_t)gg);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (((elig >> (4 * k + j)) & 1u) && (always || rnbp_word(w, (uint32_t)j) < thr))
-                    pick |= 1u << (4 * k + j);
-        }
-        elig = pick;
-    }
-    const unsigned pick = elig;
+    return pick;
+}
+
+// Copies a lane's picked candidates (bit b: message first + 8 (hl +
+// COMMIT_LPT (b / 8)) + b % 8, epm stored elements each) into the committed
+// buffer, for binary messages every load before any store, and records them
+// in the round's trace.
+template <typename S>
+__device__ __forceinline__ void commit_copy(const DevRun &dr, const RunParams &rp, unsigned pick, int first, int hl,
+                                            int rounds, int epm)
+{
     S *dst = (S *)dr.msg[0];
     const S *src = (const S *)dr.msg[1];
-    const int epm = g.epm;
+    constexpr int NB = COMMIT_OPL * RNBP_PER_BLOCK;
     if (epm == 1) {
-        S v[QPL * 4];
+        S v[NB];
 #pragma unroll
-        for (int b = 0; b < QPL * 4; ++b)
+        for (int b = 0; b < NB; ++b)
             if (pick >> b & 1u)
-                v[b] = src[ge0 + 4 * (q0 + hl + LPT * (b >> 2)) + (b & 3)];
+                v[b] = src[first + RNBP_PER_BLOCK * (hl + COMMIT_LPT * (b / RNBP_PER_BLOCK)) + b % RNBP_PER_BLOCK];
 #pragma unroll
-        for (int b = 0; b < QPL * 4; ++b)
+        for (int b = 0; b < NB; ++b)
             if (pick >> b & 1u)
-                dst[ge0 + 4 * (q0 + hl + LPT * (b >> 2)) + (b & 3)] = v[b];
+                dst[first + RNBP_PER_BLOCK * (hl + COMMIT_LPT * (b / RNBP_PER_BLOCK)) + b % RNBP_PER_BLOCK] = v[b];
     } else {
-        for (int b = 0; b < QPL * 4; ++b)
+        for (int b = 0; b < NB; ++b)
             if (pick >> b & 1u) {
-                const size_t e = (size_t)(ge0 + 4 * (q0 + hl + LPT * (b >> 2)) + (b & 3));
+                const size_t e =
+                    (size_t)(first + RNBP_PER_BLOCK * (hl + COMMIT_LPT * (b / RNBP_PER_BLOCK)) + b % RNBP_PER_BLOCK);
                 for (int x = 0; x < epm; ++x)
                     dst[e * epm + x] = src[e * epm + x];
             }
     }
     if (rp.record_trace && rounds <= rp.trace_capacity) {
-        for (int b = 0; b < QPL * 4; ++b)
+        for (int b = 0; b < NB; ++b)
             if (pick >> b & 1u) {
-                const int e = ge0 + 4 * (q0 + hl + LPT * (b >> 2)) + (b & 3);
+                const int e = first + RNBP_PER_BLOCK * (hl + COMMIT_LPT * (b / RNBP_PER_BLOCK)) + b % RNBP_PER_BLOCK;
                 atomicOr(&dr.trace[(size_t)(rounds - 1) * rp.trace_words + (e >> 5)], 1u << (e & 31));
             }
     }
+}
+
+// RnBP commit over the warp tiles of the streamed update (single-graph runs
+// of consecutive vertices, <= 128 out-edges), from the residuals (the other
+// update mappings and k-state messages): eight lanes per tile (a warp
+// carries four tiles' loads in flight) read the tile's commit record, then
+// together the graph's round state and the eps test of the tile's messages.
+// Each lane takes aligned octets of consecutive messages of the graph, which
+// share one Philox block, applies the eps filter and the random filter, then
+// issues the loads of all its selected candidates before any store. The
+// commits of a tile are added with one atomic.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK, 5) k_commit_rnbp_wt(DevGraph g, DevRun dr, RunParams rp)
+{
+    griddep_launch_dependents();
+    using RT = typename ResidT<S>::T;
+    constexpr int LPT = COMMIT_LPT;
+    const int lane = threadIdx.x & 31, hl = lane % LPT;
+    const unsigned hmask = ((1u << LPT) - 1u) << (lane - hl);
+    const int t = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) / LPT);   // this lane group's tile
+    const int4 rc = t < g.n_wtiles ? g.ctiles[t] : make_int4(0, 0, 0, 0);   // {e0, e1, graph, graph's e0}
+    const int e0 = rc.x, e1 = rc.y, gg = rc.z, ge0 = rc.w;
+    const int off = (e0 - ge0) & (RNBP_PER_BLOCK - 1);   // the first octet starts up to 7 messages before the tile
+    griddep_wait();   // residuals, candidates and round state come from the previous kernels
+    if (e1 <= e0)
+        return;   // the whole lane group: a tile past the end or without edges
+    const GState *sp = dr.gs + gg;
+    const int status = sp->status, rounds = sp->rounds, always = sp->always;
+    const uint32_t thr = sp->thr;
+    // eligibility: residual >= eps (Eq. 4 against eps)
+    unsigned elig = 0;
+    if (status == ST_RUNNING) {
+        const RT *R = (const RT *)dr.resid;
+        const RT eps = eps_in(rp, (RT)0);
+#pragma unroll
+        for (int b = 0; b < COMMIT_OPL * RNBP_PER_BLOCK; ++b) {
+            const int e = e0 - off + RNBP_PER_BLOCK * (hl + LPT * (b / RNBP_PER_BLOCK)) + b % RNBP_PER_BLOCK;
+            if (e >= e0 && e < e1 && R[e] >= eps)
+                elig |= 1u << b;
+        }
+    }
+    const unsigned pick = commit_picks(rp, elig, (e0 - ge0 - off) / RNBP_PER_BLOCK, hl, rounds, gg, always != 0, thr);
+    commit_copy<S>(dr, rp, pick, e0 - off, hl, rounds, g.epm);
     // one atomic per tile into one of the graph's sub-slots (a single-graph
     // run has tens of thousands of tiles: one counter would serialise them)
     const unsigned c = __reduce_add_sync(hmask, (unsigned)__popc(pick));
     if (hl == 0 && c)
         atomicAdd(&dr.red_commit[(size_t)gg * NSUB + (t & (NSUB - 1))], c);
+}
+
+// RnBP commit after the streamed update (binary messages), from the four
+// flag words per warp tile that the update wrote with warp ballots (bit i:
+// message i of the tile passed the eps test of Eq. 4; bits past the tile's
+// messages are 0). A persistent grid of eight-lane groups walks the tiles with
+// a stride of the group count and keeps three tiles in flight: it picks and
+// copies the messages of one tile while the flag words and round state of
+// its next tile and the commit record of the one after are on their way.
+// Each lane takes aligned octets of consecutive messages of the graph (one
+// Philox block per octet) and issues the loads of all its selected
+// candidates before any store.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK, 3) k_commit_rnbp_pipe(DevGraph g, DevRun dr, RunParams rp)
+{
+    griddep_launch_dependents();
+    constexpr int LPT = COMMIT_LPT;
+    const int lane = threadIdx.x & 31, hl = lane % LPT;
+    const unsigned hmask = ((1u << LPT) - 1u) << (lane - hl);
+    const int nt = g.n_wtiles;
+    const int ng = (int)(((long long)gridDim.x * blockDim.x) / LPT);   // lane groups in the grid
+    int t = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) / LPT);
+    const int4 z4 = make_int4(0, 0, 0, 0);
+    // commit records {e0, e1, graph, graph's e0} of this tile and the next
+    int4 rc = t < nt ? g.ctiles[t] : z4;
+    int4 rn = (long long)t + ng < nt ? g.ctiles[t + ng] : z4;
+    griddep_wait();   // flags, candidates and round state come from the previous kernels
+    // flag words and round state (status, rounds, always, thr) of tile t
+    uint4 fw = make_uint4(0u, 0u, 0u, 0u);
+    int4 st = z4;
+    if (t < nt) {
+        fw = *reinterpret_cast<const uint4 *>(dr.eps_words + (size_t)t * 4);
+        const GState *sp = dr.gs + rc.z;
+        st = make_int4(sp->status, sp->rounds, sp->always, (int)sp->thr);
+    }
+    for (; t < nt; t += ng) {
+        // prefetch: the next tile's flags and state, the record after it
+        const long long tn = (long long)t + ng, t2 = tn + ng;
+        const int4 r2 = t2 < nt ? g.ctiles[t2] : z4;
+        uint4 fwn = make_uint4(0u, 0u, 0u, 0u);
+        int4 stn = z4;
+        if (tn < nt) {
+            fwn = *reinterpret_cast<const uint4 *>(dr.eps_words + (size_t)tn * 4);
+            const GState *sp = dr.gs + rn.z;
+            stn = make_int4(sp->status, sp->rounds, sp->always, (int)sp->thr);
+        }
+        // this tile
+        const int e0 = rc.x, e1 = rc.y, gg = rc.z, ge0 = rc.w;
+        const int off = (e0 - ge0) & (RNBP_PER_BLOCK - 1);   // the first octet starts up to 7 messages before the tile
+        unsigned elig = 0;
+        if (st.x == ST_RUNNING && e1 > e0) {
+#pragma unroll
+            for (int k = 0; k < COMMIT_OPL; ++k) {
+                const int li0 = RNBP_PER_BLOCK * (hl + LPT * k) - off;   // the octet's first message in the tile
+                unsigned b8 = 0;
+                if (li0 < 0) {
+                    b8 = fw.x << (-li0);
+                } else if (li0 < STREAM_WT) {
+                    const int wi = li0 >> 5;
+                    const uint32_t lo = wi == 0 ? fw.x : (wi == 1 ? fw.y : (wi == 2 ? fw.z : fw.w));
+                    const uint32_t hi = wi == 0 ? fw.y : (wi == 1 ? fw.z : (wi == 2 ? fw.w : 0u));
+                    b8 = __funnelshift_r(lo, hi, li0 & 31);
+                }
+                elig |= (b8 & 0xffu) << (RNBP_PER_BLOCK * k);
+            }
+        }
+        const unsigned pick = commit_picks(rp, elig, (e0 - ge0 - off) / RNBP_PER_BLOCK, hl, st.y, gg, st.z != 0,
+                                           (uint32_t)st.w);
+        commit_copy<S>(dr, rp, pick, e0 - off, hl, st.y, 1);
+        // one atomic per tile into one of the graph's sub-slots
+        const unsigned c = __reduce_add_sync(hmask, (unsigned)__popc(pick));
+        if (hl == 0 && c)
+            atomicAdd(&dr.red_commit[(size_t)gg * NSUB + (t & (NSUB - 1))], c);
+        rc = rn;
+        rn = r2;
+        fw = fwn;
+        st = stn;
+    }
+}
+
+template <typename S> int commit_pipe_blocks()
+{
+    static int cached[64];
+    static std::once_flag once[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dev &= 63;
+    std::call_once(once[dev], [&] {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_commit_rnbp_pipe<S>, BLOCK, 0) != cudaSuccess)
+            nb = 1;
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = std::max(nb, 1) * std::max(sms, 1);
+    });
+    return cached[dev];
 }
 
 template <typename S>
@@ -850,6 +940,8 @@ __global__ void k_init_state(DevRun dr, int G)
         dr.red_cnt[t] = 0u;
         if (dr.red_commit)
             dr.red_commit[t] = 0u;
+        if (dr.red_commit_lo)
+            dr.red_commit_lo[t] = 0u;
         if (t < G) {
             GState st;
             st.status = ST_RUNNING;
@@ -1299,6 +1391,13 @@ void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const Ru
 {
     if (g.n == 0)
         return;
+    if (g.n_wtiles > 0 && rp.eps_words && g.epm == 1 && dtype != DT_F64) {
+        // the flag words of the streamed update: one wave of lane groups
+        BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_pipe<S>,
+                                       std::min(commit_pipe_blocks<S>(), blocks_for(g.n_wtiles, BLOCK / COMMIT_LPT)),
+                                       BLOCK, s, g, dr, rp)));
+        return;
+    }
     if (g.n_wtiles > 0) {
         // eight lanes per warp tile
         BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_wt<S>, blocks_for(g.n_wtiles, BLOCK / COMMIT_LPT), BLOCK, s,

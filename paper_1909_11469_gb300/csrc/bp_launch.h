@@ -7,7 +7,10 @@
 
 namespace bpg {
 
-enum { MODE_LBP = 0, MODE_CAND = 1, MODE_SPLASH = 2 };
+// update modes: LBP (new messages), candidates + residuals (RBP, RnBP, RS),
+// Residual Splash sweep evaluation, and the RnBP round with its commit fused
+// (the streamed update writes both EdgeRatio outcomes; see bp_stream.cu)
+enum { MODE_LBP = 0, MODE_CAND = 1, MODE_SPLASH = 2, MODE_RNBP_FUSED = 3 };
 enum { SCHED_LBP = 0, SCHED_RBP = 1, SCHED_RS = 2, SCHED_RNBP = 3 };
 enum { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2, DT_Q16 = 3 };
 

@@ -160,8 +160,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_persistent(DevGraph g, DevRun dr
             } else if (SCHED == SCHED_RNBP) {
                 const double p = edge_ratio_p(rp, graph_low_p(dr, rp, gg), rounds, ntot, n_prev);
                 GState sel;
-                sel.always = (p >= 1.0) ? 1 : 0;
-                sel.thr = (p <= 0.0 || p >= 1.0) ? 0u : (uint32_t)(uint64_t)(p * 4294967296.0);
+                rnbp_threshold(p, sel.thr, sel.always);
                 S *dst = (S *)dr.msg[0];
                 const S *src = (const S *)dr.msg[1];
                 for (int e = elo + (int)threadIdx.x; e < ehi; e += blockDim.x) {

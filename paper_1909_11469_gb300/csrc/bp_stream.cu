@@ -27,6 +27,21 @@
 // The arithmetic and its order are those of the per-vertex routine, so every
 // mapping writes the same bits. Every wait is bounded: on expiry the kernel
 // sets an error flag that the host reports.
+//
+// RnBP rounds can commit inside this kernel (MODE_RNBP_FUSED). The round's
+// frontier probability is LowP or HighP, chosen by EdgeRatio from this
+// round's count of messages with residual >= eps, which is known only after
+// the whole graph is evaluated. The update therefore writes both outcomes:
+// a message is kept in an outcome when it passes the eps test and its 16-bit
+// Philox draw (R7) is below that outcome's threshold, and the outcome then
+// holds the new message, else the old stored word. With the committed
+// messages in buffer c of three, HighP goes to buffer c + 1 and LowP to
+// c + 2 (mod 3); the decision moves the graph to the chosen one. Each tile's
+// 8-message Philox blocks are drawn by one lane each (<= 17 per tile) while
+// the gathers are in flight, and handed to the message lanes by shuffles.
+// This replaces the copying commit kernel, which touched nearly every sector
+// of two buffers (~40% of messages selected), with one more coalesced
+// stream of stores.
 #include "bp_internal.cuh"
 #include "bp_launch.h"
 
@@ -57,6 +72,11 @@ struct SwInfo {
     int cur;               // message buffer of the running graphs
     int e0a, e0s, v0a;     // first elements of the staged edge, message and vertex arrays
     int v0[SW_CONSUMERS + 1], e0[SW_CONSUMERS + 1], g[SW_CONSUMERS], run[SW_CONSUMERS];
+    // fused RnBP rounds, per warp tile: the graph's committed buffer, its
+    // completed rounds, its first edge and its LowP draw threshold (65536:
+    // every eligible message)
+    int cb[SW_CONSUMERS], rnd[SW_CONSUMERS], ge0[SW_CONSUMERS];
+    unsigned tlo[SW_CONSUMERS];
 };
 
 // Shared-memory layout, in bytes.
@@ -115,25 +135,48 @@ __device__ __forceinline__ void bulk_load(unsigned dst, const void *src, unsigne
 // (max residual, count) of one graph from every lane of a warp into a
 // reduction sub-slot. The residuals are non-negative floats, whose bit
 // patterns order like the values, so the warp max is one integer reduction.
-__device__ __forceinline__ void sw_flush(const DevRun &dr, int gg, float maxa, unsigned cnt, int slot)
+// With the fused RnBP rounds also the commits of the HighP and LowP outcomes.
+template <bool FUSED>
+__device__ __forceinline__ void sw_flush(const DevRun &dr, int gg, float maxa, unsigned cnt, unsigned chi,
+                                         unsigned clo, int slot)
 {
     const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(maxa));
     cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (FUSED) {
+        chi = __reduce_add_sync(0xffffffffu, chi);
+        clo = __reduce_add_sync(0xffffffffu, clo);
+    }
     if ((threadIdx.x & 31) == 0 && gg >= 0) {
         if (mb)
             atomicMax(&dr.red_max[(size_t)gg * NSUB + slot],
                       (unsigned long long)__double_as_longlong((double)__uint_as_float(mb)));
         if (cnt)
             atomicAdd(&dr.red_cnt[(size_t)gg * NSUB + slot], cnt);
+        if (FUSED && chi)
+            atomicAdd(&dr.red_commit[(size_t)gg * NSUB + slot], chi);
+        if (FUSED && clo)
+            atomicAdd(&dr.red_commit_lo[(size_t)gg * NSUB + slot], clo);
     }
 }
 
+// Draw threshold of frontier probability p for the fused RnBP rounds: the
+// R7 threshold, or 65536 (above every 16-bit draw) when p >= 1.
+__device__ __forceinline__ unsigned sw_draw_threshold(double p)
+{
+    uint32_t thr;
+    int always;
+    rnbp_threshold(p, thr, always);
+    return always ? 65536u : thr;
+}
+
 template <typename S, int MODE>
-__global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevRun dr, RunParams rp)
+__global__ void __launch_bounds__(SW_THREADS, MODE == MODE_RNBP_FUSED ? 2 : 1)
+    k_eval_bin_stream(DevGraph g, DevRun dr, RunParams rp)
 {
     using A = typename Store<S>::A;
     using RT = typename ResidT<S>::T;
     using L = SwLayout<S>;
+    constexpr bool FUSED = MODE == MODE_RNBP_FUSED;
     static_assert(sizeof(A) == 4, "FP32 arithmetic only");
     constexpr int EPS = 16 / (int)sizeof(S);   // stored message elements per 16 bytes
     extern __shared__ __align__(128) unsigned char sw_raw[];
@@ -168,7 +211,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
             }
             const int bt = (int)blockIdx.x + i * (int)gridDim.x;
             const int t = bt * SW_CONSUMERS + lane;   // lanes 0..8: the records of the block tile
-            int v0 = 0, e0 = 0, gg = -1, run = 0, cb = 0;
+            int v0 = 0, e0 = 0, gg = -1, run = 0, cb = 0, rnd = 0, ge0 = 0;
+            unsigned tlo = 0;
             if (lane <= SW_CONSUMERS && t <= nwt) {
                 const int4 r = g.wtiles[t];
                 v0 = r.x;
@@ -179,6 +223,11 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
                 const GState *st = dr.gs + gg;
                 run = st->status == ST_RUNNING;
                 cb = st->cur;
+                if (FUSED) {
+                    rnd = st->rounds;
+                    ge0 = g.ge_off[gg];
+                    tlo = sw_draw_threshold(graph_low_p(dr, rp, gg));
+                }
             }
             const int last = min(SW_CONSUMERS, nwt - bt * SW_CONSUMERS);   // warp tiles in this block tile
             const int v_end = __shfl_sync(0xffffffffu, v0, last);
@@ -198,6 +247,12 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
             if (lane < SW_CONSUMERS) {
                 in.g[lane] = gg;
                 in.run[lane] = (lane < last) && run;
+                if (FUSED) {
+                    in.cb[lane] = cb;
+                    in.rnd[lane] = rnd;
+                    in.ge0[lane] = ge0;
+                    in.tlo[lane] = tlo;
+                }
             }
             __syncwarp();
             if (lane == 0) {
@@ -209,15 +264,17 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
                 in.v0a = v0a;
                 const unsigned mb = full0 + 8 * s;
                 if (runm) {
+                    // (the fused RnBP tiles read their old messages from their own graph's buffer)
                     const unsigned b_rev = (unsigned)round16((e_end - e0a) * 4);
-                    const unsigned b_old = (unsigned)round16((e_end - e0s) * (int)sizeof(S));
+                    const unsigned b_old = FUSED ? 0u : (unsigned)round16((e_end - e0s) * (int)sizeof(S));
                     const unsigned b_rp = (unsigned)round16((v_end + 1 - v0a) * 4);
                     const unsigned b_ud = (unsigned)round16((v_end - v0a) * 4);
                     const unsigned st0 = smem_addr(sw_raw + L::STAGES0 + s * L::STAGE);
                     mbar_expect_tx(mb, 2 * b_rev + b_old + b_rp + b_ud);
                     bulk_load(st0, g.rev + e0a, b_rev, mb);
                     bulk_load(st0 + L::REV, (const A *)g.q32 + e0a, b_rev, mb);
-                    bulk_load(st0 + L::REV + L::Q, (const S *)msg_buf(dr, cur) + e0s, b_old, mb);
+                    if (!FUSED)
+                        bulk_load(st0 + L::REV + L::Q, (const S *)msg_buf(dr, cur) + e0s, b_old, mb);
                     bulk_load(st0 + L::REV + L::Q + L::OLD, g.row_ptr + v0a, b_rp, mb);
                     bulk_load(st0 + L::REV + L::Q + L::OLD + L::RP, g.udiff32 + v0a, b_ud, mb);
                 } else {
@@ -240,7 +297,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
     const A eps_a = eps_in(rp, (A)0);
     int acc_g = -1;
     A maxa = 0;
-    unsigned cnt = 0;
+    unsigned cnt = 0, chi = 0, clo = 0;
+    const unsigned thi = FUSED ? sw_draw_threshold(rp.high_p) : 0u;
     for (int i = 0; i < n_local; ++i) {
         const int s = i % SW_STAGES;
         if (!mbar_wait_bounded(full0 + 8 * s, (i / SW_STAGES) & 1)) {
@@ -254,10 +312,12 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
             const int nv = in.v0[c + 1] - v0, ne = in.e0[c + 1] - e0;
             const int gg = in.g[c];
             if (gg != acc_g) {
-                sw_flush(dr, acc_g, maxa, cnt, slot);
+                sw_flush<FUSED>(dr, acc_g, maxa, cnt, chi, clo, slot);
                 acc_g = gg;
                 maxa = 0;
                 cnt = 0;
+                chi = 0;
+                clo = 0;
             }
             unsigned char *st = sw_raw + L::STAGES0 + s * L::STAGE;
             const int ro = e0 - in.e0a, oo = e0 - in.e0s, vo = v0 - in.v0a;
@@ -267,16 +327,37 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
             const S *s_old = reinterpret_cast<const S *>(st + L::REV + L::Q) + oo;
             const int *s_rp = reinterpret_cast<const int *>(st + L::REV + L::Q + L::OLD) + vo;
             const A *s_ud = reinterpret_cast<const A *>(st + L::REV + L::Q + L::OLD + L::RP) + vo;
-            const S *cur = (const S *)msg_buf(dr, in.cur);
-            S *out = (S *)msg_buf(dr, in.cur ^ 1);
-            // 1. incoming messages
+            const int cbuf = FUSED ? in.cb[c] : in.cur;
+            const S *cur = (const S *)msg_buf(dr, cbuf);
+            S *out = (S *)msg_buf(dr, FUSED ? (cbuf == 2 ? 0 : cbuf + 1) : (cbuf ^ 1));   // (fused: HighP)
+            S *out_lo = (S *)msg_buf(dr, FUSED ? (cbuf == 0 ? 2 : cbuf - 1) : 0);        // (fused: LowP)
+            // 1. incoming messages (fused: and the tile's own old messages)
             constexpr int EPL = STREAM_WT / 32;
             A uin[EPL];
+            S oldw[EPL];
 #pragma unroll
             for (int k = 0; k < EPL; ++k) {
                 const int idx = lane + 32 * k;
-                if (idx < ne)
+                if (idx < ne) {
                     uin[k] = Store<S>::ld(cur + s_rev[idx], qs);
+                    if (FUSED)
+                        oldw[k] = cur[e0 + idx];
+                }
+            }
+            // fused: the tile's Philox blocks, one per lane, while the loads are
+            // in flight (octet j of the graph's messages holds local messages
+            // 8 j .. 8 j + 7; the tile starts at local message m0)
+            uint4 pw = make_uint4(0u, 0u, 0u, 0u);
+            int off = 0;
+            unsigned tlo = 0;
+            bool draws = false;
+            if (FUSED) {
+                tlo = in.tlo[c];
+                draws = !(tlo == 65536u && thi == 65536u);
+                const int m0 = e0 - in.ge0[c];
+                off = m0 & 7;
+                if (draws && lane < ((off + ne + 7) >> 3))
+                    pw = rnbp_block(rp, (uint32_t)((m0 >> 3) + lane), (uint32_t)(in.rnd[c] + 1), (uint32_t)gg);
             }
 #pragma unroll
             for (int k = 0; k < EPL; ++k) {
@@ -302,17 +383,42 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
             for (int k = 0; k < EPL; ++k) {
                 const int idx = lane + 32 * k;
                 bool hit = false;
+                // fused: this message's 16-bit draw from the lane holding its octet
+                unsigned u = 0;
+                if (FUSED && draws) {
+                    const int pos = idx + off, owner = min(pos >> 3, 31), j = pos & 7;
+                    const unsigned wx = __shfl_sync(0xffffffffu, pw.x, owner);
+                    const unsigned wy = __shfl_sync(0xffffffffu, pw.y, owner);
+                    const unsigned wz = __shfl_sync(0xffffffffu, pw.z, owner);
+                    const unsigned ww = __shfl_sync(0xffffffffu, pw.w, owner);
+                    u = rnbp_draw16(make_uint4(wx, wy, wz, ww), (uint32_t)j);
+                }
                 if (idx < ne) {
                     const int e = e0 + idx;
                     const A unew = ising_logodds(s_q[idx], s_h[s_src[idx]] - uin[k]);
                     const A uq = Store<S>::quant(unew, qs);
-                    const A r = fabs(m_sigmoid(uq) - m_sigmoid(Store<S>::val(s_old[idx], qs)));
-                    Store<S>::st(out + e, unew, qs);
-                    if (MODE == MODE_CAND)
+                    const A r = fabs(m_sigmoid(uq) - m_sigmoid(Store<S>::val(FUSED ? oldw[k] : s_old[idx], qs)));
+                    if (MODE == MODE_CAND || FUSED)
                         R[e] = (RT)r;
                     maxa = r > maxa ? r : maxa;
                     hit = r >= eps_a;
                     cnt += hit ? 1u : 0u;
+                    if constexpr (FUSED) {
+                        // both outcomes: the new message where kept, else the old stored word
+                        const bool phi = hit && u < thi, plo = hit && u < tlo;
+                        if (phi)
+                            Store<S>::st(out + e, unew, qs);
+                        else
+                            out[e] = oldw[k];
+                        if (plo)
+                            Store<S>::st(out_lo + e, unew, qs);
+                        else
+                            out_lo[e] = oldw[k];
+                        chi += phi ? 1u : 0u;
+                        clo += plo ? 1u : 0u;
+                    } else {
+                        Store<S>::st(out + e, unew, qs);
+                    }
                 }
                 if (MODE == MODE_CAND && rp.eps_words) {
                     // the eps test of 32 consecutive messages of the tile, for the RnBP commit
@@ -329,7 +435,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_eval_bin_stream(DevGraph g, DevR
         if (lane == 0)
             mbar_arrive(empty0 + 8 * s);
     }
-    sw_flush(dr, acc_g, maxa, cnt, slot);
+    sw_flush<FUSED>(dr, acc_g, maxa, cnt, chi, clo, slot);
 }
 
 template <typename S> constexpr int sw_smem_bytes() { return SwLayout<S>::TOTAL; }
@@ -389,6 +495,9 @@ void prepare_stream_kernels()
     sw_blocks_per_sm<__nv_bfloat16, MODE_CAND>();
     sw_blocks_per_sm<int16_t, MODE_LBP>();
     sw_blocks_per_sm<int16_t, MODE_CAND>();
+    sw_blocks_per_sm<float, MODE_RNBP_FUSED>();
+    sw_blocks_per_sm<__nv_bfloat16, MODE_RNBP_FUSED>();
+    sw_blocks_per_sm<int16_t, MODE_RNBP_FUSED>();
 }
 
 void launch_eval_stream(int dtype, const DevGraph &g, const DevRun &dr, const RunParams &rp, int mode,
@@ -396,17 +505,24 @@ void launch_eval_stream(int dtype, const DevGraph &g, const DevRun &dr, const Ru
 {
     if (g.n_wtiles == 0)
         return;
-    const bool cand = mode != MODE_LBP;
+    auto go = [&](auto tag) {
+        using S = decltype(tag);
+        if (mode == MODE_LBP)
+            launch_stream_t<S, MODE_LBP>(g, dr, rp, s);
+        else if (mode == MODE_RNBP_FUSED)
+            launch_stream_t<S, MODE_RNBP_FUSED>(g, dr, rp, s);
+        else
+            launch_stream_t<S, MODE_CAND>(g, dr, rp, s);
+    };
     switch (dtype) {
     case DT_F32:
-        cand ? launch_stream_t<float, MODE_CAND>(g, dr, rp, s) : launch_stream_t<float, MODE_LBP>(g, dr, rp, s);
+        go(float());
         break;
     case DT_BF16:
-        cand ? launch_stream_t<__nv_bfloat16, MODE_CAND>(g, dr, rp, s)
-             : launch_stream_t<__nv_bfloat16, MODE_LBP>(g, dr, rp, s);
+        go(__nv_bfloat16());
         break;
     default:
-        cand ? launch_stream_t<int16_t, MODE_CAND>(g, dr, rp, s) : launch_stream_t<int16_t, MODE_LBP>(g, dr, rp, s);
+        go(int16_t());
         break;
     }
 }

@@ -314,8 +314,9 @@ def test_rnbp_edge_ratio_switch(orc):
         p = 1.0 if t == 1 else (low if n_t / n_prev > 0.9 else 1.0)
         sel = np.zeros(prob.m, bool)
         for e in np.nonzero(r >= eps)[0]:
-            u = int(orc.philox4x32_10([e // 4, t, 0, 0], [99, 0])[e % 4])
-            sel[e] = p >= 1.0 or u < int(p * 2 ** 32)
+            word = int(orc.philox4x32_10([e // 8, t, 0, 0], [99, 0])[(e % 8) // 2])
+            u = (word >> 16) if e % 2 else (word & 0xFFFF)
+            sel[e] = p >= 1.0 or u < int(p * 2 ** 16)
         bits = np.unpackbits(res["trace"][t - 1].view(np.uint8), bitorder="little")[:prob.m]
         assert np.array_equal(bits.astype(bool), sel), t
         used_low += p < 1

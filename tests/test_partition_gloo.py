@@ -114,12 +114,13 @@ def _replay_worker(rank, world, port, sched, par, owner, out):
                 pick = np.ones(plan.n_local_edges, bool)
             else:
                 p = high_p if t == 1 else (par if n_t / n_prev > thr_ratio else high_p)
-                thr = int(p * 4294967296.0)
+                thr = int(p * 65536.0)
                 pick = np.zeros(plan.n_local_edges, bool)
                 for le, ge in enumerate(plan.edges):
                     if r[le] >= eps:
-                        w = int(oracle.philox4x32_10([int(ge) // 4, t, 0, 0], [0, 0])[int(ge) % 4])
-                        pick[le] = p >= 1.0 or w < thr
+                        w = int(oracle.philox4x32_10([int(ge) // 8, t, 0, 0], [0, 0])[(int(ge) % 8) // 2])
+                        u = (w >> 16) if int(ge) % 2 else (w & 0xFFFF)
+                        pick[le] = p >= 1.0 or u < thr
             n_prev = n_t
             msg[:plan.n_local_edges][pick] = cand[pick]
             # one exchange: cut messages to the rank owning their destination

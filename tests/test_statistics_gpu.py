@@ -1,6 +1,12 @@
 """Independent statistics over 50 seeds: the GPU (FP32 messages) and the FP64
 oracle each select their own frontiers. The converged fraction may differ by
-at most one seed (a threshold flip) and converged beliefs agree within 10 eps
+at most one seed (a threshold flip), except under RnBP, whose random frontiers
+(Section IV-A) make convergence within the cap a matter of the random stream
+on a marginal seed (on the 100x100 seeds at LowP 0.5 the oracle's own
+converged count varies between 45 and 47 over random streams 0 to 3): there
+the seeds converged on one side only must not lean to one side beyond chance,
+by the exact two-sided McNemar test at level 0.01 (with all of them on one
+side that takes 8 such seeds). Converged beliefs agree within 10 eps
 per incoming message (both are eps fixed points of the same map and a belief
 combines up to d_max = 4 incoming messages, so the bound is 4 * 10 eps).
 Rounds: LBP is deterministic, so every seed's round count agrees within 10%;
@@ -13,6 +19,7 @@ of the seeds; a single marginal seed, 1448 against 374 rounds, moves the mean
 log ratio of 8 seeds by 0.17). The per-seed statement holds exactly for FP64
 messages: there GPU and oracle select the same frontiers every round, so
 converged flags and round counts are identical on all 50 seeds."""
+import math
 import multiprocessing as mp
 
 import numpy as np
@@ -39,6 +46,17 @@ def _oracle_one(args):
     return r["converged"], r["rounds"], r["beliefs"]
 
 
+def _mcnemar_exact(b, c):
+    """Two-sided exact McNemar p-value of b against c discordant pairs: under
+    equal converged fractions each discordant seed leans either way with
+    probability 1/2."""
+    n = b + c
+    if n == 0:
+        return 1.0
+    tail = sum(math.comb(n, i) for i in range(min(b, c) + 1)) / 2.0 ** n
+    return min(1.0, 2.0 * tail)
+
+
 def _compare(side, beta_max, sched, par, cap, n_seeds=50):
     batch = synth.ising_grid_batch(side, beta_max, range(n_seeds))
     with bp.Graph(batch) as g:
@@ -50,7 +68,14 @@ def _compare(side, beta_max, sched, par, cap, n_seeds=50):
         ref = pool.map(_oracle_one, [(side, beta_max, s, s, sched, par, cap) for s in range(n_seeds)])
     conv_g = np.array([x["converged"] for x in gst], bool)
     conv_o = np.array([r[0] for r in ref], bool)
-    assert abs(int(conv_g.sum()) - int(conv_o.sum())) <= 1, (conv_g.sum(), conv_o.sum())
+    if sched == "rnbp":
+        b = int((conv_g & ~conv_o).sum())
+        c = int((conv_o & ~conv_g).sum())
+        pv = _mcnemar_exact(b, c)
+        print(f"\n  converged on the GPU only: {b}, on the oracle only: {c} (exact McNemar p = {pv:.3f})")
+        assert pv >= 0.01, (b, c, pv)
+    else:
+        assert abs(int(conv_g.sum()) - int(conv_o.sum())) <= 1, (conv_g.sum(), conv_o.sum())
     both = [s for s in range(n_seeds) if conv_g[s] and conv_o[s]]
     rg = np.array([gst[s]["rounds"] for s in both], float)
     ro = np.array([ref[s][1] for s in both], float)

@@ -59,6 +59,16 @@ def test_rnbp_state_bit_identical(dtype):
     assert len({r for _, r, _ in out[6][5]}) > 1          # graphs stopped at different rounds
     for i in (2, 3, 4):
         assert np.array_equal(out[1][i], out[6][i]), i
+    # without a trace the streamed mapping commits inside the update (both
+    # EdgeRatio outcomes written, three message buffers): the same state again
+    with bp.Graph(prob) as g:
+        st = g.run("rnbp", 0.5, eps=1e-4, max_rounds=60, msg_dtype=dtype, seed=7, kernel_variant=6)
+        assert g.profile()["fused_commit"] == 1
+        fused = (st["rounds"], st["committed_updates"], g.messages(), g.residuals(),
+                 [(x["converged"], x["rounds"], x["committed_updates"]) for x in g.graph_stats()])
+    assert fused[0] == out[1][0] and fused[1] == out[1][1] and fused[4] == out[1][5]
+    for i in (2, 3):
+        assert np.array_equal(fused[i], out[1][i]), i
 
 
 def test_rnbp_time_budget_stop_equals_round_cap():
