@@ -79,9 +79,11 @@ MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
 # kernel is unchanged since the capture (the summaries and commands are in
 # profiles/). Captures are cold (ncu flushes the caches), so they bound the warm
 # traffic from above. Keys: (workload, storage, update mapping) and (workload,
-# storage, sweep form).
+# storage, sweep form). The 4096-graph ER capture is of an RnBP round with the
+# commit fused (the residual and both EdgeRatio outcomes stored: 2/3 of the
+# step's update launches); an LBP launch writes 8 B per message less.
 NCU_SWEEP_TRAFFIC = {}
-NCU_UPDATE_TRAFFIC = {}
+NCU_UPDATE_TRAFFIC = {("er4096_b3", "f32", 6): 255.460608e6 + 168.418048e6}
 BYTES_PER_VERTEX = 12
 
 
