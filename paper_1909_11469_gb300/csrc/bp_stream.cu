@@ -38,7 +38,9 @@
 // messages in buffer c of three, HighP goes to buffer c + 1 and LowP to
 // c + 2 (mod 3); the decision moves the graph to the chosen one. Each tile's
 // 8-message Philox blocks are drawn by one lane each (<= 17 per tile) while
-// the gathers are in flight, and handed to the message lanes by shuffles.
+// the gathers are in flight, and handed to the message lanes through shared
+// memory: the block's four words read as eight little-endian 16-bit halves
+// are the draws of its eight messages in order (half j = draw j of R7).
 // This replaces the copying commit kernel, which touched nearly every sector
 // of two buffers (~40% of messages selected), with one more coalesced
 // stream of stores.
@@ -91,7 +93,10 @@ template <typename S> struct SwLayout {
     static constexpr int EMPTY = 64;                                     // SW_STAGES x 8 bytes
     static constexpr int INFO = 128;                                     // SW_STAGES records
     static constexpr int WARPS = round16(INFO + SW_STAGES * (int)sizeof(SwInfo));
-    static constexpr int WARP_B = STREAM_WV * 4 + STREAM_WT;             // per consumer: h, src
+    // per consumer: h, src, and (fused RnBP rounds) the tile's Philox blocks,
+    // read back as 16-bit draws (<= 17 blocks of 16 bytes)
+    static constexpr int DRAW = STREAM_WV * 4 + STREAM_WT;
+    static constexpr int WARP_B = DRAW + 18 * 16;
     static constexpr int STAGES0 = (WARPS + SW_CONSUMERS * WARP_B + 127) / 128 * 128;
     static constexpr int TOTAL = STAGES0 + SW_STAGES * STAGE;
 };
@@ -291,6 +296,7 @@ __global__ void __launch_bounds__(SW_THREADS, MODE == MODE_RNBP_FUSED ? 2 : 1)
     unsigned char *wb = sw_raw + L::WARPS + c * L::WARP_B;
     A *s_h = reinterpret_cast<A *>(wb);
     uint8_t *s_src = wb + STREAM_WV * 4;
+    uint4 *s_draw = reinterpret_cast<uint4 *>(wb + L::DRAW);
     const int slot = ((int)blockIdx.x * SW_CONSUMERS + c) & (NSUB - 1);
     const float qs = g.qscale;
     RT *R = (RT *)dr.resid;
@@ -347,7 +353,6 @@ __global__ void __launch_bounds__(SW_THREADS, MODE == MODE_RNBP_FUSED ? 2 : 1)
             // fused: the tile's Philox blocks, one per lane, while the loads are
             // in flight (octet j of the graph's messages holds local messages
             // 8 j .. 8 j + 7; the tile starts at local message m0)
-            uint4 pw = make_uint4(0u, 0u, 0u, 0u);
             int off = 0;
             unsigned tlo = 0;
             bool draws = false;
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(SW_THREADS, MODE == MODE_RNBP_FUSED ? 2 : 1)
                 const int m0 = e0 - in.ge0[c];
                 off = m0 & 7;
                 if (draws && lane < ((off + ne + 7) >> 3))
-                    pw = rnbp_block(rp, (uint32_t)((m0 >> 3) + lane), (uint32_t)(in.rnd[c] + 1), (uint32_t)gg);
+                    s_draw[lane] = rnbp_block(rp, (uint32_t)((m0 >> 3) + lane), (uint32_t)(in.rnd[c] + 1), (uint32_t)gg);
             }
 #pragma unroll
             for (int k = 0; k < EPL; ++k) {
@@ -383,16 +388,6 @@ __global__ void __launch_bounds__(SW_THREADS, MODE == MODE_RNBP_FUSED ? 2 : 1)
             for (int k = 0; k < EPL; ++k) {
                 const int idx = lane + 32 * k;
                 bool hit = false;
-                // fused: this message's 16-bit draw from the lane holding its octet
-                unsigned u = 0;
-                if (FUSED && draws) {
-                    const int pos = idx + off, owner = min(pos >> 3, 31), j = pos & 7;
-                    const unsigned wx = __shfl_sync(0xffffffffu, pw.x, owner);
-                    const unsigned wy = __shfl_sync(0xffffffffu, pw.y, owner);
-                    const unsigned wz = __shfl_sync(0xffffffffu, pw.z, owner);
-                    const unsigned ww = __shfl_sync(0xffffffffu, pw.w, owner);
-                    u = rnbp_draw16(make_uint4(wx, wy, wz, ww), (uint32_t)j);
-                }
                 if (idx < ne) {
                     const int e = e0 + idx;
                     const A unew = ising_logodds(s_q[idx], s_h[s_src[idx]] - uin[k]);
@@ -404,7 +399,10 @@ __global__ void __launch_bounds__(SW_THREADS, MODE == MODE_RNBP_FUSED ? 2 : 1)
                     hit = r >= eps_a;
                     cnt += hit ? 1u : 0u;
                     if constexpr (FUSED) {
-                        // both outcomes: the new message where kept, else the old stored word
+                        // this message's 16-bit draw (tile message idx is draw idx + off
+                        // of the tile's first block); both outcomes: the new message
+                        // where kept, else the old stored word
+                        const unsigned u = draws ? (unsigned)reinterpret_cast<const uint16_t *>(s_draw)[idx + off] : 0u;
                         const bool phi = hit && u < thi, plo = hit && u < tlo;
                         if (phi)
                             Store<S>::st(out + e, unew, qs);
