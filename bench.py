@@ -83,7 +83,7 @@ MSG_BYTES = {"f32": 4, "bf16": 2, "q16": 2, "f64": 8}
 # commit fused (the residual and both EdgeRatio outcomes stored: 2/3 of the
 # step's update launches); an LBP launch writes 8 B per message less.
 NCU_SWEEP_TRAFFIC = {}
-NCU_UPDATE_TRAFFIC = {}
+NCU_UPDATE_TRAFFIC = {("er4096_b3", "f32", 6): 255.336448e6 + 168.353536e6}
 BYTES_PER_VERTEX = 12
 
 
