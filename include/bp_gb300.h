@@ -118,7 +118,8 @@ typedef struct {
     int32_t kernel_variant;   /* binary Ising update mapping (every mapping computes the
                                  same bits): 0 = automatic (the choice bp_autotune
                                  recorded for the handle's size class; else, for
-                                 messages that are not FP64, 4 when no vertex has more
+                                 messages that are not FP64, 6 for RnBP when the
+                                 streamed tiles apply, 4 when no vertex has more
                                  than 4 edges and 6 when the streamed tiles apply; 1
                                  otherwise), 1 =
                                  per-round kernels, one thread per vertex, 3 = persistent
