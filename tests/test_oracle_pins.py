@@ -45,6 +45,34 @@ def test_rnbp_random_filter_fraction(orc):
     assert abs(picked - 0.3 * m) < 5 * sd
 
 
+def test_rnbp_random_filter_independent(orc):
+    """The random filter's picks are independent Bernoulli(p) draws: for two
+    messages that share a Philox block (adjacent ids: the two halves of one
+    word, or neighbouring words) and for one message in two graphs of a batch
+    (graph ids 0 and 1), both are picked with probability p^2 (within 5 sigma;
+    round 1, where every message is eligible). A draw reused across the halves
+    of a word, across the words of a block or across graphs would give p
+    instead."""
+    prob = synth.ising_grid(60, 1.0, seed=3)
+    p = 0.3
+    m = prob.m
+    picks = []
+    for gid in (0, 1):
+        res = orc.run(prob, "rnbp", parallelism=p, high_p=p, eps=1e-12, max_rounds=1, trace_cap=1, graph_id=gid)
+        picks.append(np.unpackbits(res["trace"][0].view(np.uint8), bitorder="little")[:m].astype(bool))
+    r1, r1b = picks
+
+    def near_p2(both, n):
+        sd = np.sqrt(n * p * p * (1 - p * p))
+        assert abs(both - p * p * n) < 5 * sd, (both, p * p * n, sd)
+
+    m8 = m - m % 8
+    near_p2(int((r1[0:m8:2] & r1[1:m8:2]).sum()), m8 // 2)        # halves of one word
+    near_p2(int((r1[0:m8:8] & r1[2:m8:8]).sum()), m8 // 8)        # words 0 and 1 of a block
+    near_p2(int((r1[0:m8:8] & r1[7:m8:8]).sum()), m8 // 8)        # first and last message of a block
+    near_p2(int((r1 & r1b).sum()), m)                             # one message in two graphs
+
+
 # --------------------------------------------------------------------------- Eq. 2
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_ising_message_closed_form(orc, seed):
