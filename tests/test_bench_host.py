@@ -19,6 +19,20 @@ def test_bytes_per_message():
     # k-state: rev 4 + 3 k s + residual 4
     assert bench.bytes_per_msg("rnbp", "f32", k=32) == 4 + 3 * 32 * 4 + 4
     assert bench.bytes_per_vertex() == 12 and bench.bytes_per_vertex(32) == 8 + 128
+    # RnBP with the commit inside the streamed update: + the second outcome (s)
+    assert bench.bytes_per_msg("rnbp", "f32", fused=True) == 28
+    assert bench.bytes_per_msg("rnbp", "bf16", fused=True) == 20
+
+
+def test_eval_roofline_counts_the_fused_outcome():
+    """A profiled RnBP step whose rounds committed inside the update counts the
+    second outcome's bytes; the same step without it does not."""
+    plain = _step("rnbp", full_evals=1000, vertices=250, eval_ms=1.0)
+    fused = _step("rnbp", full_evals=1000, vertices=250, eval_ms=1.0, extra={"fused_commit": 1})
+    a, _ = bench.eval_roofline([plain], "f32", 1000.0, "measured")
+    b, _ = bench.eval_roofline([fused], "f32", 1000.0, "measured")
+    assert a["bytes_per_launch"] == (24 * 1000 + 12 * 250) / 10
+    assert b["bytes_per_launch"] == (28 * 1000 + 12 * 250) / 10
 
 
 def test_round_caps():
