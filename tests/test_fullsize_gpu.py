@@ -115,6 +115,27 @@ def test_er_batch_4096_sampled(variant):
         assert np.abs(bel[v0:v1] - ref["beliefs"]).max() < 1e-9, gi
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_er_batch_4096_fused_commit_equals_commit_kernel(dtype):
+    """The benchmark's workload as the bench runs it (RnBP on the streamed
+    update without a trace: the commit inside the update, both EdgeRatio
+    outcomes written) against the same run with a recorded trace (the commit
+    kernel after the update, whose frontiers the trace-follow test below checks
+    against the oracle): the same messages, residuals and per-graph counters,
+    bit for bit, after 30 rounds."""
+    batch = synth.er_batch(4096, seed=0)
+    out = []
+    for trace in (0, 1):
+        with bp.Graph(batch) as g:
+            st = g.run("rnbp", 0.5, eps=1e-4, max_rounds=30, msg_dtype=dtype, record_trace=trace,
+                       trace_capacity=30 if trace else 0, seed=3, kernel_variant=6, **_stream_opts())
+            assert g.profile()["fused_commit"] == (0 if trace else 1)
+            out.append((st["rounds"], st["committed_updates"], g.messages(), g.residuals(),
+                        [(x["converged"], x["rounds"], x["committed_updates"]) for x in g.graph_stats()]))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1] and out[0][4] == out[1][4]
+    assert np.array_equal(out[0][2], out[1][2]) and np.array_equal(out[0][3], out[1][3])
+
+
 @pytest.mark.parametrize("dtype,tol,T", [("f32", 1e-5, 20), ("bf16", 2e-3, 6)])
 @pytest.mark.parametrize("variant", [0, 6])
 def test_er_batch_4096_trace_follow(dtype, tol, T, variant):
