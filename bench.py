@@ -204,9 +204,10 @@ def sweep_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str)
 
 def select_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str, which: str):
     """Roofline of one frontier kernel from a profiled step (which = "rbp":
-    k_select_rbp, "rs": k_select_rs, "rnbp": k_commit_rnbp_wt). RBP reads every
-    residual once per round (4 B), RnBP its eps test (4 B of residual, or 1/8 B
-    of flag words after the streamed update), and both read and write each
+    k_select_rbp, "rs": k_select_rs, "rnbp": the RnBP commit kernel, which runs
+    only when the round does not commit inside the streamed update). RBP reads
+    every residual once per round (4 B), RnBP its eps test (4 B of residual, or
+    1/8 B of flag words after the streamed update), and both read and write each
     committed message (2 s B); the RS selection gathers the residuals of every
     vertex's incoming messages (rev 4 + residual 4 B per message) and writes
     the splash levels and level lists (1 + 4 B per vertex)."""
@@ -227,7 +228,7 @@ def select_roofline(step, dtype: str, n: int, m: int, peak: float, peak_src: str
     a = b / (ms / 1e3) / 1e9
     name = {"rbp": "k_select_rbp (cluster radix top-k of the residuals + commit)",
             "rs": "k_select_rs (vertex residuals, cluster top-k roots, BFS levels, level lists)",
-            "rnbp": "k_commit_rnbp_wt (eps filter + Philox Bernoulli + commit)"}[which]
+            "rnbp": "k_commit_rnbp_pipe / k_commit_rnbp_wt (eps filter + Philox Bernoulli + commit)"}[which]
     return {"bound": "hbm", "kernel": f"{name}, {dtype} messages", "achieved": a, "peak": peak, "unit": "GB/s",
             "peak_source": peak_src, "frac": a / peak, "traffic": None, "launches": launches,
             "bytes_per_launch": b / launches, "avg_launch_us": 1e3 * ms / launches}
