@@ -267,6 +267,12 @@ int bp_set_potentials(bp_graph *g, const float *unary_log, int32_t pair_kind,
  * (defaults). stats (nullable) receives the whole-handle summary: converged =
  * 1 only if all graphs converged, rounds = the largest round count, counters
  * summed. On return the beliefs (Eq. 3) are ready for bp_get_beliefs.
+ * Device memory: the handle keeps two message buffers of the storage format
+ * (n_dir_edges x elements per message), residuals, and per-graph state from
+ * the first run on; an RnBP run on the streamed mapping (kernel_variant 6)
+ * without a recorded trace adds a third message buffer (it writes both
+ * EdgeRatio outcomes of a round, Section IV-A), kept until the storage format
+ * changes or the handle is destroyed. A failed allocation returns BP_ERR_OOM.
  */
 int bp_run(bp_graph *g, int32_t schedule, double parallelism, double eps, int32_t max_rounds,
            const bp_options *opt, bp_run_stats *stats);
