@@ -1392,10 +1392,19 @@ void launch_commit_rnbp(int dtype, const DevGraph &g, const DevRun &dr, const Ru
     if (g.n == 0)
         return;
     if (g.n_wtiles > 0 && rp.eps_words && g.epm == 1 && dtype != DT_F64) {
-        // the flag words of the streamed update: one wave of lane groups
-        BPG_DISPATCH4(dtype, (launch_k(rp.pdl, k_commit_rnbp_pipe<S>,
-                                       std::min(commit_pipe_blocks<S>(), blocks_for(g.n_wtiles, BLOCK / COMMIT_LPT)),
-                                       BLOCK, s, g, dr, rp)));
+        // the flag words of the streamed update (FP32 / BF16 / Q16): one wave of lane groups
+        auto go = [&](auto tag) {
+            using S = decltype(tag);
+            launch_k(rp.pdl, k_commit_rnbp_pipe<S>,
+                     std::min(commit_pipe_blocks<S>(), blocks_for(g.n_wtiles, BLOCK / COMMIT_LPT)), BLOCK, s, g, dr,
+                     rp);
+        };
+        if (dtype == DT_F32)
+            go(float());
+        else if (dtype == DT_BF16)
+            go(__nv_bfloat16());
+        else
+            go(int16_t());
         return;
     }
     if (g.n_wtiles > 0) {
