@@ -88,3 +88,15 @@ def test_select_roofline():
     out = bench.select_roofline([rs], "f32", 100, 400, 1000.0, "m", "rs")
     assert out["achieved"] == pytest.approx((8 * 4000 + 5 * 1000) / 0.4e-3 / 1e9)
     assert bench.select_roofline([rs], "f32", 100, 400, 1000.0, "m", "rbp") is None
+
+
+def test_mcnemar_exact_known_values():
+    """The statistics tests' paired test: two-sided exact McNemar p-values,
+    against Binomial(n, 1/2) tails worked by hand (8 pairs all on one side:
+    2 / 2^8; 5 against 1: 2 (1 + 6) / 2^6)."""
+    from tests._stats import mcnemar_exact
+    assert mcnemar_exact(0, 0) == 1.0
+    assert mcnemar_exact(8, 0) == 2 / 2 ** 8
+    assert mcnemar_exact(0, 8) == 2 / 2 ** 8
+    assert mcnemar_exact(5, 1) == 2 * 7 / 2 ** 6
+    assert mcnemar_exact(3, 3) == 1.0

@@ -19,13 +19,13 @@ of the seeds; a single marginal seed, 1448 against 374 rounds, moves the mean
 log ratio of 8 seeds by 0.17). The per-seed statement holds exactly for FP64
 messages: there GPU and oracle select the same frontiers every round, so
 converged flags and round counts are identical on all 50 seeds."""
-import math
 import multiprocessing as mp
 
 import numpy as np
 import pytest
 
 from paper_1909_11469_gb300 import bp, synth
+from tests._stats import mcnemar_exact
 
 pytestmark = pytest.mark.gpu
 
@@ -46,17 +46,6 @@ def _oracle_one(args):
     return r["converged"], r["rounds"], r["beliefs"]
 
 
-def _mcnemar_exact(b, c):
-    """Two-sided exact McNemar p-value of b against c discordant pairs: under
-    equal converged fractions each discordant seed leans either way with
-    probability 1/2."""
-    n = b + c
-    if n == 0:
-        return 1.0
-    tail = sum(math.comb(n, i) for i in range(min(b, c) + 1)) / 2.0 ** n
-    return min(1.0, 2.0 * tail)
-
-
 def _compare(side, beta_max, sched, par, cap, n_seeds=50):
     batch = synth.ising_grid_batch(side, beta_max, range(n_seeds))
     with bp.Graph(batch) as g:
@@ -71,7 +60,7 @@ def _compare(side, beta_max, sched, par, cap, n_seeds=50):
     if sched == "rnbp":
         b = int((conv_g & ~conv_o).sum())
         c = int((conv_o & ~conv_g).sum())
-        pv = _mcnemar_exact(b, c)
+        pv = mcnemar_exact(b, c)
         print(f"\n  converged on the GPU only: {b}, on the oracle only: {c} (exact McNemar p = {pv:.3f})")
         assert pv >= 0.01, (b, c, pv)
     else:
